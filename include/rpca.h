@@ -1,0 +1,185 @@
+/*
+ * rpca.h -- C-ABI of the GB300 randomized block-Lanczos PCA library.
+ *
+ * Computes the rank-k approximation A ~ U diag(S) V^T of Halko, Martinsson,
+ * Shkolnisky and Tygert, "An algorithm for the principal component analysis
+ * of large data sets" (Section 1, eq. svd_approx; Section 3, Steps 1-6):
+ *
+ *   Step 1  G (n x l) standard Gaussian; H^(0) = A G; H^(j) = A (A^T H^(j-1))
+ *           for j = 1..i (eqs. first_prod .. last_prod), H = [H^(0) .. H^(i)]
+ *   Step 2  H = Q R with Q m x (i+1)l orthonormal (eq. good_approx23)
+ *   Step 3  T = A^T Q (eq. product_t3)
+ *   Step 4  T = V~ Sigma~ W^T, singular values descending (eq. svd_small3)
+ *   Step 5  U~ = Q W (eq. product33)
+ *   Step 6  U = U~[:, :k], V = V~[:, :k], S = diag(Sigma~)[:k]
+ *
+ * Every streamed pass over A (Step 1's products and Step 3) reads each row
+ * tile of A once: pass j forms H^(j)_b = A_b X and accumulates
+ * F += A_b^T H^(j)_b in the same kernel, where X = G for j = 0 and the
+ * orthonormalised F of the previous pass otherwise (the normalised iteration
+ * suggested by the Remark on over/underflow at the end of Section 3; same
+ * span(H) in exact arithmetic).  A row-major A is the layout of Section 4.2.
+ *
+ * Conventions for every function below
+ *   - Matrices are row-major with an explicit leading dimension (elements).
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary host memory.  Pointers marked
+ *     "host or device" are copied with cudaMemcpyDefault.
+ *   - The caller owns every buffer it passes; the library owns its
+ *     workspace, allocated in rpca_init and freed by rpca_destroy /
+ *     rpca_finish.
+ *   - No exception or longjmp crosses this boundary: every call returns an
+ *     rpca_status.  After an error the context stays valid for
+ *     rpca_last_error and rpca_destroy.
+ *   - Without a usable CUDA device every call that would compute returns
+ *     RPCA_ENODEV; there is no CPU fallback.
+ *   - One context per host thread; calls on one context are not reentrant.
+ */
+#ifndef RPCA_H
+#define RPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RPCA_OK = 0,
+  RPCA_MORE = 1,          /* rpca_pass: more passes remain */
+  RPCA_EINVAL = -1,       /* invalid argument (sizes, pointers, dtype) */
+  RPCA_ENOMEM = -2,       /* device or pinned-host allocation failed */
+  RPCA_ECUDA = -3,        /* a CUDA runtime/driver call failed */
+  RPCA_ENODEV = -4,       /* no usable CUDA device */
+  RPCA_EBREAKDOWN = -5,   /* QR could not orthonormalise (rank loss) */
+  RPCA_ETIMEOUT = -6,     /* a bounded device-side wait gave up */
+  RPCA_ESTATE = -7        /* call out of order (e.g. finish before passes) */
+} rpca_status;
+
+/* Storage type of A.  Compute precision: FP64 for RPCA_F64, otherwise FP32
+ * accumulation (tensor-core inputs TF32 / BF16 / FP8 widened to BF16). */
+typedef enum {
+  RPCA_F64 = 0,
+  RPCA_F32 = 1,
+  RPCA_BF16 = 2,
+  RPCA_FP8E4M3 = 3        /* OCP e4m3 bytes, with per-column FP32 scales */
+} rpca_dtype;
+
+/* rpca_problem.flags */
+#define RPCA_CENTER     0x1u  /* subtract column means first (Section 1) */
+#define RPCA_HOST_A     0x2u  /* A lives in host memory (pinned recommended);
+                                 each pass streams it to the device in tiles
+                                 of tile_rows rows, double-buffered (the
+                                 out-of-core form of Section 4.2) */
+#define RPCA_SIMT       0x4u  /* force the CUDA-core pass kernels (testing) */
+
+typedef struct {
+  int64_t m, n;           /* A is m x n; 1 <= k < min(m, n) */
+  int32_t k, l, i;        /* rank, block width (l >= k), power steps (i >= 0);
+                             (i+1) l <= min(m, n) (Sections 2-3) */
+  uint64_t seed;          /* G drawn from Philox4x32-10, key = seed, domain 0,
+                             Box-Muller, row-major, when G == NULL */
+  const double* G;        /* optional host FP64 test matrix, row-major
+                             min... rows: n x l when n <= m, else m x l */
+  rpca_dtype dtype;       /* storage type of A */
+  uint32_t flags;         /* RPCA_* flags above */
+  int64_t tile_rows;      /* RPCA_HOST_A: rows per streamed tile (0: 1 GiB) */
+  void* stream;           /* cudaStream_t for all work; NULL: library stream */
+} rpca_problem;
+
+typedef struct {
+  const void* data;       /* m x n row-major, type = problem dtype; device
+                             memory, or host memory with RPCA_HOST_A */
+  int64_t ld;             /* leading dimension in elements, >= n */
+  const float* col_scale; /* device FP32[n]: value = stored * col_scale[j];
+                             required for RPCA_FP8E4M3, optional otherwise
+                             (NULL = 1) */
+} rpca_matrix;
+
+typedef struct rpca_ctx rpca_ctx;
+
+/* Validate *p, allocate the workspace on the current device and draw G.
+ * Errors: RPCA_EINVAL (bad sizes/flags), RPCA_ENODEV, RPCA_ENOMEM. */
+rpca_status rpca_init(rpca_ctx** out, const rpca_problem* p);
+
+/* One streamed pass over A (Section 4.2).  Passes 0..i are the fused
+ * Step-1 passes; pass i+1 runs Step 2 (QR of H) and then Step 3 (T = A^T Q).
+ * Returns RPCA_MORE while passes remain, RPCA_OK after the last.  A must be
+ * the same matrix on every call.  Work is queued on the context stream. */
+rpca_status rpca_pass(rpca_ctx* c, const rpca_matrix* A);
+
+/* Steps 4-6 and copy-out.  U: m x k (ldu >= k), V: n x k (ldv >= k), element
+ * type FP64 for RPCA_F64 problems and FP32 otherwise; S: k FP64 values,
+ * descending.  U, S, V are host or device pointers (NULL skips that output).
+ * Synchronises the stream and reports any device-side error.  Does not free
+ * the context. */
+rpca_status rpca_finish(rpca_ctx* c, void* U, int64_t ldu, double* S,
+                        void* V, int64_t ldv);
+
+/* Free the context and its workspace.  NULL is a no-op. */
+void rpca_destroy(rpca_ctx* c);
+
+/* init + all passes + finish + destroy in one call. */
+rpca_status rpca_run(const rpca_problem* p, const rpca_matrix* A, void* U,
+                     int64_t ldu, double* S, void* V, int64_t ldv);
+
+/* Re-run all passes and Steps 2-6 on a new A of the same shape and type,
+ * reusing the context's workspace and G (no allocation). */
+rpca_status rpca_rerun(rpca_ctx* c, const rpca_matrix* A, void* U,
+                       int64_t ldu, double* S, void* V, int64_t ldv);
+
+const char* rpca_strerror(rpca_status s);
+/* Last error message of a context (never NULL). */
+const char* rpca_last_error(const rpca_ctx* c);
+
+/* ---------------------------------------------------------------------- */
+/* Single operations (used by the tests to check one pass at a time).     */
+/* All pointers device memory unless noted; FP32 compute unless dtype is   */
+/* RPCA_F64 (then FP64 buffers).  Work runs on `stream` (NULL = default).  */
+/* ---------------------------------------------------------------------- */
+
+/* One fused pass of Step 1 (eqs. first_prod..last_prod, Section 4.2):
+ *   H[:, 0:p] = A_c X        (m x p, ldh)
+ *   F         = A_c^T H      (n x p, ldf; overwritten; skipped if F NULL)
+ * with A_c = A diag(col_scale) - 1 shift^T (shift NULL = 0, FP32/FP64 as
+ * compute).  X: n x p, ldx.  p <= 256.  kernel: 0 auto, 1 CUDA cores,
+ * 2 tensor cores (RPCA_EINVAL where unsupported). */
+rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n,
+                               int32_t p, const void* A, int64_t lda,
+                               const float* col_scale, const void* shift,
+                               const void* X, int64_t ldx, void* H,
+                               int64_t ldh, void* F, int64_t ldf,
+                               int32_t kernel, void* stream);
+
+/* Step 3 (eq. product_t3): T = A_c^T Q, T n x w (ldt), Q m x w (ldq). */
+rpca_status rpca_op_t_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t w,
+                           const void* A, int64_t lda, const float* col_scale,
+                           const void* shift, const void* Q, int64_t ldq,
+                           void* T, int64_t ldt, int32_t kernel, void* stream);
+
+/* Step 2 on a block-structured H (m x (nblk*l), ld): replaces H by Q with
+ * orthonormal columns spanning the same space (block Gram-Schmidt twice +
+ * Cholesky QR twice, Gram matrices and Cholesky in FP64). */
+rpca_status rpca_op_qr(int32_t f64, int64_t m, int32_t nblk, int32_t l,
+                       void* H, int64_t ld, void* stream);
+
+/* Step 4 on T (n x w, ldt, FP32 or FP64 per f64): S[w] (FP64, device),
+ * Vt (n x w, ldv, same type as T) and W (w x w FP64 row-major, device). */
+rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w,
+                              const void* T, int64_t ldt, double* S, void* Vt,
+                              int64_t ldv, double* W, void* stream);
+
+/* Library-side test-matrix stream: `count` standard normals (FP64, host)
+ * from Philox4x32-10 (key = seed, counter = (p, 0, domain, 0)) and
+ * Box-Muller, element 2p and 2p+1 from counter p. */
+rpca_status rpca_gaussian(uint64_t seed, uint32_t domain, int64_t count,
+                          double* out);
+
+/* Number of the library's own kernels launched since load (all devices). */
+uint64_t rpca_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPCA_H */

@@ -1,0 +1,718 @@
+// Small and tall-skinny linear algebra around the streamed passes:
+//   Step 2 (QR of H): block Gram-Schmidt twice + Cholesky QR twice, Gram
+//           matrices accumulated in FP64, Cholesky in FP64;
+//   Step 4 (SVD of T): QR of T the same way, then one-sided Jacobi on its
+//           triangular factor;
+//   Steps 5-6 and the centring corrections: tall x small products.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rpca {
+
+namespace {
+
+template <typename TC>
+__device__ __forceinline__ TC ld_or0(const TC* p, bool ok) { return ok ? *p : TC(0); }
+
+// ------------------------------------------------------------------- Gram
+// C[p0.., q0..] += X^T Y over this block's rows.  256 threads, 64 x 64 tile.
+// Products summed in the compute type over SUB rows, then in FP64.
+template <typename TC>
+__global__ void __launch_bounds__(256)
+k_gram(int64_t m, int p, int q, const TC* __restrict__ X, int64_t ldx, const TC* __restrict__ Y,
+       int64_t ldy, double* __restrict__ C, int64_t ldc, int64_t rows_per_block,
+       const uint32_t* __restrict__ active) {
+  if (active && *active == 0u) return;
+  constexpr int RC = 32;                       // rows per smem chunk
+  constexpr int SUB = 256;                     // rows per FP64 flush
+  __shared__ TC Xs[RC][64 + 1];
+  __shared__ TC Ys[RC][64 + 1];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int p0 = blockIdx.y * 64, q0 = blockIdx.z * 64;
+  const int64_t rbeg = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t rend = min(m, rbeg + rows_per_block);
+  TC acc[4][4];
+  double dacc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc[a][b] = TC(0); dacc[a][b] = 0.0; }
+  int since = 0;
+  for (int64_t r0 = rbeg; r0 < rend; r0 += RC) {
+    for (int e = tid; e < RC * 64; e += 256) {
+      int rr = e / 64, cc = e % 64;
+      int64_t r = r0 + rr;
+      bool rok = r < rend;
+      Xs[rr][cc] = ld_or0(X + r * ldx + p0 + cc, rok && p0 + cc < p);
+      Ys[rr][cc] = ld_or0(Y + r * ldy + q0 + cc, rok && q0 + cc < q);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < RC; ++rr) {
+      TC xv[4], yv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xv[a] = Xs[rr][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yv[b] = Ys[rr][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xv[a], yv[b], acc[a][b]);
+    }
+    __syncthreads();
+    since += RC;
+    if (since >= SUB) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { dacc[a][b] += (double)acc[a][b]; acc[a][b] = TC(0); }
+      since = 0;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int i = p0 + ty * 4 + a, j = q0 + tx * 4 + b;
+      if (i < p && j < q) atomicAdd(&C[(int64_t)i * ldc + j], dacc[a][b] + (double)acc[a][b]);
+    }
+}
+
+// ------------------------------------------------------------------ X * M
+template <typename TC, int BM>
+__global__ void __launch_bounds__(256)
+k_gemm_xm(int64_t m, int p, int q, const TC* __restrict__ X, int64_t ldx,
+          const double* __restrict__ M, int64_t ldm, double alpha, double beta, TC* Y, int64_t ldy,
+          const uint32_t* __restrict__ active) {
+  if (active && *active == 0u) return;
+  constexpr int RPT = BM / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* Xs = reinterpret_cast<TC*>(smem_raw);          // [BM][p]
+  TC* Ms = Xs + BM * p;                               // [p][64]
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int64_t nblk = (m + BM - 1) / BM;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t r0 = blk * BM;
+    for (int e = tid; e < BM * p; e += 256) {
+      int rr = e / p, kk = e % p;
+      int64_t r = r0 + rr;
+      Xs[e] = (r < m) ? X[r * ldx + kk] : TC(0);
+    }
+    __syncthreads();                                  // rows staged before any write
+    for (int c0 = 0; c0 < q; c0 += 64) {
+      for (int e = tid; e < p * 64; e += 256) {
+        int kk = e / 64, cc = e % 64;
+        Ms[e] = (c0 + cc < q) ? TC(alpha * M[(int64_t)kk * ldm + c0 + cc]) : TC(0);
+      }
+      __syncthreads();
+      TC acc[RPT][4];
+#pragma unroll
+      for (int a = 0; a < RPT; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = TC(0);
+      for (int kk = 0; kk < p; ++kk) {
+        TC mv[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) mv[b] = Ms[kk * 64 + tx * 4 + b];
+#pragma unroll
+        for (int a = 0; a < RPT; ++a) {
+          TC xv = Xs[(ty * RPT + a) * p + kk];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(xv, mv[b], acc[a][b]);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < RPT; ++a) {
+        int64_t r = r0 + ty * RPT + a;
+        if (r >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int c = c0 + tx * 4 + b;
+          if (c < q) {
+            TC* y = Y + r * ldy + c;
+            *y = (beta == 0.0) ? acc[a][b] : TC(beta) * (*y) + acc[a][b];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// --------------------------------------------------------------- Cholesky
+// One CTA.  G = R^T R (R upper), then Rinv by back substitution.
+// Pass `pass` (0..3) of a Cholesky-QR sequence on one block (qf: 4 words
+// private to the block: qf[0] = which passes needed a shift, qf[2], qf[3] =
+// whether passes 2 and 3 run).  A pivot below piv_rel * max(diag G) retries
+// with G + shift_rel * max(diag G) I (shifted Cholesky QR); passes 2-3 only
+// run after a shifted pass and otherwise leave identities (exact no-ops).
+__global__ void __launch_bounds__(256)
+k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ R,
+       double* __restrict__ Rinv, int pass, double piv_rel, double shift_rel, uint32_t* qf,
+       uint32_t* dev_err) {
+  const int tid = threadIdx.x;
+  __shared__ int fail;
+  __shared__ double dmax;
+  const bool active = (pass < 2) || (qf[pass] != 0u);
+  if (!active) {
+    for (int e = tid; e < p * p; e += blockDim.x) {
+      double v = (e / p == e % p) ? 1.0 : 0.0;
+      R[e] = v;
+      Rinv[e] = v;
+    }
+    if (tid == 0 && pass == 2) qf[3] = 0u;
+    return;
+  }
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < p; ++i) mx = fmax(mx, G[(int64_t)i * ldg + i]);
+    dmax = mx;
+    if (pass == 0) qf[0] = 0u;
+  }
+  __syncthreads();
+  bool shifted = false;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const double shift = (attempt == 0) ? 0.0 : shift_rel * dmax;
+    for (int e = tid; e < p * p; e += blockDim.x) {
+      int i = e / p, j = e % p;
+      R[e] = (j >= i) ? G[(int64_t)i * ldg + j] + (i == j ? shift : 0.0) : 0.0;
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int k = 0; k < p; ++k) {
+      double d = R[k * p + k];
+      bool bad = !(d > piv_rel * dmax) || !isfinite(d);
+      if (bad) {
+        if (tid == 0) fail = 1;
+        break;
+      }
+      double rkk = sqrt(d);
+      __syncthreads();
+      for (int j = k + tid; j < p; j += blockDim.x) R[k * p + j] = (j == k) ? rkk : R[k * p + j] / rkk;
+      __syncthreads();
+      const int nt = p - k - 1;
+      for (int e = tid; e < nt * nt; e += blockDim.x) {
+        int i = k + 1 + e / nt, j = k + 1 + e % nt;
+        if (j >= i) R[i * p + j] -= R[k * p + i] * R[k * p + j];
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!fail) break;
+    if (attempt == 1 || !(dmax > 0.0) || !isfinite(dmax)) {
+      if (tid == 0) atomicOr(dev_err, DEV_ERR_BREAKDOWN);
+      for (int e = tid; e < p * p; e += blockDim.x) {
+        double v = (e / p == e % p) ? 1.0 : 0.0;
+        R[e] = v;
+        Rinv[e] = v;
+      }
+      return;
+    }
+    shifted = true;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (shifted) {
+      qf[0] |= 1u << pass;
+      atomicOr(dev_err, DEV_ERR_SHIFTED);
+      if (pass == 3) atomicOr(dev_err, DEV_ERR_BREAKDOWN);
+    }
+    if (pass == 1) qf[2] = (qf[0] & 3u) ? 1u : 0u;
+    if (pass == 2) qf[3] = ((qf[0] >> 1) & 3u) ? 1u : 0u;
+  }
+  __syncthreads();
+  // Rinv: column c solves R x = e_c (upper triangular back substitution).
+  for (int c = tid; c < p; c += blockDim.x) {
+    for (int i = p - 1; i >= 0; --i) {
+      double v;
+      if (i > c) {
+        v = 0.0;
+      } else {
+        double sum = (i == c) ? 1.0 : 0.0;
+        for (int j = i + 1; j <= c; ++j) sum -= R[i * p + j] * Rinv[j * p + c];
+        v = sum / R[i * p + i];
+      }
+      Rinv[i * p + c] = v;
+    }
+  }
+}
+
+// Racc (p x p) = Rk * Racc, FP64, one CTA (accumulates the triangular
+// factor of a Cholesky-QR sequence: H = Q (R3 R2 R1 R0)).
+__global__ void k_left_mul(int p, const double* __restrict__ Rk, double* __restrict__ Racc) {
+  extern __shared__ double tmp[];
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    int i = e / p, j = e % p;
+    double s = 0.0;
+    for (int t = 0; t < p; ++t) s += Rk[i * p + t] * Racc[t * p + j];
+    tmp[e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) Racc[e] = tmp[e];
+}
+
+__global__ void k_set_identity(int p, double* __restrict__ M) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < p * p) M[e] = (e / p == e % p) ? 1.0 : 0.0;
+}
+
+// dst (rows x cols, ldd) += src (ldsrc), FP64
+__global__ void k_mat_add(int rows, int cols, const double* __restrict__ src, int64_t lds,
+                          double* __restrict__ dst, int64_t ldd) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int r = e / cols, c = e % cols;
+  dst[(int64_t)r * ldd + c] += src[(int64_t)r * lds + c];
+}
+
+// ------------------------------------------------------------------ Jacobi
+// One-sided (Hestenes) Jacobi on the columns of B (w x w), one CTA of 1024
+// threads: rounds of a round-robin tournament, one warp per column pair.
+// Columns are stored contiguously (Bc[c*w + r] = B[r][c]); J accumulates the
+// rotations (J[c*w + r] = W[r][c]).
+template <typename TJ>
+__global__ void __launch_bounds__(1024)
+k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc, TJ* __restrict__ Jc,
+         double tol, int max_sweeps, uint32_t* dev_err) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const bool in_smem = ((size_t)w * w * sizeof(TJ) <= 160 * 1024);
+  TJ* Bw = in_smem ? reinterpret_cast<TJ*>(smem_raw) : Bc;
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    int c = e / w, r = e % w;
+    Bw[e] = TJ(B[(int64_t)r * w + c]);
+    Jc[e] = TJ(r == c ? 1 : 0);
+  }
+  __shared__ float off_max;
+  __syncthreads();
+  const int N = w + (w & 1);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) off_max = 0.f;
+    __syncthreads();
+    float local_off = 0.f;
+    for (int rnd = 0; rnd < N - 1; ++rnd) {
+      for (int pi = warp; pi < N / 2; pi += nw) {
+        int a, b;
+        if (pi == 0) { a = N - 1; b = rnd; }
+        else { a = (rnd + pi) % (N - 1); b = (rnd - pi + N - 1) % (N - 1); }
+        if (a >= w || b >= w) continue;
+        const int pcol = min(a, b), qcol = max(a, b);
+        TJ* bp = Bw + (int64_t)pcol * w;
+        TJ* bq = Bw + (int64_t)qcol * w;
+        TJ al = 0, be = 0, ga = 0;
+        for (int r = lane; r < w; r += 32) {
+          TJ x = bp[r], y = bq[r];
+          al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        TJ nrm = sqrt(al * be);
+        if (nrm == TJ(0) || fabs(ga) <= tol * nrm) continue;
+        local_off = fmaxf(local_off, (float)(fabs(ga) / nrm));
+        TJ zeta = (be - al) / (TJ(2) * ga);
+        TJ t = (zeta >= 0 ? TJ(1) : TJ(-1)) / (fabs(zeta) + sqrt(TJ(1) + zeta * zeta));
+        TJ c = TJ(1) / sqrt(TJ(1) + t * t), s = c * t;
+        for (int r = lane; r < w; r += 32) {
+          TJ x = bp[r], y = bq[r];
+          bp[r] = c * x - s * y;
+          bq[r] = s * x + c * y;
+        }
+        TJ* jp = Jc + (int64_t)pcol * w;
+        TJ* jq = Jc + (int64_t)qcol * w;
+        for (int r = lane; r < w; r += 32) {
+          TJ x = jp[r], y = jq[r];
+          jp[r] = c * x - s * y;
+          jq[r] = s * x + c * y;
+        }
+      }
+      __syncthreads();
+    }
+    if (lane == 0 && local_off > 0.f) atomicMax(reinterpret_cast<int*>(&off_max), __float_as_int(local_off));
+    __syncthreads();
+    if (off_max == 0.f) break;
+    __syncthreads();
+  }
+  if (tid == 0 && sweep >= max_sweeps) atomicOr(dev_err, DEV_ERR_JACOBI);
+}
+
+// Normalise the columns of J into W (FP64, row-major w x w).
+template <typename TJ>
+__global__ void k_jacobi_w(int w, const TJ* __restrict__ Jc, double* __restrict__ W) {
+  const int c = blockIdx.x;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int r = threadIdx.x; r < w; r += blockDim.x) {
+    double v = (double)Jc[(int64_t)c * w + r];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double inv = red[0] > 0 ? 1.0 / sqrt(red[0]) : 0.0;
+  for (int r = threadIdx.x; r < w; r += blockDim.x) W[(int64_t)r * w + c] = (double)Jc[(int64_t)c * w + r] * inv;
+}
+
+// B64 = R W already formed (row-major).  Singular values = column norms,
+// sorted descending; Ub = B64 / sigma; W permuted alike.  One CTA.
+__global__ void k_svd_finish(int w, const double* __restrict__ B64, const double* __restrict__ Win,
+                             double* __restrict__ S, double* __restrict__ Ub, double* __restrict__ W) {
+  extern __shared__ double sig[];
+  int* pos = reinterpret_cast<int*>(sig + w);
+  for (int c = threadIdx.x; c < w; c += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < w; ++r) { double v = B64[(int64_t)r * w + c]; s += v * v; }
+    sig[c] = sqrt(s);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < w; c += blockDim.x) {
+    int rank = 0;
+    for (int o = 0; o < w; ++o)
+      rank += (sig[o] > sig[c]) || (sig[o] == sig[c] && o < c);
+    pos[c] = rank;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+    int r = e / w, c = e % w;
+    int d = pos[c];
+    double sc = sig[c];
+    Ub[(int64_t)r * w + d] = sc > 0 ? B64[e] / sc : (r == c ? 1.0 : 0.0);
+    W[(int64_t)r * w + d] = Win[e];
+  }
+  for (int c = threadIdx.x; c < w; c += blockDim.x) S[pos[c]] = sig[c];
+}
+
+// ----------------------------------------------------------------- small ops
+template <typename TA, typename TC>
+__global__ void k_panel_mean(const TA* __restrict__ A, int64_t lda, int64_t rows, int64_t n,
+                             const float* __restrict__ scale, TC* __restrict__ s) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double acc = 0.0;
+  for (int64_t r = 0; r < rows; ++r) {
+    double v;
+    if constexpr (std::is_same<TA, double>::value) v = A[r * lda + j];
+    else v = (double)to_f32(A[r * lda + j]);
+    if (scale) v *= (double)scale[j];
+    acc += v;
+  }
+  s[j] = TC(acc / (double)rows);
+}
+
+template <typename TC>
+__global__ void k_vec_mat(int64_t n, int p, const double* __restrict__ x, const TC* __restrict__ M,
+                          int64_t ldm, double* __restrict__ out) {
+  // one block per output column, reduction over n
+  const int c = blockIdx.x;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s += x[j] * (double)M[j * ldm + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) out[c] = v;
+  }
+}
+
+template <typename TC>
+__global__ void k_cast_from64(int64_t count, const double* __restrict__ src, TC* __restrict__ dst) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < count) dst[e] = TC(src[e]);
+}
+template <typename TC>
+__global__ void k_cast_to64(int64_t count, const TC* __restrict__ src, double* __restrict__ dst) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < count) dst[e] = (double)src[e];
+}
+
+template <typename TC>
+__global__ void k_rank1_sub(int64_t n, int p, double alpha, const double* __restrict__ x,
+                            const double* __restrict__ y, TC* __restrict__ M, int64_t ldm) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * p) return;
+  int64_t j = e / p;
+  int c = (int)(e % p);
+  M[j * ldm + c] = TC((double)M[j * ldm + c] - alpha * x[j] * y[c]);
+}
+
+template <typename TC>
+__global__ void k_column_to_vec(int64_t n, const TC* __restrict__ F, int64_t ldf, int col,
+                                double scale, double* __restrict__ d) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) d[j] = (double)F[j * ldf + col] * scale;
+}
+
+template <typename TC>
+__global__ void k_col_sums(int64_t m, int p, const TC* __restrict__ Q, int64_t ldq,
+                           double* __restrict__ out) {
+  // grid-stride over rows, per-thread column; atomics into FP64 out (zeroed)
+  const int c = threadIdx.x % 64 + blockIdx.y * 64;
+  const int rl = threadIdx.x / 64;
+  if (c >= p) return;
+  double s = 0.0;
+  for (int64_t r = blockIdx.x * 4 + rl; r < m; r += (int64_t)gridDim.x * 4) s += (double)Q[r * ldq + c];
+  atomicAdd(&out[c], s);
+}
+
+template <typename TC>
+__global__ void k_sub_rowvec(int64_t m, int p, const double* __restrict__ v, TC* __restrict__ H,
+                             int64_t ldh) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * p) return;
+  int64_t r = e / p;
+  int c = (int)(e % p);
+  H[r * ldh + c] -= TC(v[c]);
+}
+
+template <typename T>
+__global__ void k_transpose(int64_t rows, int64_t cols, const T* __restrict__ in, int64_t ld_in,
+                            T* __restrict__ out, int64_t ld_out) {
+  // out[r][c] = in[c][r]; out is rows x cols
+  __shared__ T tile[32][33];
+  int64_t c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int64_t ic = c0 + k, ir = r0 + threadIdx.x;   // in row = ic (out col), in col = ir
+    if (ic < cols && ir < rows) tile[k][threadIdx.x] = in[ic * ld_in + ir];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int64_t orow = r0 + k, ocol = c0 + threadIdx.x;
+    if (orow < rows && ocol < cols) out[orow * ld_out + ocol] = tile[threadIdx.x][k];
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void k_copy_matrix(int64_t rows, int64_t cols, const TI* __restrict__ in, int64_t ld_in,
+                              TO* __restrict__ out, int64_t ld_out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t r = e / cols, c = e % cols;
+  out[r * ld_out + c] = TO(in[r * ld_in + c]);
+}
+
+inline unsigned grid1(int64_t count, int threads = 256) {
+  return (unsigned)std::max<int64_t>(1, cdiv(count, threads));
+}
+
+}  // namespace
+
+// ===================================================================== host
+void gram(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, const void* Y,
+          int64_t ldy, double* C, int64_t ldc, bool accumulate, cudaStream_t st,
+          const uint32_t* active) {
+  if (!accumulate)
+    RPCA_CUDA_TRY(cudaMemset2DAsync(C, ldc * sizeof(double), 0, q * sizeof(double), p, st));
+  if (m <= 0) return;
+  const int tp = (int)cdiv(p, 64), tq = (int)cdiv(q, 64);
+  const int sms = num_sms();
+  int64_t want = std::max<int64_t>(1, (int64_t)sms * 4 / (tp * tq));
+  int64_t rpb = std::max<int64_t>(256, round_up(cdiv(m, want), 32));
+  unsigned gx = (unsigned)cdiv(m, rpb);
+  dim3 grid(gx, tp, tq);
+  if (f64)
+    k_gram<double><<<grid, 256, 0, st>>>(m, p, q, (const double*)X, ldx, (const double*)Y, ldy, C, ldc, rpb, active);
+  else
+    k_gram<float><<<grid, 256, 0, st>>>(m, p, q, (const float*)X, ldx, (const float*)Y, ldy, C, ldc, rpb, active);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+template <typename TC, int BM>
+static void gemm_launch(int64_t m, int p, int q, const void* X, int64_t ldx, const double* M,
+                        int64_t ldm, double alpha, double beta, void* Y, int64_t ldy,
+                        cudaStream_t st, const uint32_t* active) {
+  size_t smem = sizeof(TC) * ((size_t)BM * p + (size_t)p * 64);
+  auto kern = k_gemm_xm<TC, BM>;
+  RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int64_t nblk = cdiv(m, BM);
+  unsigned g = (unsigned)std::min<int64_t>(nblk, (int64_t)num_sms() * 4);
+  kern<<<std::max(1u, g), 256, smem, st>>>(m, p, q, (const TC*)X, ldx, M, ldm, alpha, beta, (TC*)Y, ldy, active);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void gemm_xm(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, const double* M,
+             int64_t ldm, double alpha, double beta, void* Y, int64_t ldy, cudaStream_t st,
+             const uint32_t* active) {
+  if (m <= 0 || q <= 0) return;
+  if (p > 256) throw Invalid("gemm_xm: p > 256");
+  if (f64) {
+    if (m <= 1024) gemm_launch<double, 16>(m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy, st, active);
+    else gemm_launch<double, 32>(m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy, st, active);
+  } else {
+    if (m <= 4096) gemm_launch<float, 16>(m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy, st, active);
+    else gemm_launch<float, 64>(m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy, st, active);
+  }
+}
+
+void chol_small(int p, const double* G, int64_t ldg, double* R, double* Rinv, int pass,
+                double piv_rel, double shift_rel, uint32_t* qf, uint32_t* dev_err, cudaStream_t st) {
+  k_chol<<<1, 256, 0, st>>>(p, G, ldg, R, Rinv, pass, piv_rel, shift_rel, qf, dev_err);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void left_mul(int p, const double* Rk, double* Racc, cudaStream_t st) {
+  k_left_mul<<<1, 256, (size_t)p * p * sizeof(double), st>>>(p, Rk, Racc);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void set_identity(int p, double* M, cudaStream_t st) {
+  k_set_identity<<<grid1((int64_t)p * p), 256, 0, st>>>(p, M);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void mat_add(int rows, int cols, const double* src, int64_t lds, double* dst, int64_t ldd,
+             cudaStream_t st) {
+  k_mat_add<<<grid1((int64_t)rows * cols), 256, 0, st>>>(rows, cols, src, lds, dst, ldd);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void jacobi_svd(bool f64, int w, const double* B, double* S, double* Ub, double* W, double* work,
+                uint32_t* dev_err, cudaStream_t st) {
+  // work layout (doubles): Bc [w*w], Jc [w*w], W0 [w*w], B64 [w*w]
+  double* Bc = work;
+  double* Jc = work + (size_t)w * w;
+  double* W0 = work + 2 * (size_t)w * w;
+  double* B64 = work + 3 * (size_t)w * w;
+  if (f64) {
+    size_t smem = (size_t)w * w * sizeof(double) <= 160 * 1024 ? (size_t)w * w * sizeof(double) : 0;
+    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    k_jacobi<double><<<1, 1024, smem, st>>>(w, B, Bc, Jc, 4.0 * std::sqrt((double)w) * 1.11e-16, 60, dev_err);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    k_jacobi_w<double><<<w, 128, 0, st>>>(w, Jc, W0);
+  } else {
+    float* Bc32 = reinterpret_cast<float*>(Bc);
+    float* Jc32 = reinterpret_cast<float*>(Jc);
+    size_t smem = (size_t)w * w * sizeof(float) <= 160 * 1024 ? (size_t)w * w * sizeof(float) : 0;
+    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    k_jacobi<float><<<1, 1024, smem, st>>>(w, B, Bc32, Jc32, 4.0 * std::sqrt((double)w) * 5.96e-8, 40, dev_err);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    k_jacobi_w<float><<<w, 128, 0, st>>>(w, Jc32, W0);
+  }
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch(2);
+  // B64 = B W0 (FP64): singular values as column norms of B times unit
+  // approximate right singular vectors (second-order accurate).
+  gemm_xm(true, w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st, nullptr);
+  size_t smem = (size_t)w * (sizeof(double) + sizeof(int));
+  k_svd_finish<<<1, 256, smem, st>>>(w, B64, W0, S, Ub, W);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void panel_mean(rpca_dtype dt, const void* A, int64_t lda, int64_t rows, int64_t n,
+                const float* scale, void* s, cudaStream_t st) {
+  unsigned g = grid1(n);
+  switch (dt) {
+    case RPCA_F64: k_panel_mean<double, double><<<g, 256, 0, st>>>((const double*)A, lda, rows, n, scale, (double*)s); break;
+    case RPCA_F32: k_panel_mean<float, float><<<g, 256, 0, st>>>((const float*)A, lda, rows, n, scale, (float*)s); break;
+    case RPCA_BF16: k_panel_mean<__nv_bfloat16, float><<<g, 256, 0, st>>>((const __nv_bfloat16*)A, lda, rows, n, scale, (float*)s); break;
+    case RPCA_FP8E4M3: k_panel_mean<__nv_fp8_e4m3, float><<<g, 256, 0, st>>>((const __nv_fp8_e4m3*)A, lda, rows, n, scale, (float*)s); break;
+  }
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void vec_mat(bool f64, int64_t n, int p, const double* x, const void* M, int64_t ldm, double* out,
+             cudaStream_t st) {
+  if (f64) k_vec_mat<double><<<p, 256, 0, st>>>(n, p, x, (const double*)M, ldm, out);
+  else k_vec_mat<float><<<p, 256, 0, st>>>(n, p, x, (const float*)M, ldm, out);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void cast_f64_to(bool f64, int64_t count, const double* src, void* dst, cudaStream_t st) {
+  if (f64) RPCA_CUDA_TRY(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  else {
+    k_cast_from64<float><<<grid1(count), 256, 0, st>>>(count, src, (float*)dst);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+}
+
+void cast_to_f64(bool f64, int64_t count, const void* src, double* dst, cudaStream_t st) {
+  if (f64) RPCA_CUDA_TRY(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  else {
+    k_cast_to64<float><<<grid1(count), 256, 0, st>>>(count, (const float*)src, dst);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+}
+
+void rank1_sub(bool f64, int64_t n, int p, double alpha, const double* x, const double* y, void* M,
+               int64_t ldm, cudaStream_t st) {
+  if (f64) k_rank1_sub<double><<<grid1(n * p), 256, 0, st>>>(n, p, alpha, x, y, (double*)M, ldm);
+  else k_rank1_sub<float><<<grid1(n * p), 256, 0, st>>>(n, p, alpha, x, y, (float*)M, ldm);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void column_to_vec(bool f64, int64_t n, const void* F, int64_t ldf, int col, double scale, double* d,
+                   cudaStream_t st) {
+  if (f64) k_column_to_vec<double><<<grid1(n), 256, 0, st>>>(n, (const double*)F, ldf, col, scale, d);
+  else k_column_to_vec<float><<<grid1(n), 256, 0, st>>>(n, (const float*)F, ldf, col, scale, d);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void col_sums(bool f64, int64_t m, int p, const void* Q, int64_t ldq, double* out, cudaStream_t st) {
+  RPCA_CUDA_TRY(cudaMemsetAsync(out, 0, p * sizeof(double), st));
+  dim3 grid((unsigned)std::min<int64_t>(cdiv(m, 4), 1024), (unsigned)cdiv(p, 64));
+  if (f64) k_col_sums<double><<<grid, 256, 0, st>>>(m, p, (const double*)Q, ldq, out);
+  else k_col_sums<float><<<grid, 256, 0, st>>>(m, p, (const float*)Q, ldq, out);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void sub_rowvec(bool f64, int64_t m, int p, const double* v, void* H, int64_t ldh, cudaStream_t st) {
+  if (f64) k_sub_rowvec<double><<<grid1(m * p), 256, 0, st>>>(m, p, v, (double*)H, ldh);
+  else k_sub_rowvec<float><<<grid1(m * p), 256, 0, st>>>(m, p, v, (float*)H, ldh);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void transpose(rpca_dtype dt, int64_t rows, int64_t cols, const void* in, int64_t ld_in, void* out,
+               int64_t ld_out, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(rows, 32));
+  dim3 blk(32, 8);
+  switch (dtype_bytes(dt)) {
+    case 8: k_transpose<uint64_t><<<grid, blk, 0, st>>>(rows, cols, (const uint64_t*)in, ld_in, (uint64_t*)out, ld_out); break;
+    case 4: k_transpose<uint32_t><<<grid, blk, 0, st>>>(rows, cols, (const uint32_t*)in, ld_in, (uint32_t*)out, ld_out); break;
+    case 2: k_transpose<uint16_t><<<grid, blk, 0, st>>>(rows, cols, (const uint16_t*)in, ld_in, (uint16_t*)out, ld_out); break;
+    default: k_transpose<uint8_t><<<grid, blk, 0, st>>>(rows, cols, (const uint8_t*)in, ld_in, (uint8_t*)out, ld_out); break;
+  }
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void copy_matrix(bool in_f64, bool out_f64, int64_t rows, int64_t cols, const void* in, int64_t ld_in,
+                 void* out, int64_t ld_out, cudaStream_t st) {
+  unsigned g = grid1(rows * cols);
+  if (in_f64 && out_f64) k_copy_matrix<double, double><<<g, 256, 0, st>>>(rows, cols, (const double*)in, ld_in, (double*)out, ld_out);
+  else if (in_f64) k_copy_matrix<double, float><<<g, 256, 0, st>>>(rows, cols, (const double*)in, ld_in, (float*)out, ld_out);
+  else if (out_f64) k_copy_matrix<float, double><<<g, 256, 0, st>>>(rows, cols, (const float*)in, ld_in, (double*)out, ld_out);
+  else k_copy_matrix<float, float><<<g, 256, 0, st>>>(rows, cols, (const float*)in, ld_in, (float*)out, ld_out);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+}  // namespace rpca

@@ -1,0 +1,95 @@
+// Internal launcher interface between the host orchestration and kernels.
+#pragma once
+#include "common.cuh"
+
+namespace rpca {
+
+enum PassMode { MODE_FUSED = 0, MODE_H = 1, MODE_T = 2 };
+
+// One streamed pass over A (see k_stream_simt.cu / k_stream_tc.cu).
+struct PassArgs {
+  rpca_dtype dtype = RPCA_F32;
+  int mode = MODE_FUSED;
+  const void* A = nullptr;
+  int64_t lda = 0, m = 0, n = 0;
+  const float* scale = nullptr;  // per-column scale (FP8), may be null
+  const void* shift = nullptr;   // per-column shift (compute type), may be null
+  const void* X = nullptr;       // n x p right factor (compute type)
+  int64_t ldx = 0;
+  int p = 0;                     // columns of X / H / F
+  void* H = nullptr;             // m x p output (MODE_FUSED/H) or input Q (MODE_T)
+  int64_t ldh = 0;
+  const void* corr = nullptr;    // p-vector subtracted from each H row, may be null
+  int ones_col = -1;             // >= 0: F column `ones_col` accumulates A~^T 1
+  void* F = nullptr;             // n x (p [+1]) accumulator (zeroed by the launcher)
+  int64_t ldf = 0;
+  bool accumulate_f = false;     // true: add into F (caller zeroed it)
+};
+
+void launch_pass_simt(const PassArgs& a, cudaStream_t st);
+// Tensor-core pass; returns false when the shape/dtype is not supported.
+bool launch_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
+
+// ---------------------------------------------------------------- linalg
+// C (p x q, FP64, ldc) (+)= X^T Y over rows [0, m); X m x p (ldx), Y m x q.
+// Compute type TC: FP32 sums over short row chunks, FP64 accumulation.
+void gram(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, const void* Y,
+          int64_t ldy, double* C, int64_t ldc, bool accumulate, cudaStream_t st,
+          const uint32_t* active = nullptr);
+// Y[:, 0:q] = beta * Y + alpha * X M, X m x p, M p x q FP64 (ldm).  In-place
+// safe when Y aliases X (rows are staged before they are overwritten).
+// `active` (device word, may be null): the kernel does nothing when it is 0.
+void gemm_xm(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, const double* M,
+             int64_t ldm, double alpha, double beta, void* Y, int64_t ldy, cudaStream_t st,
+             const uint32_t* active = nullptr);
+// Pass `pass` (0..3) of a Cholesky-QR sequence on one block: factor the
+// FP64 Gram G = R^T R (R upper), write R and Rinv (p x p, ld p).  A pivot
+// below piv_rel * max diag retries with a diagonal shift shift_rel * max
+// diag.  Passes 2 and 3 run only after a shifted pass (else identities).
+// qf: 4 device words private to the block; the word qf + pass gates the
+// Gram/gemm of passes 2-3 (qf[2], qf[3]).
+void chol_small(int p, const double* G, int64_t ldg, double* R, double* Rinv, int pass,
+                double piv_rel, double shift_rel, uint32_t* qf, uint32_t* dev_err, cudaStream_t st);
+// Racc = Rk * Racc (p x p FP64)
+void left_mul(int p, const double* Rk, double* Racc, cudaStream_t st);
+// M = I (p x p FP64)
+void set_identity(int p, double* M, cudaStream_t st);
+// dst += src (rows x cols FP64)
+void mat_add(int rows, int cols, const double* src, int64_t lds, double* dst, int64_t ldd,
+             cudaStream_t st);
+// One-sided Jacobi SVD of a w x w FP64 matrix B (row-major): B = Ub S W^T,
+// S descending.  FP32 sweeps with an FP64 finish (f64 = false) or FP64.
+// work: 4 w^2 doubles.
+void jacobi_svd(bool f64, int w, const double* B, double* S, double* Ub, double* W,
+                double* work, uint32_t* dev_err, cudaStream_t st);
+
+// ----------------------------------------------------------------- small ops
+// s[j] = mean of (scaled) A[0:rows, j] in the compute type.
+void panel_mean(rpca_dtype dt, const void* A, int64_t lda, int64_t rows, int64_t n,
+                const float* scale, void* s, cudaStream_t st);
+// out[c] = sum_j x[j] * M[j, c] (x length n FP64, M n x p compute type).
+void vec_mat(bool f64, int64_t n, int p, const double* x, const void* M, int64_t ldm,
+             double* out, cudaStream_t st);
+// v (compute type, p) = out (FP64) cast.
+void cast_f64_to(bool f64, int64_t count, const double* src, void* dst, cudaStream_t st);
+void cast_to_f64(bool f64, int64_t count, const void* src, double* dst, cudaStream_t st);
+// M[j, c] -= alpha * x[j] * y[c] for j < n, c < p (M compute type).
+void rank1_sub(bool f64, int64_t n, int p, double alpha, const double* x, const double* y,
+               void* M, int64_t ldm, cudaStream_t st);
+// d[j] = F[j, col] / m  (F compute type, d FP64)
+void column_to_vec(bool f64, int64_t n, const void* F, int64_t ldf, int col, double scale,
+                   double* d, cudaStream_t st);
+// colsum[c] = sum_r Q[r, c]  (FP64 out)
+void col_sums(bool f64, int64_t m, int p, const void* Q, int64_t ldq, double* out,
+              cudaStream_t st);
+// H[r, c] -= v[c]
+void sub_rowvec(bool f64, int64_t m, int p, const double* v, void* H, int64_t ldh,
+                cudaStream_t st);
+// out (rows x cols, ld_out) = in^T (cols x rows, ld_in), storage type dt
+void transpose(rpca_dtype dt, int64_t rows, int64_t cols, const void* in, int64_t ld_in,
+               void* out, int64_t ld_out, cudaStream_t st);
+// 2-D strided copy of compute-type matrix with optional type change to out_f64
+void copy_matrix(bool in_f64, bool out_f64, int64_t rows, int64_t cols, const void* in,
+                 int64_t ld_in, void* out, int64_t ld_out, cudaStream_t st);
+
+}  // namespace rpca

@@ -1,0 +1,666 @@
+// C-ABI and host orchestration of the randomized block-Lanczos PCA
+// (Halko, Martinsson, Shkolnisky, Tygert, Section 3, Steps 1-6; streamed
+// passes as in Section 4.2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rpca {
+
+std::atomic<uint64_t> g_launches{0};
+
+// ------------------------------------------------------------- Philox (host)
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with key bumps by the Weyl constants.
+static void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Standard normals: counter (p, 0, domain, 0); two 53-bit uniforms per
+// counter; Box-Muller gives elements 2p and 2p+1.
+static void gaussian_stream(uint64_t seed, uint32_t domain, int64_t count, double* out) {
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  const double two_pi = 6.283185307179586476925286766559;
+  const double scale = 1.0 / 9007199254740992.0;  // 2^-53
+  for (int64_t p = 0; 2 * p < count; ++p) {
+    uint32_t c[4] = {(uint32_t)((uint64_t)p & 0xffffffffu), (uint32_t)((uint64_t)p >> 32), domain, 0u};
+    philox4x32_10(c, k0, k1);
+    double u1 = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6) + 0.5) * scale;
+    double u2 = ((double)(c[2] >> 5) * 67108864.0 + (double)(c[3] >> 6) + 0.5) * scale;
+    double r = std::sqrt(-2.0 * std::log(u1));
+    double t = two_pi * u2;
+    out[2 * p] = r * std::cos(t);
+    if (2 * p + 1 < count) out[2 * p + 1] = r * std::sin(t);
+  }
+}
+
+// --------------------------------------------------------------- utilities
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  void alloc(size_t b) {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = b;
+    if (b == 0) return;
+    cudaError_t e = cudaMalloc(&ptr, b);
+    if (e != cudaSuccess) {
+      ptr = nullptr;
+      throw CudaFailure(e, "cudaMalloc", __FILE__, __LINE__);
+    }
+  }
+  ~DevBuf() {
+    if (ptr) cudaFree(ptr);
+  }
+  template <typename T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+static bool device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void check_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    throw CudaFailure(cudaErrorNoDevice, "cudaGetDeviceCount", __FILE__, __LINE__);
+  }
+}
+
+// Block Gram-Schmidt twice + Cholesky QR (up to 4 passes) on H (m x nblk*l):
+// Step 2 with Gram matrices and Cholesky factors in FP64.  Optional R_out
+// (w x w FP64, ld w, zeroed here) receives the triangular factor.
+struct QrScratch {
+  double* C = nullptr;     // w x l
+  double* Gm = nullptr;    // l x l
+  double* Rk = nullptr;    // l x l
+  double* Rinv = nullptr;  // l x l
+  double* Racc = nullptr;  // l x l
+  uint32_t* qf = nullptr;  // 4 words per block
+};
+
+static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, double* R_out,
+                     const QrScratch& s, uint32_t* dev_err, cudaStream_t st) {
+  const size_t es = f64 ? 8 : 4;
+  const int w = nblk * l;
+  const double piv_rel = f64 ? 1e-12 : 1e-5;
+  const double shift_rel = f64 ? 1e-12 : 1e-5;
+  if (R_out) RPCA_CUDA_TRY(cudaMemsetAsync(R_out, 0, (size_t)w * w * sizeof(double), st));
+  for (int j = 0; j < nblk; ++j) {
+    char* Hj = static_cast<char*>(H) + (size_t)j * l * es;
+    const int jl = j * l;
+    if (j > 0) {
+      for (int rep = 0; rep < 2; ++rep) {
+        gram(f64, m, jl, l, H, ld, Hj, ld, s.C, l, false, st);
+        gemm_xm(f64, m, jl, l, H, ld, s.C, l, -1.0, 1.0, Hj, ld, st);
+        if (R_out) mat_add(jl, l, s.C, l, R_out + jl, w, st);
+      }
+    }
+    uint32_t* qf = s.qf + 4 * j;
+    if (R_out) set_identity(l, s.Racc, st);
+    for (int pass = 0; pass < 4; ++pass) {
+      const uint32_t* active = pass >= 2 ? qf + pass : nullptr;
+      gram(f64, m, l, l, Hj, ld, Hj, ld, s.Gm, l, false, st, active);
+      chol_small(l, s.Gm, l, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st);
+      gemm_xm(f64, m, l, l, Hj, ld, s.Rinv, l, 1.0, 0.0, Hj, ld, st, active);
+      if (R_out) left_mul(l, s.Rk, s.Racc, st);
+    }
+    if (R_out) mat_add(l, l, s.Racc, l, R_out + (size_t)jl * w + jl, w, st);
+  }
+}
+
+}  // namespace rpca
+
+using namespace rpca;
+
+// ============================================================ the context
+struct rpca_ctx {
+  rpca_problem prob{};
+  bool f64 = false, transposed = false, host_a = false, simt = false;
+  int64_t m = 0, n = 0;   // working orientation (m >= n)
+  int k = 0, l = 0, i = 0, w = 0;
+  int64_t ldx = 0;        // ld of X and F (compute type)
+  cudaStream_t stream = nullptr, copy_stream = nullptr;
+  bool own_stream = false;
+  int next_pass = 0;
+  bool centered = false;
+  std::string last_error;
+
+  DevBuf X, F, H, T, shift, corr, d, vtmp, q1, G64, small, err, At, tiles[2];
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  int64_t tile_rows = 0;
+  QrScratch qs;
+  double *RT = nullptr, *S = nullptr, *Ub = nullptr, *W = nullptr, *svdwork = nullptr;
+  DevBuf outU, outV;
+
+  ~rpca_ctx() {
+    for (int t = 0; t < 2; ++t) {
+      if (ev_copied[t]) cudaEventDestroy(ev_copied[t]);
+      if (ev_used[t]) cudaEventDestroy(ev_used[t]);
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+  size_t cbytes() const { return f64 ? 8 : 4; }
+  uint32_t* dev_err() const { return err.as<uint32_t>(); }
+};
+
+namespace {
+
+rpca_status fail(rpca_ctx* c, rpca_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+template <typename Fn>
+rpca_status guarded(rpca_ctx* c, Fn&& fn) {
+  try {
+    return fn();
+  } catch (const CudaFailure& e) {
+    rpca_status s = RPCA_ECUDA;
+    if (e.code == cudaErrorMemoryAllocation) s = RPCA_ENOMEM;
+    if (e.code == cudaErrorNoDevice || e.code == cudaErrorInsufficientDriver) s = RPCA_ENODEV;
+    return fail(c, s, e.what);
+  } catch (const Invalid& e) {
+    return fail(c, RPCA_EINVAL, e.what);
+  } catch (const std::bad_alloc&) {
+    return fail(c, RPCA_ENOMEM, "host allocation failed");
+  }
+}
+
+void validate(const rpca_problem* p) {
+  if (!p) throw Invalid("null problem");
+  if (p->m < 1 || p->n < 1) throw Invalid("m and n must be positive");
+  const int64_t mn = std::min(p->m, p->n);
+  if (p->k < 1 || p->k >= mn) throw Invalid("need 1 <= k < min(m, n)");
+  if (p->l < p->k) throw Invalid("need l >= k");
+  if (p->i < 0) throw Invalid("need i >= 0");
+  if ((int64_t)(p->i + 1) * p->l > mn) throw Invalid("need (i+1) l <= min(m, n)");
+  if (p->l > 255) throw Invalid("l > 255 is not supported");
+  if ((int64_t)(p->i + 1) * p->l > 256) throw Invalid("(i+1) l > 256 is not supported");
+  if (p->dtype < RPCA_F64 || p->dtype > RPCA_FP8E4M3) throw Invalid("unknown dtype");
+  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT)) throw Invalid("unknown flag");
+  if ((p->flags & RPCA_HOST_A) && p->n > p->m) throw Invalid("RPCA_HOST_A needs n <= m");
+}
+
+// One streamed pass over the working matrix (device-resident or tiles).
+void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
+  const size_t ab = dtype_bytes(c->prob.dtype);
+  if (!c->host_a) {
+    a.A = c->transposed ? c->At.ptr : Am->data;
+    a.lda = c->transposed ? c->n : Am->ld;
+    a.m = c->m;
+    if (!(c->simt) && launch_pass_tc(a, c->stream, c->dev_err())) return;
+    launch_pass_simt(a, c->stream);
+    return;
+  }
+  // Out-of-core form (Section 4.2): stream tiles of rows from host memory,
+  // two device buffers, copies on their own stream overlapping the kernels.
+  const int64_t tr = c->tile_rows;
+  const int64_t ntiles = cdiv(c->m, tr);
+  const size_t es = c->cbytes();
+  const size_t fcols = a.p + (a.ones_col >= 0 ? 1 : 0);
+  if (a.F && a.mode != MODE_H)
+    RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * es, 0, fcols * es, a.n, c->stream));
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const int b = (int)(t & 1);
+    const int64_t r0 = t * tr, rows = std::min(tr, c->m - r0);
+    RPCA_CUDA_TRY(cudaStreamWaitEvent(c->copy_stream, c->ev_used[b], 0));
+    const char* src = static_cast<const char*>(Am->data) + (size_t)r0 * Am->ld * ab;
+    RPCA_CUDA_TRY(cudaMemcpy2DAsync(c->tiles[b].ptr, (size_t)c->n * ab, src, (size_t)Am->ld * ab,
+                                    (size_t)c->n * ab, (size_t)rows, cudaMemcpyHostToDevice,
+                                    c->copy_stream));
+    RPCA_CUDA_TRY(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+    RPCA_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_copied[b], 0));
+    PassArgs ta = a;
+    ta.A = c->tiles[b].ptr;
+    ta.lda = c->n;
+    ta.m = rows;
+    ta.H = static_cast<char*>(a.H) + (size_t)r0 * a.ldh * es;
+    ta.accumulate_f = true;
+    if (!(c->simt) && launch_pass_tc(ta, c->stream, c->dev_err())) {
+    } else {
+      launch_pass_simt(ta, c->stream);
+    }
+    RPCA_CUDA_TRY(cudaEventRecord(c->ev_used[b], c->stream));
+  }
+}
+
+void compute_shift(rpca_ctx* c, const rpca_matrix* Am) {
+  // s = column means of the first rows (at most 128) of A, in the compute type
+  const int64_t rows = std::min<int64_t>(c->m, 128);
+  if (c->host_a) {
+    const size_t ab = dtype_bytes(c->prob.dtype);
+    RPCA_CUDA_TRY(cudaMemcpy2DAsync(c->tiles[0].ptr, (size_t)c->n * ab, Am->data, (size_t)Am->ld * ab,
+                                    (size_t)c->n * ab, (size_t)rows, cudaMemcpyHostToDevice, c->stream));
+    panel_mean(c->prob.dtype, c->tiles[0].ptr, c->n, rows, c->n, Am->col_scale, c->shift.ptr, c->stream);
+    RPCA_CUDA_TRY(cudaEventRecord(c->ev_used[0], c->stream));
+  } else {
+    const void* A = c->transposed ? c->At.ptr : Am->data;
+    const int64_t lda = c->transposed ? c->n : Am->ld;
+    panel_mean(c->prob.dtype, A, lda, rows, c->n, Am->col_scale, c->shift.ptr, c->stream);
+  }
+}
+
+void reset_x(rpca_ctx* c) {
+  // X = G in the compute type, ld = ldx
+  copy_matrix(true, c->f64, c->n, c->l, c->G64.ptr, c->l, c->X.ptr, c->ldx, c->stream);
+}
+
+rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
+  if (!Am || !Am->data) throw Invalid("null matrix");
+  if (c->next_pass > c->i + 1) throw Invalid("all passes already done");
+  const bool f64 = c->f64;
+  const size_t es = c->cbytes();
+  const int64_t ld_orig = Am->ld;
+  const int64_t ncols_orig = c->transposed ? c->m : c->n;
+  if (ld_orig < ncols_orig) throw Invalid("ld < n");
+  if (c->prob.dtype == RPCA_FP8E4M3 && !Am->col_scale) throw Invalid("FP8 needs col_scale");
+  if (c->transposed && Am->col_scale) throw Invalid("col_scale with n > m is not supported");
+  cudaStream_t st = c->stream;
+  const int j = c->next_pass;
+  if (j == 0) {
+    RPCA_CUDA_TRY(cudaMemsetAsync(c->err.ptr, 0, 64 * sizeof(uint32_t), st));
+    if (c->transposed)
+      transpose(c->prob.dtype, c->m, c->n, Am->data, Am->ld, c->At.ptr, c->n, st);
+    if (c->centered) compute_shift(c, Am);
+    reset_x(c);
+  }
+  PassArgs a;
+  a.dtype = c->prob.dtype;
+  a.n = c->n;
+  a.scale = Am->col_scale;
+  a.shift = c->centered ? c->shift.ptr : nullptr;
+  if (j <= c->i) {
+    // Step 1: pass j forms H^(j) = A_c X and (j < i) F = A_c^T H^(j)
+    a.mode = (j < c->i) ? MODE_FUSED : MODE_H;
+    a.X = c->X.ptr;
+    a.ldx = c->ldx;
+    a.p = c->l;
+    a.H = static_cast<char*>(c->H.ptr) + (size_t)j * c->l * es;
+    a.ldh = c->w;
+    a.F = c->F.ptr;
+    a.ldf = c->ldx;
+    if (c->centered && j == 0 && c->i > 0) a.ones_col = c->l;
+    if (c->centered && j == 0 && c->i == 0) a.ones_col = c->l, a.mode = MODE_FUSED;
+    if (c->centered && j > 0) {
+      // corr = d^T X: H = A~ X - 1 (d^T X)   (A_c = A~ - 1 d^T)
+      vec_mat(f64, c->n, c->l, c->d.as<double>(), c->X.ptr, c->ldx, c->vtmp.as<double>(), st);
+      cast_f64_to(f64, c->l, c->vtmp.as<double>(), c->corr.ptr, st);
+      a.corr = c->corr.ptr;
+    }
+    run_pass(c, Am, a);
+    if (c->centered && j == 0) {
+      // d = A~^T 1 / m = c - s;  H^(0) -= 1 (d^T G);  F -= m d (d^T G)
+      column_to_vec(f64, c->n, c->F.ptr, c->ldx, c->l, 1.0 / (double)c->m, c->d.as<double>(), st);
+      vec_mat(f64, c->n, c->l, c->d.as<double>(), c->X.ptr, c->ldx, c->vtmp.as<double>(), st);
+      sub_rowvec(f64, c->m, c->l, c->vtmp.as<double>(), c->H.ptr, c->w, st);
+      if (j < c->i)
+        rank1_sub(f64, c->n, c->l, (double)c->m, c->d.as<double>(), c->vtmp.as<double>(), c->F.ptr,
+                  c->ldx, st);
+    }
+    if (j < c->i) {
+      // normalised iteration: X = orth(F)
+      block_qr(f64, c->n, 1, c->l, c->F.ptr, c->ldx, nullptr, c->qs, c->dev_err(), st);
+      std::swap(c->X.ptr, c->F.ptr);
+      std::swap(c->X.bytes, c->F.bytes);
+    }
+    c->next_pass = j + 1;
+    return RPCA_MORE;
+  }
+  // Step 2: H = Q R (Q in place of H); Step 3: T = A_c^T Q
+  block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->qs, c->dev_err(), st);
+  a.mode = MODE_T;
+  a.p = c->w;
+  a.H = c->H.ptr;
+  a.ldh = c->w;
+  a.F = c->T.ptr;
+  a.ldf = c->w;
+  run_pass(c, Am, a);
+  if (c->centered) {
+    // T = A~^T Q - d (1^T Q)
+    col_sums(f64, c->m, c->w, c->H.ptr, c->w, c->q1.as<double>(), st);
+    rank1_sub(f64, c->n, c->w, 1.0, c->d.as<double>(), c->q1.as<double>(), c->T.ptr, c->w, st);
+  }
+  c->next_pass = c->i + 2;
+  return RPCA_OK;
+}
+
+rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int64_t ldv) {
+  if (c->next_pass != c->i + 2) throw Invalid("finish before all passes");
+  const bool f64 = c->f64;
+  cudaStream_t st = c->stream;
+  const size_t es = c->cbytes();
+  // Step 4: T = Q_T R_T, R_T = Ub S W^T  => V~ = Q_T Ub
+  block_qr(f64, c->n, c->i + 1, c->l, c->T.ptr, c->w, c->RT, c->qs, c->dev_err(), st);
+  jacobi_svd(f64, c->w, c->RT, c->S, c->Ub, c->W, c->svdwork, c->dev_err(), st);
+  // Steps 5-6: U = Q W[:, :k], V = Q_T Ub[:, :k]
+  // (working orientation; swapped back when the problem was transposed)
+  gemm_xm(f64, c->n, c->w, c->k, c->T.ptr, c->w, c->Ub, c->w, 1.0, 0.0, c->outV.ptr, c->k, st);
+  gemm_xm(f64, c->m, c->w, c->k, c->H.ptr, c->w, c->W, c->w, 1.0, 0.0, c->outU.ptr, c->k, st);
+  void* Uw = c->transposed ? V : U;
+  int64_t ldUw = c->transposed ? ldv : ldu;
+  void* Vw = c->transposed ? U : V;
+  int64_t ldVw = c->transposed ? ldu : ldv;
+  if (Uw) {
+    if (ldUw < c->k) throw Invalid("ldu/ldv < k");
+    RPCA_CUDA_TRY(cudaMemcpy2DAsync(Uw, ldUw * es, c->outU.ptr, c->k * es, c->k * es, c->m,
+                                    cudaMemcpyDefault, st));
+  }
+  if (Vw) {
+    if (ldVw < c->k) throw Invalid("ldu/ldv < k");
+    RPCA_CUDA_TRY(cudaMemcpy2DAsync(Vw, ldVw * es, c->outV.ptr, c->k * es, c->k * es, c->n,
+                                    cudaMemcpyDefault, st));
+  }
+  if (S) RPCA_CUDA_TRY(cudaMemcpyAsync(S, c->S, c->k * sizeof(double), cudaMemcpyDefault, st));
+  uint32_t flags = 0;
+  RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, c->err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (flags & DEV_ERR_TIMEOUT) return fail(c, RPCA_ETIMEOUT, "a device-side wait timed out");
+  if (flags & DEV_ERR_BREAKDOWN) return fail(c, RPCA_EBREAKDOWN, "Cholesky QR broke down");
+  return RPCA_OK;
+}
+
+rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
+  validate(p);
+  check_device();
+  c->prob = *p;
+  c->f64 = p->dtype == RPCA_F64;
+  c->transposed = p->n > p->m;
+  c->host_a = (p->flags & RPCA_HOST_A) != 0;
+  c->simt = (p->flags & RPCA_SIMT) != 0 || c->f64;
+  c->centered = (p->flags & RPCA_CENTER) != 0;
+  c->m = c->transposed ? p->n : p->m;
+  c->n = c->transposed ? p->m : p->n;
+  c->k = p->k;
+  c->l = p->l;
+  c->i = p->i;
+  c->w = (p->i + 1) * p->l;
+  c->ldx = c->l + 1;
+  const size_t es = c->cbytes();
+  if (p->stream) {
+    c->stream = static_cast<cudaStream_t>(p->stream);
+  } else {
+    RPCA_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  c->X.alloc((size_t)c->n * c->ldx * es);
+  c->F.alloc((size_t)c->n * c->ldx * es);
+  c->H.alloc((size_t)c->m * c->w * es);
+  c->T.alloc((size_t)c->n * c->w * es);
+  c->shift.alloc((size_t)c->n * es);
+  c->corr.alloc((size_t)256 * es);
+  c->d.alloc((size_t)c->n * sizeof(double));
+  c->vtmp.alloc(256 * sizeof(double));
+  c->q1.alloc(256 * sizeof(double));
+  c->err.alloc(64 * sizeof(uint32_t));
+  c->outU.alloc((size_t)c->m * c->k * es);
+  c->outV.alloc((size_t)c->n * c->k * es);
+  const size_t w = c->w, l = c->l;
+  const size_t small_doubles = w * l + 4 * l * l + w * w * 4 + w + 4 * w * w;
+  c->small.alloc(small_doubles * sizeof(double) + 4 * 16 * sizeof(uint32_t));
+  double* s = c->small.as<double>();
+  c->qs.C = s; s += w * l;
+  c->qs.Gm = s; s += l * l;
+  c->qs.Rk = s; s += l * l;
+  c->qs.Rinv = s; s += l * l;
+  c->qs.Racc = s; s += l * l;
+  c->RT = s; s += w * w;
+  c->Ub = s; s += w * w;
+  c->W = s; s += w * w;
+  c->S = s; s += w;
+  c->svdwork = s; s += 4 * w * w;
+  s += w * w;  // spare
+  c->qs.qf = reinterpret_cast<uint32_t*>(s);
+  RPCA_CUDA_TRY(cudaMemsetAsync(c->qs.qf, 0, 4 * 16 * sizeof(uint32_t), c->stream));
+  if (c->transposed) c->At.alloc((size_t)c->m * c->n * dtype_bytes(p->dtype));
+  if (c->host_a) {
+    const size_t ab = dtype_bytes(p->dtype);
+    int64_t tr = p->tile_rows > 0 ? p->tile_rows : std::max<int64_t>(128, (int64_t)((1ull << 30) / (c->n * ab)));
+    tr = std::min<int64_t>(tr, c->m);
+    c->tile_rows = tr;
+    for (int t = 0; t < 2; ++t) {
+      c->tiles[t].alloc((size_t)tr * c->n * ab);
+      RPCA_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_copied[t], cudaEventDisableTiming));
+      RPCA_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_used[t], cudaEventDisableTiming));
+    }
+    RPCA_CUDA_TRY(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  }
+  // G (n x l, working orientation): caller's, or the Philox stream of `seed`
+  std::vector<double> G((size_t)c->n * c->l);
+  if (p->G) std::memcpy(G.data(), p->G, G.size() * sizeof(double));
+  else gaussian_stream(p->seed, 0u, (int64_t)G.size(), G.data());
+  c->G64.alloc(G.size() * sizeof(double));
+  RPCA_CUDA_TRY(cudaMemcpy(c->G64.ptr, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
+  c->next_pass = 0;
+  return RPCA_OK;
+}
+
+}  // namespace
+
+// ================================================================== C-ABI
+extern "C" {
+
+rpca_status rpca_init(rpca_ctx** out, const rpca_problem* p) {
+  if (!out) return RPCA_EINVAL;
+  *out = nullptr;
+  rpca_ctx* c = new (std::nothrow) rpca_ctx();
+  if (!c) return RPCA_ENOMEM;
+  rpca_status s = guarded(c, [&] { return do_init(c, p); });
+  if (s != RPCA_OK) {
+    delete c;
+    return s;
+  }
+  *out = c;
+  return RPCA_OK;
+}
+
+rpca_status rpca_pass(rpca_ctx* c, const rpca_matrix* A) {
+  if (!c) return RPCA_EINVAL;
+  return guarded(c, [&] { return do_pass(c, A); });
+}
+
+rpca_status rpca_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int64_t ldv) {
+  if (!c) return RPCA_EINVAL;
+  return guarded(c, [&] {
+    if (c->next_pass != c->i + 2) return fail(c, RPCA_ESTATE, "finish before all passes");
+    return do_finish(c, U, ldu, S, V, ldv);
+  });
+}
+
+void rpca_destroy(rpca_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  delete c;
+}
+
+rpca_status rpca_rerun(rpca_ctx* c, const rpca_matrix* A, void* U, int64_t ldu, double* S, void* V,
+                       int64_t ldv) {
+  if (!c) return RPCA_EINVAL;
+  c->next_pass = 0;
+  for (;;) {
+    rpca_status s = rpca_pass(c, A);
+    if (s == RPCA_OK) break;
+    if (s != RPCA_MORE) return s;
+  }
+  return rpca_finish(c, U, ldu, S, V, ldv);
+}
+
+rpca_status rpca_run(const rpca_problem* p, const rpca_matrix* A, void* U, int64_t ldu, double* S,
+                     void* V, int64_t ldv) {
+  rpca_ctx* c = nullptr;
+  rpca_status s = rpca_init(&c, p);
+  if (s != RPCA_OK) return s;
+  s = rpca_rerun(c, A, U, ldu, S, V, ldv);
+  rpca_destroy(c);
+  return s;
+}
+
+const char* rpca_strerror(rpca_status s) {
+  switch (s) {
+    case RPCA_OK: return "ok";
+    case RPCA_MORE: return "more passes remain";
+    case RPCA_EINVAL: return "invalid argument";
+    case RPCA_ENOMEM: return "out of memory";
+    case RPCA_ECUDA: return "CUDA error";
+    case RPCA_ENODEV: return "no CUDA device";
+    case RPCA_EBREAKDOWN: return "QR breakdown";
+    case RPCA_ETIMEOUT: return "device wait timed out";
+    case RPCA_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* rpca_last_error(const rpca_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+rpca_status rpca_gaussian(uint64_t seed, uint32_t domain, int64_t count, double* out) {
+  if (count < 0 || (count > 0 && !out)) return RPCA_EINVAL;
+  gaussian_stream(seed, domain, count, out);
+  return RPCA_OK;
+}
+
+uint64_t rpca_kernel_launches(void) { return g_launches.load(); }
+
+// ------------------------------------------------------------ single ops
+rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t p, const void* A,
+                               int64_t lda, const float* col_scale, const void* shift, const void* X,
+                               int64_t ldx, void* H, int64_t ldh, void* F, int64_t ldf,
+                               int32_t kernel, void* stream) {
+  return guarded(nullptr, [&] {
+    check_device();
+    if (m < 1 || n < 1 || p < 1 || p > 255 || lda < n || ldx < p || ldh < p) throw Invalid("bad sizes");
+    if (F && ldf < p) throw Invalid("bad ldf");
+    if (!A || !X || !H) throw Invalid("null pointer");
+    PassArgs a;
+    a.dtype = dtype;
+    a.mode = F ? MODE_FUSED : MODE_H;
+    a.A = A; a.lda = lda; a.m = m; a.n = n; a.scale = col_scale; a.shift = shift;
+    a.X = X; a.ldx = ldx; a.p = p; a.H = H; a.ldh = ldh; a.F = F; a.ldf = ldf;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (kernel == 2) {
+      if (!launch_pass_tc(a, st, nullptr)) throw Invalid("tensor-core pass unsupported for this shape");
+    } else if (kernel == 1 || !launch_pass_tc(a, st, nullptr)) {
+      launch_pass_simt(a, st);
+    }
+    return RPCA_OK;
+  });
+}
+
+rpca_status rpca_op_t_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t w, const void* A, int64_t lda,
+                           const float* col_scale, const void* shift, const void* Q, int64_t ldq,
+                           void* T, int64_t ldt, int32_t kernel, void* stream) {
+  return guarded(nullptr, [&] {
+    check_device();
+    if (m < 1 || n < 1 || w < 1 || w > 256 || lda < n || ldq < w || ldt < w) throw Invalid("bad sizes");
+    if (!A || !Q || !T) throw Invalid("null pointer");
+    PassArgs a;
+    a.dtype = dtype;
+    a.mode = MODE_T;
+    a.A = A; a.lda = lda; a.m = m; a.n = n; a.scale = col_scale; a.shift = shift;
+    a.p = w; a.H = const_cast<void*>(Q); a.ldh = ldq; a.F = T; a.ldf = ldt;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (kernel == 2) {
+      if (!launch_pass_tc(a, st, nullptr)) throw Invalid("tensor-core pass unsupported for this shape");
+    } else if (kernel == 1 || !launch_pass_tc(a, st, nullptr)) {
+      launch_pass_simt(a, st);
+    }
+    return RPCA_OK;
+  });
+}
+
+rpca_status rpca_op_qr(int32_t f64, int64_t m, int32_t nblk, int32_t l, void* H, int64_t ld, void* stream) {
+  return guarded(nullptr, [&] {
+    check_device();
+    if (m < 1 || nblk < 1 || l < 1 || l > 255 || (int64_t)nblk * l > 256 || ld < (int64_t)nblk * l ||
+        (int64_t)nblk * l > m)
+      throw Invalid("bad sizes");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevBuf scratch;
+    const size_t w = (size_t)nblk * l;
+    scratch.alloc((w * l + 4 * (size_t)l * l) * sizeof(double) + 4 * nblk * sizeof(uint32_t) + 64 * sizeof(uint32_t));
+    QrScratch qs;
+    double* s = scratch.as<double>();
+    qs.C = s; s += w * l;
+    qs.Gm = s; s += (size_t)l * l;
+    qs.Rk = s; s += (size_t)l * l;
+    qs.Rinv = s; s += (size_t)l * l;
+    qs.Racc = s; s += (size_t)l * l;
+    qs.qf = reinterpret_cast<uint32_t*>(s);
+    uint32_t* err = qs.qf + 4 * nblk;
+    RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
+    block_qr(f64 != 0, m, nblk, l, H, ld, nullptr, qs, err, st);
+    uint32_t flags = 0;
+    RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags & DEV_ERR_BREAKDOWN) return RPCA_EBREAKDOWN;
+    return RPCA_OK;
+  });
+}
+
+rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w, const void* T, int64_t ldt, double* S,
+                              void* Vt, int64_t ldv, double* W, void* stream) {
+  return guarded(nullptr, [&] {
+    check_device();
+    if (n < w || w < 1 || w > 256 || ldt < w || ldv < w) throw Invalid("bad sizes");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t es = f64 ? 8 : 4;
+    // blocks: the largest divisor of w that is at most 64
+    int l = std::min(64, (int)w);
+    while (w % l) --l;
+    const int nblk = w / l;
+    DevBuf Tq, scratch;
+    Tq.alloc((size_t)n * w * es);
+    RPCA_CUDA_TRY(cudaMemcpy2DAsync(Tq.ptr, w * es, T, ldt * es, w * es, n, cudaMemcpyDeviceToDevice, st));
+    const size_t ww = (size_t)w * w;
+    scratch.alloc((w * l + 4 * (size_t)l * l + ww * 6) * sizeof(double) + (4 * nblk + 64) * sizeof(uint32_t));
+    QrScratch qs;
+    double* s = scratch.as<double>();
+    qs.C = s; s += (size_t)w * l;
+    qs.Gm = s; s += (size_t)l * l;
+    qs.Rk = s; s += (size_t)l * l;
+    qs.Rinv = s; s += (size_t)l * l;
+    qs.Racc = s; s += (size_t)l * l;
+    double* RT = s; s += ww;
+    double* Ub = s; s += ww;
+    double* work = s; s += 4 * ww;
+    qs.qf = reinterpret_cast<uint32_t*>(s);
+    uint32_t* err = qs.qf + 4 * nblk;
+    RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
+    block_qr(f64 != 0, n, nblk, l, Tq.ptr, w, RT, qs, err, st);
+    jacobi_svd(f64 != 0, w, RT, S, Ub, W, work, err, st);
+    gemm_xm(f64 != 0, n, w, w, Tq.ptr, w, Ub, w, 1.0, 0.0, Vt, ldv, st);
+    uint32_t flags = 0;
+    RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags & DEV_ERR_BREAKDOWN) return RPCA_EBREAKDOWN;
+    return RPCA_OK;
+  });
+}
+
+}  // extern "C"

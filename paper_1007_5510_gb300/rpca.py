@@ -1,0 +1,276 @@
+"""Python binding of the C-ABI in include/rpca.h (argument marshalling only).
+
+Every step of the PCA runs inside the CUDA library; this module passes
+pointers, sizes and the CUDA stream.  PyTorch provides device memory and
+streams.  If the library is missing the functions raise: there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librpca.so")
+
+OK, MORE = 0, 1
+STATUS = {0: "RPCA_OK", 1: "RPCA_MORE", -1: "RPCA_EINVAL", -2: "RPCA_ENOMEM", -3: "RPCA_ECUDA",
+          -4: "RPCA_ENODEV", -5: "RPCA_EBREAKDOWN", -6: "RPCA_ETIMEOUT", -7: "RPCA_ESTATE"}
+F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
+CENTER, HOST_A, SIMT = 0x1, 0x2, 0x4
+
+EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
+           "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
+           "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches"]
+
+
+class RpcaError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s%s" % (STATUS.get(status, status), (": " + msg) if msg else ""))
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("l", ctypes.c_int32), ("i", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("G", ctypes.POINTER(ctypes.c_double)), ("dtype", ctypes.c_int),
+                ("flags", ctypes.c_uint32), ("tile_rows", ctypes.c_int64),
+                ("stream", ctypes.c_void_p)]
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("ld", ctypes.c_int64), ("col_scale", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load librpca.so (build it with __graft_entry__.build()).  Loading does
+    not touch the GPU."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("CUDA library %s is missing: run __graft_entry__.build()" % p)
+    lib = ctypes.CDLL(p)
+    vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    st = ctypes.c_int
+    lib.rpca_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Problem)]
+    lib.rpca_init.restype = st
+    lib.rpca_pass.argtypes = [vp, ctypes.POINTER(Matrix)]
+    lib.rpca_pass.restype = st
+    lib.rpca_finish.argtypes = [vp, vp, i64, vp, vp, i64]
+    lib.rpca_finish.restype = st
+    lib.rpca_destroy.argtypes = [vp]
+    lib.rpca_destroy.restype = None
+    lib.rpca_run.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(Matrix), vp, i64, vp, vp, i64]
+    lib.rpca_run.restype = st
+    lib.rpca_rerun.argtypes = [vp, ctypes.POINTER(Matrix), vp, i64, vp, vp, i64]
+    lib.rpca_rerun.restype = st
+    lib.rpca_strerror.argtypes = [st]
+    lib.rpca_strerror.restype = ctypes.c_char_p
+    lib.rpca_last_error.argtypes = [vp]
+    lib.rpca_last_error.restype = ctypes.c_char_p
+    lib.rpca_op_fused_pass.argtypes = [st, i64, i64, i32, vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, i32, vp]
+    lib.rpca_op_fused_pass.restype = st
+    lib.rpca_op_t_pass.argtypes = [st, i64, i64, i32, vp, i64, vp, vp, vp, i64, vp, i64, i32, vp]
+    lib.rpca_op_t_pass.restype = st
+    lib.rpca_op_qr.argtypes = [i32, i64, i32, i32, vp, i64, vp]
+    lib.rpca_op_qr.restype = st
+    lib.rpca_op_small_svd.argtypes = [i32, i64, i32, vp, i64, vp, vp, i64, vp, vp]
+    lib.rpca_op_small_svd.restype = st
+    lib.rpca_gaussian.argtypes = [u64, ctypes.c_uint32, i64, ctypes.POINTER(ctypes.c_double)]
+    lib.rpca_gaussian.restype = st
+    lib.rpca_kernel_launches.argtypes = []
+    lib.rpca_kernel_launches.restype = u64
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status in (OK, MORE):
+        return status
+    msg = ""
+    if ctx:
+        msg = load_library().rpca_last_error(ctx).decode()
+    raise RpcaError(status, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    if t.dtype in (torch.uint8, getattr(torch, "float8_e4m3fn", None)):
+        return FP8E4M3
+    raise ValueError("unsupported dtype %s" % t.dtype)
+
+
+def gaussian(seed, count, domain=0):
+    """Library-side Philox/Box-Muller stream (host, no GPU needed)."""
+    out = np.empty(int(count), dtype=np.float64)
+    _check(load_library().rpca_gaussian(ctypes.c_uint64(seed), domain, int(count),
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def kernel_launches():
+    return int(load_library().rpca_kernel_launches())
+
+
+class PCA:
+    """A context: rpca_init on construction, passes, finish, rerun."""
+
+    def __init__(self, m, n, k, l, i, dtype=F32, seed=0, center=False, G=None, host_a=False,
+                 tile_rows=0, simt=False, stream=None):
+        lib = load_library()
+        self.m, self.n, self.k, self.l, self.i, self.dtype = m, n, k, l, i, dtype
+        flags = (CENTER if center else 0) | (HOST_A if host_a else 0) | (SIMT if simt else 0)
+        self._G = None
+        Gp = None
+        if G is not None:
+            self._G = np.ascontiguousarray(G, dtype=np.float64)
+            Gp = self._G.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self.stream = stream
+        sp = _stream_ptr(stream) if not host_a or stream is not None else _stream_ptr(stream)
+        self.prob = Problem(m, n, k, l, i, ctypes.c_uint64(seed), Gp, dtype, flags, tile_rows, sp)
+        self.ctx = ctypes.c_void_p()
+        _check(lib.rpca_init(ctypes.byref(self.ctx), ctypes.byref(self.prob)))
+
+    def _matrix(self, A, col_scale=None, ld=None):
+        if isinstance(A, np.ndarray):
+            data = A.ctypes.data
+            ld = A.strides[0] // A.itemsize if ld is None else ld
+        else:
+            data = A.data_ptr()
+            ld = A.stride(0) if ld is None else ld
+        return Matrix(ctypes.c_void_p(data), ld, None if col_scale is None else col_scale.data_ptr())
+
+    def passes(self, A, col_scale=None):
+        lib = load_library()
+        mat = self._matrix(A, col_scale)
+        while True:
+            s = _check(lib.rpca_pass(self.ctx, ctypes.byref(mat)), self.ctx)
+            if s == OK:
+                break
+
+    def finish(self, U=None, S=None, V=None):
+        torch = _torch()
+        cdt = torch.float64 if self.dtype == F64 else torch.float32
+        dev = torch.device("cuda")
+        if U is None:
+            U = torch.empty(self.m, self.k, dtype=cdt, device=dev)
+        if V is None:
+            V = torch.empty(self.n, self.k, dtype=cdt, device=dev)
+        if S is None:
+            S = torch.empty(self.k, dtype=torch.float64, device=dev)
+        _check(load_library().rpca_finish(self.ctx, _ptr(U), U.stride(0), _ptr(S), _ptr(V),
+                                          V.stride(0)), self.ctx)
+        return U, S, V
+
+    def run(self, A, col_scale=None, U=None, S=None, V=None):
+        """All passes + Steps 2-6 (rpca_rerun: no allocation)."""
+        torch = _torch()
+        cdt = torch.float64 if self.dtype == F64 else torch.float32
+        if U is None:
+            U = torch.empty(self.m, self.k, dtype=cdt, device="cuda")
+        if V is None:
+            V = torch.empty(self.n, self.k, dtype=cdt, device="cuda")
+        if S is None:
+            S = torch.empty(self.k, dtype=torch.float64, device="cuda")
+        mat = self._matrix(A, col_scale)
+        _check(load_library().rpca_rerun(self.ctx, ctypes.byref(mat), _ptr(U), U.stride(0),
+                                         _ptr(S), _ptr(V), V.stride(0)), self.ctx)
+        return U, S, V
+
+    def close(self):
+        if self.ctx:
+            load_library().rpca_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pca(A, k, l, i, seed=0, center=False, G=None, col_scale=None, simt=False):
+    """Rank-k PCA of a device tensor A (FP64/FP32/BF16/FP8 bytes)."""
+    m, n = A.shape
+    ctx = PCA(m, n, k, l, i, dtype_code(A), seed=seed, center=center, G=G, simt=simt)
+    try:
+        return ctx.run(A, col_scale=col_scale)
+    finally:
+        ctx.close()
+
+
+# --------------------------------------------------------------- single ops
+def fused_pass(A, X, shift=None, col_scale=None, with_f=True, kernel=0):
+    """H = A_c X (and F = A_c^T H): one Step-1 pass.  Returns (H, F)."""
+    torch = _torch()
+    m, n = A.shape
+    p = X.shape[1]
+    cdt = torch.float64 if A.dtype == torch.float64 else torch.float32
+    H = torch.empty(m, p, dtype=cdt, device=A.device)
+    F = torch.empty(n, p, dtype=cdt, device=A.device) if with_f else None
+    _check(load_library().rpca_op_fused_pass(
+        dtype_code(A), m, n, p, _ptr(A), A.stride(0), _ptr(col_scale), _ptr(shift), _ptr(X),
+        X.stride(0), _ptr(H), H.stride(0), _ptr(F), (F.stride(0) if F is not None else 0),
+        kernel, _stream_ptr()))
+    return H, F
+
+
+def t_pass(A, Q, shift=None, col_scale=None, kernel=0):
+    """T = A_c^T Q (Step 3)."""
+    torch = _torch()
+    m, n = A.shape
+    w = Q.shape[1]
+    cdt = torch.float64 if A.dtype == torch.float64 else torch.float32
+    T = torch.empty(n, w, dtype=cdt, device=A.device)
+    _check(load_library().rpca_op_t_pass(
+        dtype_code(A), m, n, w, _ptr(A), A.stride(0), _ptr(col_scale), _ptr(shift), _ptr(Q),
+        Q.stride(0), _ptr(T), T.stride(0), kernel, _stream_ptr()))
+    return T
+
+
+def qr_inplace(H, nblk, l):
+    """Step 2 on H (m x nblk*l): H <- Q."""
+    torch = _torch()
+    f64 = 1 if H.dtype == torch.float64 else 0
+    _check(load_library().rpca_op_qr(f64, H.shape[0], nblk, l, _ptr(H), H.stride(0), _stream_ptr()))
+    return H
+
+
+def small_svd(T):
+    """Step 4: T = Vt diag(S) W^T; returns (S, Vt, W)."""
+    torch = _torch()
+    n, w = T.shape
+    f64 = 1 if T.dtype == torch.float64 else 0
+    S = torch.empty(w, dtype=torch.float64, device=T.device)
+    Vt = torch.empty(n, w, dtype=T.dtype, device=T.device)
+    W = torch.empty(w, w, dtype=torch.float64, device=T.device)
+    _check(load_library().rpca_op_small_svd(f64, n, w, _ptr(T), T.stride(0), _ptr(S), _ptr(Vt),
+                                            Vt.stride(0), _ptr(W), _stream_ptr()))
+    return S, Vt, W

@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances.  FP32 workloads: relative singular-value error <= 1e-4 and
+largest principal angle <= 1e-3 rad.  FP64 workload: 1e-10 and 1e-9 rad
+(rounding of the normalised FP64 iteration is ~1e-12 relative at the
+smallest kept singular value).  Single passes: elementwise relative to the
+largest entry, 2e-5 (FP32 accumulation over <= a few thousand terms).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import rpca_oracle as ro, estimator as est  # noqa: E402
+from synth import generators as gen  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1007_5510_gb300 import rpca
+    rpca.load_library()
+
+
+def R():
+    from paper_1007_5510_gb300 import rpca
+    return rpca
+
+
+def _tt(x, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dtype)
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _stored(A, dtype):
+    """Values the library sees for storage dtype (FP64 copy for the oracle)."""
+    if dtype == "f64":
+        return _tt(A, torch.float64), A
+    if dtype == "f32":
+        return _tt(A, torch.float32), A.astype(np.float32).astype(np.float64)
+    if dtype == "bf16":
+        t = _tt(A, torch.float32).to(torch.bfloat16)
+        return t, t.float().cpu().double().numpy()
+    raise ValueError(dtype)
+
+
+# --------------------------------------------------------------- single pass
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("m,n,p", [(1000, 300, 12), (2345, 517, 22), (777, 1000, 60)])
+def test_fused_pass_matches_oracle(dtype, m, n, p):
+    rng = np.random.default_rng(m + n + p)
+    A = rng.standard_normal((m, n))
+    X = rng.standard_normal((n, p))
+    At, Ao = _stored(A, dtype)
+    cdt = torch.float64 if dtype == "f64" else torch.float32
+    H, F = R().fused_pass(At, _tt(X, cdt), kernel=1)
+    torch.cuda.synchronize()
+    Xo = X if dtype == "f64" else X.astype(np.float32).astype(np.float64)
+    Ho, Fo = ro.fused_pass_products(Ao, Xo)
+    tol = 1e-12 if dtype == "f64" else 2e-5
+    assert _rel(H.cpu().numpy(), Ho) < tol
+    assert _rel(F.cpu().numpy(), Fo) < tol * 5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_fused_pass_shift_and_scale(dtype):
+    rng = np.random.default_rng(5)
+    m, n, p = 1500, 333, 20
+    A = rng.standard_normal((m, n)) + 3.0
+    X = rng.standard_normal((n, p))
+    s = (A[:128].mean(axis=0)).astype(np.float32)
+    c = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    At, Ao = _stored(A, dtype)
+    H, F = R().fused_pass(At, _tt(X), shift=_tt(s), col_scale=_tt(c), kernel=1)
+    torch.cuda.synchronize()
+    Ho, Fo = ro.fused_pass_products(Ao, X.astype(np.float32).astype(np.float64), shift=s.astype(np.float64),
+                                    col_scale=c.astype(np.float64))
+    assert _rel(H.cpu().numpy(), Ho) < 5e-5
+    assert _rel(F.cpu().numpy(), Fo) < 2e-4
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_t_pass_matches_oracle(dtype):
+    rng = np.random.default_rng(11)
+    m, n, w = 3001, 257, 66
+    A = rng.standard_normal((m, n))
+    Q = np.linalg.qr(rng.standard_normal((m, w)))[0]
+    At, Ao = _stored(A, dtype)
+    cdt = torch.float64 if dtype == "f64" else torch.float32
+    T = R().t_pass(At, _tt(Q, cdt), kernel=1)
+    torch.cuda.synchronize()
+    Qo = Q if dtype == "f64" else Q.astype(np.float32).astype(np.float64)
+    To = ro.t_pass_product(Ao, Qo)
+    assert _rel(T.cpu().numpy(), To) < (1e-12 if dtype == "f64" else 5e-5)
+
+
+# ------------------------------------------------------------------ Step 2
+@pytest.mark.parametrize("f64", [True, False])
+def test_block_qr(f64):
+    rng = np.random.default_rng(3)
+    m, l, nblk = 5000, 20, 3
+    H = rng.standard_normal((m, nblk * l)) @ np.diag(0.9 ** np.arange(nblk * l))
+    Ht = _tt(H, torch.float64 if f64 else torch.float32)
+    R().qr_inplace(Ht, nblk, l)
+    torch.cuda.synchronize()
+    Q = Ht.cpu().double().numpy()
+    orth = np.abs(Q.T @ Q - np.eye(nblk * l)).max()
+    assert orth < (1e-13 if f64 else 2e-6)
+    Qo, _, _ = ro.pivoted_qr(H)
+    assert est.max_principal_angle(Q, Qo) < (1e-10 if f64 else 1e-4)
+
+
+# ------------------------------------------------------------------ Step 4
+@pytest.mark.parametrize("f64,w", [(True, 24), (False, 66), (False, 180)])
+def test_small_svd(f64, w):
+    rng = np.random.default_rng(w)
+    n = 700
+    sig = np.exp(-np.arange(w) / 15.0)
+    T = gen.lowrank_np(n, w, sig, seed=w)
+    Tt = _tt(T, torch.float64 if f64 else torch.float32)
+    S, Vt, W = R().small_svd(Tt)
+    torch.cuda.synchronize()
+    S = S.cpu().numpy()
+    Se = np.linalg.svd(Tt.cpu().double().numpy(), compute_uv=False)
+    assert np.max(np.abs(S - Se) / Se) < (1e-12 if f64 else 1e-5)
+    Vt = Vt.cpu().double().numpy()
+    W = W.cpu().numpy()
+    recon = (Vt * S[None, :]) @ W.T
+    assert _rel(recon, Tt.cpu().double().numpy()) < (1e-12 if f64 else 2e-5)
+
+
+# ------------------------------------------------------------- whole method
+def _compare(U, S, V, Uo, So, Vo, s_tol, a_tol):
+    S = S.cpu().numpy()
+    rel = np.max(np.abs(S - So) / So)
+    au = est.max_principal_angle(U.cpu().double().numpy(), Uo)
+    av = est.max_principal_angle(V.cpu().double().numpy(), Vo)
+    assert rel <= s_tol and au <= a_tol and av <= a_tol, (rel, au, av)
+    return rel, au, av
+
+
+def test_pca_fp64_small_workload():
+    """fp64_small at full size (2000 x 1000, k=10 l=12 i=1)."""
+    cfg = gen.CONFIGS["fp64_small"]
+    A = gen.workload_np("fp64_small")
+    U, S, V = R().pca(_tt(A, torch.float64), cfg["k"], cfg["l"], cfg["i"], seed=1007)
+    Uo, So, Vo = ro.rpca(A, cfg["k"], cfg["l"], cfg["i"], seed=1007, normalize=True)
+    _compare(U, S, V, Uo, So, Vo, 1e-10, 1e-9)
+
+
+@pytest.mark.parametrize("m,n,k,l,i", [(5000, 300, 10, 12, 2), (4099, 1031, 20, 22, 1), (1000, 64, 16, 20, 1)])
+def test_pca_fp32_matches_oracle(m, n, k, l, i):
+    A = gen.lowrank_np(m, n, np.arange(1, n + 1) ** -1.0, seed=m) + 1e-4 * np.random.default_rng(1).standard_normal((m, n))
+    A32 = A.astype(np.float32)
+    U, S, V = R().pca(_tt(A32), k, l, i, seed=99)
+    Uo, So, Vo = ro.rpca(A32.astype(np.float64), k, l, i, seed=99, normalize=True)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+
+
+def test_pca_centered_fp32_reduced():
+    """fp32_center construction at reduced size (m=20,000, n=500), centred."""
+    A = gen.workload_np("fp32_center", m=20_000, n=500).astype(np.float32)
+    U, S, V = R().pca(_tt(A), 20, 22, 2, seed=7, center=True)
+    Uo, So, Vo = ro.rpca(A.astype(np.float64), 20, 22, 2, seed=7, center=True, normalize=True)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+
+
+def test_pca_transposed():
+    """n > m: the library runs on A^T (Section 3) and swaps the factors."""
+    rng = np.random.default_rng(2)
+    A = gen.lowrank_np(300, 900, 0.9 ** np.arange(300), seed=3) + 1e-5 * rng.standard_normal((300, 900))
+    A32 = A.astype(np.float32)
+    U, S, V = R().pca(_tt(A32), 6, 8, 1, seed=5)
+    assert U.shape == (300, 6) and V.shape == (900, 6)
+    Uo, So, Vo = ro.rpca(A32.astype(np.float64), 6, 8, 1, seed=5, normalize=True)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+
+
+def test_explicit_G_equals_seed():
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((800, 120)).astype(np.float32)
+    from oracle import philox
+    G = philox.gaussian_matrix(123, 120, 9)
+    U1, S1, V1 = R().pca(_tt(A), 7, 9, 1, seed=123)
+    U2, S2, V2 = R().pca(_tt(A), 7, 9, 1, G=G)
+    assert torch.allclose(S1, S2, rtol=1e-12)
+
+
+def test_host_streamed_tiles_match_device():
+    """Out-of-core form: A in pinned host memory, tiles of 700 rows (ragged)."""
+    rng = np.random.default_rng(8)
+    m, n = 5000, 256
+    A = (gen.lowrank_np(m, n, 0.8 ** np.arange(n), seed=1) + 1e-4 * rng.standard_normal((m, n))).astype(np.float32)
+    Ah = torch.from_numpy(A).pin_memory()
+    ctx = R().PCA(m, n, 10, 12, 2, R().F32, seed=3, host_a=True, tile_rows=700)
+    try:
+        U, S, V = ctx.run(Ah)
+    finally:
+        ctx.close()
+    U2, S2, V2 = R().pca(_tt(A), 10, 12, 2, seed=3)
+    assert torch.allclose(S, S2, rtol=1e-5)
+    Uo, So, Vo = ro.rpca(A.astype(np.float64), 10, 12, 2, seed=3, normalize=True)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+
+
+def test_rerun_reuses_context():
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((1200, 200)).astype(np.float32)
+    B = (A * 2.0).astype(np.float32)
+    ctx = R().PCA(1200, 200, 5, 7, 1, R().F32, seed=1)
+    try:
+        _, S1, _ = ctx.run(_tt(A))
+        _, S2, _ = ctx.run(_tt(B))
+    finally:
+        ctx.close()
+    assert torch.allclose(S2, 2 * S1, rtol=1e-5)
