@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark: randomized block-Lanczos PCA on the 'precision' workload.
+
+Workload (one step = one whole PCA, Section 3 Steps 1-6, through the C-ABI):
+A = U0 diag(exp(-j/40)) V0^T + N(0, 1e-6) noise, m = 1,000,000, n = 4,096,
+k = 50, l = 60, i = 2, stored in BF16 (headline) and in FP32 (compared in the
+same run).  Metric: A-stream GB/s = (i+2) m n bytes_per_element / t_PCA
+(every PCA streams A i+2 times: i+1 fused passes and the T pass), plus
+seconds per PCA and the BF16-over-FP32 wall-clock ratio.  A (8.2 / 16.4 GB)
+is far larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded row sample of the same
+workload (the paper's algorithm as written, on the host cores).
+Multi-GPU: independent replicas (one PCA per rank, weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="precision", m=1_000_000, n=4096, k=50, l=60, i=2, seed=1007)
+CPU_SAMPLE_ROWS = 20_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=WORKLOAD["m"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--simt", action="store_true", help="force the CUDA-core pass kernels")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_sample(A_host_fp64, k, l, i):
+    """Time the oracle on a row sample; returns (seconds, rows, cores)."""
+    from oracle import rpca_oracle
+    t0 = time.perf_counter()
+    rpca_oracle.rpca(A_host_fp64, k, l, i, seed=WORKLOAD["seed"])
+    return time.perf_counter() - t0
+
+
+def sample_rows_fp64(A, rows):
+    return A[:rows].float().cpu().double().numpy()
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------- ours
+def main():
+    args = parse()
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    W = dict(WORKLOAD)
+    W["m"] = args.m
+    m, n, k, l, i = W["m"], W["n"], W["k"], W["l"], W["i"]
+    bytes_bf16, bytes_f32 = 2, 4
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, W)
+        return
+
+    torch.cuda.set_device(local)
+    from paper_1007_5510_gb300 import rpca
+    from synth import generators as gen
+    rpca.load_library()
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    A32 = gen.workload_torch("precision", dev, m=m, n=n, seed=W["seed"] + rank, rank_cap=1024)
+    A16 = A32.to(torch.bfloat16)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    stream = torch.cuda.current_stream()
+    ctx16 = rpca.PCA(m, n, k, l, i, rpca.BF16, seed=W["seed"], timing=True, simt=args.simt)
+    ctx32 = rpca.PCA(m, n, k, l, i, rpca.F32, seed=W["seed"], timing=True, simt=args.simt)
+    U16 = torch.empty(m, k, device=dev)
+    V16 = torch.empty(n, k, device=dev)
+    S16 = torch.empty(k, dtype=torch.float64, device=dev)
+    U32, V32, S32 = torch.empty_like(U16), torch.empty_like(V16), torch.empty_like(S16)
+
+    def timed(ctx, A, U, S, V, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            ctx.run(A, U=U, S=S, V=V)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        ctx16.run(A16, U=U16, S=S16, V=V16)
+        ctx32.run(A32, U=U32, S=S32, V=V32)
+    torch.cuda.synchronize()
+    ctx16.phase_times()
+    ctx32.phase_times()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = rpca.kernel_launches()
+    ms16 = timed(ctx16, A16, U16, S16, V16, args.steps)
+    launches = rpca.kernel_launches() - launches0
+    ms32 = timed(ctx32, A32, U32, S32, V32, args.steps)
+    clocks = sampler.stop()
+    ph16, runs16 = ctx16.phase_times()
+    ph32, runs32 = ctx32.phase_times()
+
+    t16 = ms16 / args.steps / 1e3
+    t32 = ms32 / args.steps / 1e3
+    stream_bytes16 = (i + 2) * m * n * bytes_bf16
+    stream_bytes32 = (i + 2) * m * n * bytes_f32
+    value = world * stream_bytes16 / t16 / 1e9
+    hbm, peak_kind = peaks()
+
+    # dominant kernel: the fused pass (phases 0..i-1 are fused passes)
+    def per_launch(ph, runs, idx):
+        return sum(ph[j] for j in idx) / max(1, runs * len(idx))
+    fused_idx = list(range(i)) if i > 0 else [0]
+    fused_ms16 = per_launch(ph16, runs16, fused_idx)
+    fused_ms32 = per_launch(ph32, runs32, fused_idx)
+    tpass_ms16 = per_launch(ph16, runs16, [i + 2])
+    achieved = m * n * bytes_bf16 / (fused_ms16 / 1e3) / 1e9
+    names = ["pass%d" % j for j in range(i + 1)] + ["qr", "t_pass", "svd_epilogue"]
+    phases16 = {nm: round(v / max(1, runs16), 4) for nm, v in zip(names, ph16)}
+    phases32 = {nm: round(v / max(1, runs32), 4) for nm, v in zip(names, ph32)}
+
+    # accuracy: both outputs against each other and the leading spectrum
+    s16 = S16.cpu().numpy()
+    s32 = S32.cpu().numpy()
+    acc = {"sigma_rel_bf16_vs_f32": float(abs(s16 - s32).max() / s32.max()),
+           "sigma_1": float(s32[0]), "sigma_k": float(s32[-1])}
+    try:
+        acc.update(spectral_errors(A32, [(U32, S32, V32), (U16, S16, V16)], ["f32", "bf16"]))
+    except Exception as e:  # measurement only
+        acc["spectral_error_failed"] = str(e)[:200]
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(ctx16, A16, m, n, k, i, bytes_bf16, min(args.steps, 3), dev, world, dist)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rows = min(CPU_SAMPLE_ROWS, m)
+        Ah = sample_rows_fp64(A16, rows)
+        secs = oracle_sample(Ah, k, l, i)
+        cpu = {"value": round((i + 2) * rows * n * bytes_bf16 / secs / 1e9, 4), "unit": "GB/s",
+               "cores": cores(), "kind": "oracle",
+               "sample": "first %d of %d rows of the BF16 matrix, upcast to FP64, one PCA "
+                         "(%.1f s)" % (rows, m, secs)}
+
+    if rank == 0:
+        line = {
+            "metric": "A-stream GB/s (% HBM peak) and s/PCA, BF16 vs FP32 at equal spectral error",
+            "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms16 / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic", "gpu_launches": int(launches),
+            "config": {"workload": "precision: m=%d n=%d k=%d l=%d i=%d, BF16 storage "
+                                   "(FP32 measured alongside)" % (m, n, k, l, i),
+                       "m": m, "n": n, "k": k, "l": l, "i": i, "streams_per_pca": i + 2,
+                       "l2_flush": "not needed: A (%.1f GB) >> L2" % (m * n * 2 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "kernels": "cuda-cores" if args.simt else "auto"},
+            "s_per_pca": round(t16, 6),
+            "pct_hbm_peak": round(100 * stream_bytes16 / t16 / 1e9 / hbm, 2),
+            "fp32": {"value": round(world * stream_bytes32 / t32 / 1e9, 2), "unit": "GB/s",
+                     "s_per_pca": round(t32, 6), "fused_pass_ms": round(fused_ms32, 4),
+                     "phases_ms": phases32},
+            "bf16_speedup_vs_fp32": round(t32 / t16, 3),
+            "phases_ms": phases16,
+            "roofline": {"bound": "hbm", "kernel": "fused pass (BF16, l=%d)" % l,
+                         "achieved": round(achieved, 2), "peak": hbm, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                         "algorithmic_bytes_per_launch": m * n * bytes_bf16,
+                         "avg_launch_ms": round(fused_ms16, 4),
+                         "t_pass_ms": round(tpass_ms16, 4)},
+            "accuracy": acc,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gen_s": round(gen_s, 2),
+        }
+        print(json.dumps(line))
+    ctx16.close()
+    ctx32.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def spectral_errors(A, outs, labels, iters=30, nvec=4):
+    """||A - U S V^T||_2 by block power iteration on the residual (torch,
+    measurement only), same start vectors for every output."""
+    import torch
+    g = torch.Generator(device=A.device)
+    res = {}
+    for (U, S, V), lab in zip(outs, labels):
+        g.manual_seed(5)
+        x = torch.randn(A.shape[1], nvec, generator=g, device=A.device)
+        Sf = S.float()
+        est = 0.0
+        for _ in range(iters):
+            y = A @ x - U @ (Sf[:, None] * (V.T @ x))
+            z = A.T @ y - V @ (Sf[:, None] * (U.T @ y))
+            nz = torch.linalg.norm(z, dim=0)
+            est = float(torch.sqrt(nz.max() / torch.linalg.norm(x, dim=0)[nz.argmax()]))
+            x = torch.linalg.qr(z)[0]
+        res["spectral_error_" + lab] = est
+    if len(labels) == 2:
+        res["spectral_error_ratio_bf16_over_f32"] = res["spectral_error_bf16"] / res["spectral_error_f32"]
+    return res
+
+
+def end_to_end(ctx, A_dev, m, n, k, i, b, steps, dev, world, dist):
+    """Same metric through the public API with host buffers: pinned host A
+    copied in, PCA, U S V copied out, every step."""
+    import torch
+    Ah = A_dev.cpu().pin_memory()
+    Ad = torch.empty_like(A_dev)
+    Uh = torch.empty(m, k).pin_memory()
+    Vh = torch.empty(n, k).pin_memory()
+    Sh = torch.empty(k, dtype=torch.float64).pin_memory()
+    U = torch.empty(m, k, device=dev)
+    V = torch.empty(n, k, device=dev)
+    S = torch.empty(k, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Ad.copy_(Ah, non_blocking=True)
+    ctx.run(Ad, U=U, S=S, V=V)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0.record(st)
+    for _ in range(steps):
+        Ad.copy_(Ah, non_blocking=True)
+        ctx.run(Ad, U=U, S=S, V=V)
+        Uh.copy_(U, non_blocking=True)
+        Vh.copy_(V, non_blocking=True)
+        Sh.copy_(S, non_blocking=True)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    t = ms / steps / 1e3
+    return {"value": round(world * (i + 2) * m * n * b / t / 1e9, 2), "unit": "GB/s",
+            "s_per_pca": round(t, 6), "h2d_bytes_per_step": m * n * b,
+            "d2h_bytes_per_step": (m + n) * k * 4 + k * 8}
+
+
+def run_reference(args, W):
+    """The oracle arm: FP64 CPU oracle on a bounded row sample per step."""
+    import numpy as np
+    from synth import generators as gen
+    m, n, k, l, i = W["m"], W["n"], W["k"], W["l"], W["i"]
+    rows = min(CPU_SAMPLE_ROWS, m)
+    A = gen.workload_np("precision", m=rows, n=n, seed=W["seed"], rank_cap=1024)
+    A = gen.round_bf16_np(A).astype(np.float64)
+    for _ in range(args.warmup):
+        oracle_sample(A, k, l, i)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(A, k, l, i)
+    secs = (time.perf_counter() - t0) / args.steps
+    val = (i + 2) * rows * n * 2 / secs / 1e9
+    sample = ("%d-row sample of the precision workload (n=%d, BF16 values in FP64), one PCA "
+              "per step" % (rows, n))
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "A-stream GB/s (% HBM peak) and s/PCA, BF16 vs FP32 at equal spectral error",
+        "value": round(val, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(secs * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "precision: m=%d n=%d k=%d l=%d i=%d, BF16 storage" % (m, n, k, l, i),
+                   "sample_rows": rows},
+        "cpu_baseline": {"value": round(val, 4), "unit": "GB/s", "cores": cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

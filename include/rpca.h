@@ -73,6 +73,7 @@ typedef enum {
                                  of tile_rows rows, double-buffered (the
                                  out-of-core form of Section 4.2) */
 #define RPCA_SIMT       0x4u  /* force the CUDA-core pass kernels (testing) */
+#define RPCA_TIMING     0x8u  /* record per-phase CUDA-event times */
 
 typedef struct {
   int64_t m, n;           /* A is m x n; 1 <= k < min(m, n) */
@@ -80,8 +81,9 @@ typedef struct {
                              (i+1) l <= min(m, n) (Sections 2-3) */
   uint64_t seed;          /* G drawn from Philox4x32-10, key = seed, domain 0,
                              Box-Muller, row-major, when G == NULL */
-  const double* G;        /* optional host FP64 test matrix, row-major
-                             min... rows: n x l when n <= m, else m x l */
+  const double* G;        /* optional host FP64 test matrix, row-major:
+                             n x l when n <= m, else m x l (the method
+                             runs on A^T when n > m, Section 3) */
   rpca_dtype dtype;       /* storage type of A */
   uint32_t flags;         /* RPCA_* flags above */
   int64_t tile_rows;      /* RPCA_HOST_A: rows per streamed tile (0: 1 GiB) */
@@ -178,6 +180,14 @@ rpca_status rpca_gaussian(uint64_t seed, uint32_t domain, int64_t count,
 
 /* Number of the library's own kernels launched since load (all devices). */
 uint64_t rpca_kernel_launches(void);
+
+/* Per-phase device times of a context created with RPCA_TIMING, summed
+ * over the runs finished since the previous call (then reset).  Phases:
+ * 0..i the streaming kernels of the Step-1 passes, i+1 the QR of H (Step 2),
+ * i+2 the T pass (Step 3), i+3 Steps 4-6.  Writes min(cap, i+4) values (ms)
+ * to ms (host), the run count to *runs (may be NULL); returns i+4, or 0
+ * without RPCA_TIMING. */
+int32_t rpca_phase_times(rpca_ctx* c, double* ms, int32_t cap, int32_t* runs);
 
 #ifdef __cplusplus
 }

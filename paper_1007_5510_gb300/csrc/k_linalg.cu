@@ -253,6 +253,11 @@ __global__ void k_left_mul(int p, const double* __restrict__ Rk, double* __restr
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) Racc[e] = tmp[e];
 }
 
+__global__ void k_sub_identity(int p, double* __restrict__ M) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < p) M[e * p + e] -= 1.0;
+}
+
 __global__ void k_set_identity(int p, double* __restrict__ M) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < p * p) M[e] = (e / p == e % p) ? 1.0 : 0.0;
@@ -569,6 +574,12 @@ void chol_small(int p, const double* G, int64_t ldg, double* R, double* Rinv, in
 
 void left_mul(int p, const double* Rk, double* Racc, cudaStream_t st) {
   k_left_mul<<<1, 256, (size_t)p * p * sizeof(double), st>>>(p, Rk, Racc);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void sub_identity(int p, double* M, cudaStream_t st) {
+  k_sub_identity<<<grid1(p), 256, 0, st>>>(p, M);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
 }

@@ -43,13 +43,13 @@ __device__ __forceinline__ TC load_a(const TA* __restrict__ A, int64_t lda, int6
 }
 
 // grid: (panel blocks, column groups).  Persistent over panels.
-template <typename TA, typename TC, int MODE>
+template <typename TA, typename TC, int MODE, typename TF>
 __global__ void __launch_bounds__(THREADS)
 k_pass_simt(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
             const float* __restrict__ scale, const TC* __restrict__ shift,
             const TC* __restrict__ X, int64_t ldx, int p,
             TC* __restrict__ H, int64_t ldh, const TC* __restrict__ corr, int ones_col,
-            TC* __restrict__ F, int64_t ldf) {
+            TF* __restrict__ F, int64_t ldf) {
   constexpr int BM = SimtCfg<TC>::BM;
   constexpr int KC = 32;                 // phase-1 K chunk
   constexpr int JC = 64;                 // phase-2 n chunk
@@ -155,7 +155,7 @@ k_pass_simt(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int cc = tx * 4 + b;
-          if (cc < fc) atomicAdd(&F[j * ldf + c0 + cc], acc[a][b]);
+          if (cc < fc) atomicAdd(&F[j * ldf + c0 + cc], (TF)acc[a][b]);
         }
       }
       __syncthreads();
@@ -163,12 +163,12 @@ k_pass_simt(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
   }
 }
 
-template <typename TA, typename TC, int MODE>
+template <typename TA, typename TC, int MODE, typename TF>
 void launch_one(const PassArgs& a, cudaStream_t st) {
   constexpr int BM = SimtCfg<TC>::BM;
   const int groups = (int)cdiv(a.p + (a.ones_col >= 0 ? 1 : 0), PW);
   size_t smem = sizeof(TC) * (size_t)(BM * (PW + 1) + BM * (64 + 1) + 32 * PW);
-  auto kern = k_pass_simt<TA, TC, MODE>;
+  auto kern = k_pass_simt<TA, TC, MODE, TF>;
   static bool attr_done = false;
   if (!attr_done) {
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -181,7 +181,7 @@ void launch_one(const PassArgs& a, cudaStream_t st) {
   kern<<<grid, THREADS, smem, st>>>(
       static_cast<const TA*>(a.A), a.lda, a.m, a.n, a.scale, static_cast<const TC*>(a.shift),
       static_cast<const TC*>(a.X), a.ldx, a.p, static_cast<TC*>(a.H), a.ldh,
-      static_cast<const TC*>(a.corr), a.ones_col, static_cast<TC*>(a.F), a.ldf);
+      static_cast<const TC*>(a.corr), a.ones_col, static_cast<TF*>(a.F), a.ldf);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
 }
@@ -189,9 +189,12 @@ void launch_one(const PassArgs& a, cudaStream_t st) {
 template <typename TA, typename TC>
 void launch_mode(const PassArgs& a, cudaStream_t st) {
   switch (a.mode) {
-    case MODE_FUSED: launch_one<TA, TC, MODE_FUSED>(a, st); break;
-    case MODE_H: launch_one<TA, TC, MODE_H>(a, st); break;
-    case MODE_T: launch_one<TA, TC, MODE_T>(a, st); break;
+    case MODE_FUSED: launch_one<TA, TC, MODE_FUSED, TC>(a, st); break;
+    case MODE_H: launch_one<TA, TC, MODE_H, TC>(a, st); break;
+    case MODE_T:
+      if (a.f_f64) launch_one<TA, TC, MODE_T, double>(a, st);
+      else launch_one<TA, TC, MODE_T, TC>(a, st);
+      break;
   }
 }
 
@@ -200,7 +203,7 @@ void launch_mode(const PassArgs& a, cudaStream_t st) {
 void launch_pass_simt(const PassArgs& a, cudaStream_t st) {
   if (a.F && a.mode != MODE_H && !a.accumulate_f) {
     const int fcols = a.p + (a.ones_col >= 0 ? 1 : 0);
-    const size_t es = a.dtype == RPCA_F64 ? 8 : 4;
+    const size_t es = (a.dtype == RPCA_F64 || a.f_f64) ? 8 : 4;
     RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, (size_t)a.ldf * es, 0, (size_t)fcols * es, (size_t)a.n, st));
   }
   switch (a.dtype) {

@@ -24,6 +24,7 @@ struct PassArgs {
   void* F = nullptr;             // n x (p [+1]) accumulator (zeroed by the launcher)
   int64_t ldf = 0;
   bool accumulate_f = false;     // true: add into F (caller zeroed it)
+  bool f_f64 = false;            // MODE_T: F is an FP64 accumulator
 };
 
 void launch_pass_simt(const PassArgs& a, cudaStream_t st);
@@ -52,6 +53,8 @@ void chol_small(int p, const double* G, int64_t ldg, double* R, double* Rinv, in
                 double piv_rel, double shift_rel, uint32_t* qf, uint32_t* dev_err, cudaStream_t st);
 // Racc = Rk * Racc (p x p FP64)
 void left_mul(int p, const double* Rk, double* Racc, cudaStream_t st);
+// M -= I (p x p FP64, ld p)
+void sub_identity(int p, double* M, cudaStream_t st);
 // M = I (p x p FP64)
 void set_identity(int p, double* M, cudaStream_t st);
 // dst += src (rows x cols FP64)

@@ -105,8 +105,11 @@ struct QrScratch {
   uint32_t* qf = nullptr;  // 4 words per block
 };
 
+// E_out (w x w FP64, optional): Q^T Q - I of the stored Q, measured with an
+// FP64-accumulated Gram, so that consumers can apply the first-order
+// orthonormalisation Q (I - E/2) in FP64 without rewriting Q.
 static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, double* R_out,
-                     const QrScratch& s, uint32_t* dev_err, cudaStream_t st) {
+                     double* E_out, const QrScratch& s, uint32_t* dev_err, cudaStream_t st) {
   const size_t es = f64 ? 8 : 4;
   const int w = nblk * l;
   const double piv_rel = f64 ? 1e-12 : 1e-5;
@@ -133,6 +136,10 @@ static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, 
     }
     if (R_out) mat_add(l, l, s.Racc, l, R_out + (size_t)jl * w + jl, w, st);
   }
+  if (E_out) {
+    gram(f64, m, w, w, H, ld, H, ld, E_out, w, false, st);
+    sub_identity(w, E_out, st);
+  }
 }
 
 }  // namespace rpca
@@ -157,9 +164,25 @@ struct rpca_ctx {
   int64_t tile_rows = 0;
   QrScratch qs;
   double *RT = nullptr, *S = nullptr, *Ub = nullptr, *W = nullptr, *svdwork = nullptr;
+  double *E = nullptr, *ET = nullptr, *RT2 = nullptr, *MU = nullptr, *MV = nullptr;
+  DevBuf T64;
   DevBuf outU, outV;
+  // per-phase CUDA-event timing (RPCA_TIMING): phases 0..i are the fused
+  // passes' streaming kernels, i+1 the QR of H, i+2 the T pass, i+3 Steps 4-6
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<double> phase_ms;
+  int timed_runs = 0;
+
+  void tic(int ph) {
+    if (timing) RPCA_CUDA_TRY(cudaEventRecord(ev[2 * ph], stream));
+  }
+  void toc(int ph) {
+    if (timing) RPCA_CUDA_TRY(cudaEventRecord(ev[2 * ph + 1], stream));
+  }
 
   ~rpca_ctx() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (int t = 0; t < 2; ++t) {
       if (ev_copied[t]) cudaEventDestroy(ev_copied[t]);
       if (ev_used[t]) cudaEventDestroy(ev_used[t]);
@@ -205,7 +228,7 @@ void validate(const rpca_problem* p) {
   if (p->l > 255) throw Invalid("l > 255 is not supported");
   if ((int64_t)(p->i + 1) * p->l > 256) throw Invalid("(i+1) l > 256 is not supported");
   if (p->dtype < RPCA_F64 || p->dtype > RPCA_FP8E4M3) throw Invalid("unknown dtype");
-  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT)) throw Invalid("unknown flag");
+  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT | RPCA_TIMING)) throw Invalid("unknown flag");
   if ((p->flags & RPCA_HOST_A) && p->n > p->m) throw Invalid("RPCA_HOST_A needs n <= m");
 }
 
@@ -226,8 +249,9 @@ void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
   const int64_t ntiles = cdiv(c->m, tr);
   const size_t es = c->cbytes();
   const size_t fcols = a.p + (a.ones_col >= 0 ? 1 : 0);
+  const size_t fes = a.f_f64 ? 8 : es;
   if (a.F && a.mode != MODE_H)
-    RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * es, 0, fcols * es, a.n, c->stream));
+    RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * fes, 0, fcols * fes, a.n, c->stream));
   for (int64_t t = 0; t < ntiles; ++t) {
     const int b = (int)(t & 1);
     const int64_t r0 = t * tr, rows = std::min(tr, c->m - r0);
@@ -315,7 +339,9 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
       cast_f64_to(f64, c->l, c->vtmp.as<double>(), c->corr.ptr, st);
       a.corr = c->corr.ptr;
     }
+    c->tic(j);
     run_pass(c, Am, a);
+    c->toc(j);
     if (c->centered && j == 0) {
       // d = A~^T 1 / m = c - s;  H^(0) -= 1 (d^T G);  F -= m d (d^T G)
       column_to_vec(f64, c->n, c->F.ptr, c->ldx, c->l, 1.0 / (double)c->m, c->d.as<double>(), st);
@@ -327,7 +353,7 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
     }
     if (j < c->i) {
       // normalised iteration: X = orth(F)
-      block_qr(f64, c->n, 1, c->l, c->F.ptr, c->ldx, nullptr, c->qs, c->dev_err(), st);
+      block_qr(f64, c->n, 1, c->l, c->F.ptr, c->ldx, nullptr, nullptr, c->qs, c->dev_err(), st);
       std::swap(c->X.ptr, c->F.ptr);
       std::swap(c->X.bytes, c->F.bytes);
     }
@@ -335,19 +361,27 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
     return RPCA_MORE;
   }
   // Step 2: H = Q R (Q in place of H); Step 3: T = A_c^T Q
-  block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->qs, c->dev_err(), st);
+  c->tic(c->i + 1);
+  block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->E, c->qs, c->dev_err(), st);
+  c->toc(c->i + 1);
   a.mode = MODE_T;
   a.p = c->w;
   a.H = c->H.ptr;
   a.ldh = c->w;
-  a.F = c->T.ptr;
+  a.F = c->T64.ptr;   // FP64 accumulation across row blocks
   a.ldf = c->w;
+  a.f_f64 = true;
+  c->tic(c->i + 2);
   run_pass(c, Am, a);
+  c->toc(c->i + 2);
+  copy_matrix(true, f64, c->n, c->w, c->T64.ptr, c->w, c->T.ptr, c->w, st);
   if (c->centered) {
     // T = A~^T Q - d (1^T Q)
     col_sums(f64, c->m, c->w, c->H.ptr, c->w, c->q1.as<double>(), st);
     rank1_sub(f64, c->n, c->w, 1.0, c->d.as<double>(), c->q1.as<double>(), c->T.ptr, c->w, st);
   }
+  // T <- T (I - E/2): the Rayleigh-Ritz matrix of the orthonormalised basis
+  gemm_xm(f64, c->n, c->w, c->w, c->T.ptr, c->w, c->E, c->w, -0.5, 1.0, c->T.ptr, c->w, st);
   c->next_pass = c->i + 2;
   return RPCA_OK;
 }
@@ -357,13 +391,23 @@ rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int
   const bool f64 = c->f64;
   cudaStream_t st = c->stream;
   const size_t es = c->cbytes();
-  // Step 4: T = Q_T R_T, R_T = Ub S W^T  => V~ = Q_T Ub
-  block_qr(f64, c->n, c->i + 1, c->l, c->T.ptr, c->w, c->RT, c->qs, c->dev_err(), st);
-  jacobi_svd(f64, c->w, c->RT, c->S, c->Ub, c->W, c->svdwork, c->dev_err(), st);
-  // Steps 5-6: U = Q W[:, :k], V = Q_T Ub[:, :k]
+  // Step 4: T = Q_T R_T; with E_T = Q_T^T Q_T - I, T = (Q_T (I - E_T/2))
+  // ((I + E_T/2) R_T) to first order; R_T' = Ub S W^T  =>  V~ = Q_T (I - E_T/2) Ub
+  const int w = c->w, k = c->k;
+  c->tic(c->i + 3);
+  block_qr(f64, c->n, c->i + 1, c->l, c->T.ptr, c->w, c->RT, c->ET, c->qs, c->dev_err(), st);
+  copy_matrix(true, true, w, w, c->RT, w, c->RT2, w, st);
+  gemm_xm(true, w, w, w, c->ET, w, c->RT, w, 0.5, 1.0, c->RT2, w, st);
+  jacobi_svd(f64, w, c->RT2, c->S, c->Ub, c->W, c->svdwork, c->dev_err(), st);
+  // Steps 5-6: U = Q (I - E/2) W[:, :k], V = Q_T (I - E_T/2) Ub[:, :k]
   // (working orientation; swapped back when the problem was transposed)
-  gemm_xm(f64, c->n, c->w, c->k, c->T.ptr, c->w, c->Ub, c->w, 1.0, 0.0, c->outV.ptr, c->k, st);
-  gemm_xm(f64, c->m, c->w, c->k, c->H.ptr, c->w, c->W, c->w, 1.0, 0.0, c->outU.ptr, c->k, st);
+  copy_matrix(true, true, w, k, c->Ub, w, c->MV, k, st);
+  gemm_xm(true, w, w, k, c->ET, w, c->Ub, w, -0.5, 1.0, c->MV, k, st);
+  copy_matrix(true, true, w, k, c->W, w, c->MU, k, st);
+  gemm_xm(true, w, w, k, c->E, w, c->W, w, -0.5, 1.0, c->MU, k, st);
+  gemm_xm(f64, c->n, w, k, c->T.ptr, w, c->MV, k, 1.0, 0.0, c->outV.ptr, k, st);
+  gemm_xm(f64, c->m, w, k, c->H.ptr, w, c->MU, k, 1.0, 0.0, c->outU.ptr, k, st);
+  c->toc(c->i + 3);
   void* Uw = c->transposed ? V : U;
   int64_t ldUw = c->transposed ? ldv : ldu;
   void* Vw = c->transposed ? U : V;
@@ -382,6 +426,14 @@ rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int
   uint32_t flags = 0;
   RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, c->err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (c->timing) {
+    for (size_t ph = 0; ph < c->phase_ms.size(); ++ph) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev[2 * ph], c->ev[2 * ph + 1]) == cudaSuccess) c->phase_ms[ph] += ms;
+      else cudaGetLastError();
+    }
+    c->timed_runs += 1;
+  }
   if (flags & DEV_ERR_TIMEOUT) return fail(c, RPCA_ETIMEOUT, "a device-side wait timed out");
   if (flags & DEV_ERR_BREAKDOWN) return fail(c, RPCA_EBREAKDOWN, "Cholesky QR broke down");
   return RPCA_OK;
@@ -414,6 +466,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->F.alloc((size_t)c->n * c->ldx * es);
   c->H.alloc((size_t)c->m * c->w * es);
   c->T.alloc((size_t)c->n * c->w * es);
+  c->T64.alloc((size_t)c->n * c->w * sizeof(double));
   c->shift.alloc((size_t)c->n * es);
   c->corr.alloc((size_t)256 * es);
   c->d.alloc((size_t)c->n * sizeof(double));
@@ -423,7 +476,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->outU.alloc((size_t)c->m * c->k * es);
   c->outV.alloc((size_t)c->n * c->k * es);
   const size_t w = c->w, l = c->l;
-  const size_t small_doubles = w * l + 4 * l * l + w * w * 4 + w + 4 * w * w;
+  const size_t small_doubles = w * l + 4 * l * l + w * w * 4 + w + 4 * w * w + 3 * w * w + 2 * w * c->k;
   c->small.alloc(small_doubles * sizeof(double) + 4 * 16 * sizeof(uint32_t));
   double* s = c->small.as<double>();
   c->qs.C = s; s += w * l;
@@ -437,6 +490,11 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->S = s; s += w;
   c->svdwork = s; s += 4 * w * w;
   s += w * w;  // spare
+  c->E = s; s += w * w;
+  c->ET = s; s += w * w;
+  c->RT2 = s; s += w * w;
+  c->MU = s; s += w * c->k;
+  c->MV = s; s += w * c->k;
   c->qs.qf = reinterpret_cast<uint32_t*>(s);
   RPCA_CUDA_TRY(cudaMemsetAsync(c->qs.qf, 0, 4 * 16 * sizeof(uint32_t), c->stream));
   if (c->transposed) c->At.alloc((size_t)c->m * c->n * dtype_bytes(p->dtype));
@@ -458,6 +516,13 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   else gaussian_stream(p->seed, 0u, (int64_t)G.size(), G.data());
   c->G64.alloc(G.size() * sizeof(double));
   RPCA_CUDA_TRY(cudaMemcpy(c->G64.ptr, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
+  c->timing = (p->flags & RPCA_TIMING) != 0;
+  if (c->timing) {
+    const int nph = c->i + 4;
+    c->ev.assign(2 * nph, nullptr);
+    for (auto& e : c->ev) RPCA_CUDA_TRY(cudaEventCreate(&e));
+    c->phase_ms.assign(nph, 0.0);
+  }
   c->next_pass = 0;
   return RPCA_OK;
 }
@@ -547,6 +612,16 @@ rpca_status rpca_gaussian(uint64_t seed, uint32_t domain, int64_t count, double*
 
 uint64_t rpca_kernel_launches(void) { return g_launches.load(); }
 
+int32_t rpca_phase_times(rpca_ctx* c, double* ms, int32_t cap, int32_t* runs) {
+  if (!c || !c->timing) return 0;
+  const int n = (int)c->phase_ms.size();
+  for (int t = 0; t < n && t < cap; ++t) ms[t] = c->phase_ms[t];
+  if (runs) *runs = c->timed_runs;
+  for (auto& v : c->phase_ms) v = 0.0;
+  c->timed_runs = 0;
+  return n;
+}
+
 // ------------------------------------------------------------ single ops
 rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t p, const void* A,
                                int64_t lda, const float* col_scale, const void* shift, const void* X,
@@ -614,7 +689,7 @@ rpca_status rpca_op_qr(int32_t f64, int64_t m, int32_t nblk, int32_t l, void* H,
     qs.qf = reinterpret_cast<uint32_t*>(s);
     uint32_t* err = qs.qf + 4 * nblk;
     RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
-    block_qr(f64 != 0, m, nblk, l, H, ld, nullptr, qs, err, st);
+    block_qr(f64 != 0, m, nblk, l, H, ld, nullptr, nullptr, qs, err, st);
     uint32_t flags = 0;
     RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     RPCA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -638,7 +713,7 @@ rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w, const void* T, 
     Tq.alloc((size_t)n * w * es);
     RPCA_CUDA_TRY(cudaMemcpy2DAsync(Tq.ptr, w * es, T, ldt * es, w * es, n, cudaMemcpyDeviceToDevice, st));
     const size_t ww = (size_t)w * w;
-    scratch.alloc((w * l + 4 * (size_t)l * l + ww * 6) * sizeof(double) + (4 * nblk + 64) * sizeof(uint32_t));
+    scratch.alloc((w * l + 4 * (size_t)l * l + ww * 10) * sizeof(double) + (4 * nblk + 64) * sizeof(uint32_t));
     QrScratch qs;
     double* s = scratch.as<double>();
     qs.C = s; s += (size_t)w * l;
@@ -647,14 +722,21 @@ rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w, const void* T, 
     qs.Rinv = s; s += (size_t)l * l;
     qs.Racc = s; s += (size_t)l * l;
     double* RT = s; s += ww;
+    double* RT2 = s; s += ww;
+    double* ET = s; s += ww;
     double* Ub = s; s += ww;
+    double* MV = s; s += ww;
     double* work = s; s += 4 * ww;
     qs.qf = reinterpret_cast<uint32_t*>(s);
     uint32_t* err = qs.qf + 4 * nblk;
     RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
-    block_qr(f64 != 0, n, nblk, l, Tq.ptr, w, RT, qs, err, st);
-    jacobi_svd(f64 != 0, w, RT, S, Ub, W, work, err, st);
-    gemm_xm(f64 != 0, n, w, w, Tq.ptr, w, Ub, w, 1.0, 0.0, Vt, ldv, st);
+    block_qr(f64 != 0, n, nblk, l, Tq.ptr, w, RT, ET, qs, err, st);
+    copy_matrix(true, true, w, w, RT, w, RT2, w, st);
+    gemm_xm(true, w, w, w, ET, w, RT, w, 0.5, 1.0, RT2, w, st);
+    jacobi_svd(f64 != 0, w, RT2, S, Ub, W, work, err, st);
+    copy_matrix(true, true, w, w, Ub, w, MV, w, st);
+    gemm_xm(true, w, w, w, ET, w, Ub, w, -0.5, 1.0, MV, w, st);
+    gemm_xm(f64 != 0, n, w, w, Tq.ptr, w, MV, w, 1.0, 0.0, Vt, ldv, st);
     uint32_t flags = 0;
     RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     RPCA_CUDA_TRY(cudaStreamSynchronize(st));

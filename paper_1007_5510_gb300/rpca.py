@@ -17,11 +17,12 @@ OK, MORE = 0, 1
 STATUS = {0: "RPCA_OK", 1: "RPCA_MORE", -1: "RPCA_EINVAL", -2: "RPCA_ENOMEM", -3: "RPCA_ECUDA",
           -4: "RPCA_ENODEV", -5: "RPCA_EBREAKDOWN", -6: "RPCA_ETIMEOUT", -7: "RPCA_ESTATE"}
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
-CENTER, HOST_A, SIMT = 0x1, 0x2, 0x4
+CENTER, HOST_A, SIMT, TIMING = 0x1, 0x2, 0x4, 0x8
 
 EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
            "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
-           "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches"]
+           "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
+           "rpca_phase_times"]
 
 
 class RpcaError(RuntimeError):
@@ -85,6 +86,8 @@ def load_library(path=None):
     lib.rpca_gaussian.restype = st
     lib.rpca_kernel_launches.argtypes = []
     lib.rpca_kernel_launches.restype = u64
+    lib.rpca_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(i32)]
+    lib.rpca_phase_times.restype = i32
     if path is None:
         _lib = lib
     return lib
@@ -143,17 +146,18 @@ class PCA:
     """A context: rpca_init on construction, passes, finish, rerun."""
 
     def __init__(self, m, n, k, l, i, dtype=F32, seed=0, center=False, G=None, host_a=False,
-                 tile_rows=0, simt=False, stream=None):
+                 tile_rows=0, simt=False, stream=None, timing=False):
         lib = load_library()
         self.m, self.n, self.k, self.l, self.i, self.dtype = m, n, k, l, i, dtype
-        flags = (CENTER if center else 0) | (HOST_A if host_a else 0) | (SIMT if simt else 0)
+        flags = ((CENTER if center else 0) | (HOST_A if host_a else 0) | (SIMT if simt else 0)
+                 | (TIMING if timing else 0))
         self._G = None
         Gp = None
         if G is not None:
             self._G = np.ascontiguousarray(G, dtype=np.float64)
             Gp = self._G.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.stream = stream
-        sp = _stream_ptr(stream) if not host_a or stream is not None else _stream_ptr(stream)
+        sp = _stream_ptr(stream)
         self.prob = Problem(m, n, k, l, i, ctypes.c_uint64(seed), Gp, dtype, flags, tile_rows, sp)
         self.ctx = ctypes.c_void_p()
         _check(lib.rpca_init(ctypes.byref(self.ctx), ctypes.byref(self.prob)))
@@ -203,6 +207,13 @@ class PCA:
         _check(load_library().rpca_rerun(self.ctx, ctypes.byref(mat), _ptr(U), U.stride(0),
                                          _ptr(S), _ptr(V), V.stride(0)), self.ctx)
         return U, S, V
+
+    def phase_times(self):
+        """(list of per-phase ms summed over runs, run count) since last call."""
+        buf = (ctypes.c_double * 64)()
+        runs = ctypes.c_int32(0)
+        n = load_library().rpca_phase_times(self.ctx, buf, 64, ctypes.byref(runs))
+        return [buf[t] for t in range(n)], runs.value
 
     def close(self):
         if self.ctx:

@@ -111,47 +111,49 @@ def _torch():
 
 
 def lowrank_torch(m, n, sigma, seed, device, dtype=None, offset_std=0.0,
-                  noise_std=0.0, chunk_rows=1 << 18):
-    """Same construction as lowrank_np, generated with torch on ``device``
-    (Q factors via torch.linalg.qr in FP64 for the n-side and FP32 for the
-    tall side).  Returns an FP32 tensor unless ``dtype`` says otherwise.
-    Different random stream from lowrank_np: use one or the other."""
+                  noise_std=0.0, chunk_rows=1 << 17):
+    """Same construction as lowrank_np, generated with torch on ``device``:
+    the tall Q factor by Cholesky QR twice (FP64 Gram), the n-side one by
+    torch.linalg.qr, the product in FP32 row chunks.  Returns ``dtype``
+    (FP32 default).  Different random stream from lowrank_np."""
     torch = _torch()
     dtype = torch.float32 if dtype is None else dtype
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     r = len(sigma)
     sig = torch.as_tensor(np.asarray(sigma), dtype=torch.float64, device=device)
-    Zu = torch.randn(m, r, generator=g, device=device, dtype=torch.float32)
+    U0 = torch.randn(m, r, generator=g, device=device, dtype=torch.float32)
     Zv = torch.randn(n, r, generator=g, device=device, dtype=torch.float64)
-    # tall Q factor by Cholesky QR in FP64 (twice) -- plain input construction
-    U0 = Zu
     for _ in range(2):
         Gm = torch.zeros(r, r, dtype=torch.float64, device=device)
         for r0 in range(0, m, chunk_rows):
             blk = U0[r0:r0 + chunk_rows].double()
             Gm += blk.T @ blk
         L = torch.linalg.cholesky(Gm)
-        Rinv = torch.linalg.inv(L.T)
-        out = torch.empty_like(U0)
+        Rinv = torch.linalg.inv(L.T).float()
         for r0 in range(0, m, chunk_rows):
-            out[r0:r0 + chunk_rows] = (U0[r0:r0 + chunk_rows].double() @ Rinv).float()
-        U0 = out
+            U0[r0:r0 + chunk_rows] = U0[r0:r0 + chunk_rows] @ Rinv
     Qv, Rv = torch.linalg.qr(Zv)
     Qv = Qv * torch.where(torch.diagonal(Rv) < 0, -1.0, 1.0)[None, :]
-    B = (Qv * sig[None, :]).T.contiguous()           # r x n, FP64
+    B = (Qv * sig[None, :]).T.contiguous().float()     # r x n
     A = torch.empty(m, n, dtype=dtype, device=device)
     c = None
     if offset_std:
-        c = offset_std * torch.randn(n, generator=g, device=device, dtype=torch.float64)
-    for r0 in range(0, m, chunk_rows):
-        blk = U0[r0:r0 + chunk_rows].double() @ B
-        if c is not None:
-            blk += c[None, :]
-        if noise_std:
-            blk += noise_std * torch.randn(blk.shape, generator=g, device=device,
-                                           dtype=torch.float64)
-        A[r0:r0 + chunk_rows] = blk.to(dtype)
+        c = (offset_std * torch.randn(n, generator=g, device=device, dtype=torch.float64)).float()
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for r0 in range(0, m, chunk_rows):
+            blk = U0[r0:r0 + chunk_rows] @ B
+            if c is not None:
+                blk += c[None, :]
+            if noise_std:
+                blk += noise_std * torch.randn(blk.shape, generator=g, device=device,
+                                               dtype=torch.float32)
+            A[r0:r0 + chunk_rows] = blk.to(dtype)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    del U0
     return A
 
 
