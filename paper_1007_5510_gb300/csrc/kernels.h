@@ -25,11 +25,15 @@ struct PassArgs {
   int64_t ldf = 0;
   bool accumulate_f = false;     // true: add into F (caller zeroed it)
   bool f_f64 = false;            // MODE_T: F is an FP64 accumulator
+  void* work = nullptr;          // device scratch for the tensor-core path
+  size_t work_bytes = 0;
 };
 
 void launch_pass_simt(const PassArgs& a, cudaStream_t st);
 // Tensor-core pass; returns false when the shape/dtype is not supported.
 bool launch_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
+// Fused Step-1 pass on tensor cores (k_fused_tc.cu); false if unsupported.
+bool fused_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
 
 // ---------------------------------------------------------------- linalg
 // C (p x q, FP64, ldc) (+)= X^T Y over rows [0, m); X m x p (ldx), Y m x q.

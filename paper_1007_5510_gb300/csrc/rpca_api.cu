@@ -159,7 +159,7 @@ struct rpca_ctx {
   bool centered = false;
   std::string last_error;
 
-  DevBuf X, F, H, T, shift, corr, d, vtmp, q1, G64, small, err, At, tiles[2];
+  DevBuf X, F, H, T, shift, corr, d, vtmp, q1, G64, small, err, At, tiles[2], work;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   int64_t tile_rows = 0;
   QrScratch qs;
@@ -235,6 +235,8 @@ void validate(const rpca_problem* p) {
 // One streamed pass over the working matrix (device-resident or tiles).
 void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
   const size_t ab = dtype_bytes(c->prob.dtype);
+  a.work = c->work.ptr;
+  a.work_bytes = c->work.bytes;
   if (!c->host_a) {
     a.A = c->transposed ? c->At.ptr : Am->data;
     a.lda = c->transposed ? c->n : Am->ld;
@@ -498,6 +500,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->qs.qf = reinterpret_cast<uint32_t*>(s);
   RPCA_CUDA_TRY(cudaMemsetAsync(c->qs.qf, 0, 4 * 16 * sizeof(uint32_t), c->stream));
   if (c->transposed) c->At.alloc((size_t)c->m * c->n * dtype_bytes(p->dtype));
+  if (!c->simt) c->work.alloc((size_t)c->m * round_up(c->w, 64) * 2 + 4096);
   if (c->host_a) {
     const size_t ab = dtype_bytes(p->dtype);
     int64_t tr = p->tile_rows > 0 ? p->tile_rows : std::max<int64_t>(128, (int64_t)((1ull << 30) / (c->n * ab)));
@@ -638,6 +641,12 @@ rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t p
     a.A = A; a.lda = lda; a.m = m; a.n = n; a.scale = col_scale; a.shift = shift;
     a.X = X; a.ldx = ldx; a.p = p; a.H = H; a.ldh = ldh; a.F = F; a.ldf = ldf;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevBuf work;
+    if (kernel != 1 && dtype != RPCA_F64) {
+      work.alloc((size_t)64 * round_up(n, 8) * 2 + 4096);
+      a.work = work.ptr;
+      a.work_bytes = work.bytes;
+    }
     if (kernel == 2) {
       if (!launch_pass_tc(a, st, nullptr)) throw Invalid("tensor-core pass unsupported for this shape");
     } else if (kernel == 1 || !launch_pass_tc(a, st, nullptr)) {
@@ -660,6 +669,12 @@ rpca_status rpca_op_t_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t w, co
     a.A = A; a.lda = lda; a.m = m; a.n = n; a.scale = col_scale; a.shift = shift;
     a.p = w; a.H = const_cast<void*>(Q); a.ldh = ldq; a.F = T; a.ldf = ldt;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevBuf work;
+    if (kernel != 1 && dtype != RPCA_F64) {
+      work.alloc((size_t)m * round_up(w, 64) * 2 + 4096);
+      a.work = work.ptr;
+      a.work_bytes = work.bytes;
+    }
     if (kernel == 2) {
       if (!launch_pass_tc(a, st, nullptr)) throw Invalid("tensor-core pass unsupported for this shape");
     } else if (kernel == 1 || !launch_pass_tc(a, st, nullptr)) {

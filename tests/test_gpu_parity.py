@@ -247,3 +247,59 @@ def test_rerun_reuses_context():
     finally:
         ctx.close()
     assert torch.allclose(S2, 2 * S1, rtol=1e-5)
+
+
+# ------------------------------------------------- tensor-core T pass (BF16)
+@pytest.mark.parametrize("m,n,w", [(3001, 512, 66), (5000, 520, 180), (20000, 4096, 180), (777, 256, 24)])
+def test_t_pass_tensor_cores_bf16(m, n, w):
+    """tcgen05 T pass: BF16 A and BF16-rounded Q, FP32 accumulation."""
+    rng = np.random.default_rng(m + w)
+    A = rng.standard_normal((m, n))
+    Q = np.linalg.qr(rng.standard_normal((m, w)))[0]
+    At, Ao = _stored(A, "bf16")
+    T = R().t_pass(At, _tt(Q), kernel=2)
+    torch.cuda.synchronize()
+    Qo = gen.round_bf16_np(Q).astype(np.float64)
+    To = ro.t_pass_product(Ao, Qo)
+    assert _rel(T.cpu().numpy(), To) < 2e-5
+
+
+# ------------------------------------------- tensor-core fused pass (BF16)
+@pytest.mark.parametrize("m,n,l", [(1000, 512, 12), (5000, 4096, 60), (777, 1000, 22),
+                                   (3001, 2000, 30), (300, 64, 20)])
+@pytest.mark.parametrize("with_f", [True, False])
+def test_fused_pass_tensor_cores_bf16(m, n, l, with_f):
+    """Cluster-split tcgen05 pass: H = A bf16(X) and F = A^T bf16(H) (the
+    kernel feeds BF16 operands to the tensor cores, FP32 accumulation)."""
+    rng = np.random.default_rng(m + n + l)
+    A = rng.standard_normal((m, n))
+    X = rng.standard_normal((n, l))
+    At, Ao = _stored(A, "bf16")
+    H, F = R().fused_pass(At, _tt(X), with_f=with_f, kernel=2)
+    torch.cuda.synchronize()
+    Xo = gen.round_bf16_np(X).astype(np.float64)
+    Ho, _ = ro.fused_pass_products(Ao, Xo)
+    assert _rel(H.cpu().numpy(), Ho) < 2e-5
+    if with_f:
+        Hb = gen.round_bf16_np(H.cpu().numpy()).astype(np.float64)
+        Fo = ro.t_pass_product(Ao, Hb)
+        assert _rel(F.cpu().numpy(), Fo) < 2e-5
+
+
+def test_pca_bf16_tensor_cores_vs_fp32():
+    """Whole method on BF16 storage (tensor-core passes) against the oracle on
+    the same BF16 values, and its spectral error against the FP32 path's."""
+    m, n, k, l, i = 20_000, 1024, 16, 20, 2
+    A = gen.lowrank_np(m, n, np.exp(-np.arange(1, n + 1) / 10.0), seed=3) + \
+        1e-3 * np.random.default_rng(3).standard_normal((m, n))
+    A32 = A.astype(np.float32)
+    Ab = torch.from_numpy(A32).cuda().to(torch.bfloat16)
+    U, S, V = R().pca(Ab, k, l, i, seed=11)
+    U2, S2, V2 = R().pca(_tt(A32), k, l, i, seed=11)
+    Aob = Ab.float().cpu().double().numpy()
+    Uo, So, Vo = ro.rpca(Aob, k, l, i, seed=11, normalize=True)
+    rel = np.max(np.abs(S.cpu().numpy() - So) / So)
+    assert rel < 1e-3, rel
+    e16 = est.spectral_error(A32.astype(np.float64), U.cpu().double().numpy(), S.cpu().numpy(), V.cpu().double().numpy())
+    e32 = est.spectral_error(A32.astype(np.float64), U2.cpu().double().numpy(), S2.cpu().numpy(), V2.cpu().double().numpy())
+    assert e16 <= 1.05 * e32, (e16, e32)
