@@ -222,7 +222,7 @@ def main():
     fused_ms32 = per_launch(ph32, runs32, fused_idx)
     tpass_ms16 = per_launch(ph16, runs16, [i + 2])
     achieved = m * n * bytes_bf16 / (fused_ms16 / 1e3) / 1e9
-    names = ["pass%d" % j for j in range(i + 1)] + ["qr", "t_pass", "svd_epilogue"]
+    names = ["pass%d" % j for j in range(i + 1)] + ["qr_h", "t_pass", "small_svd", "u_v"]
     phases16 = {nm: round(v / max(1, runs16), 4) for nm, v in zip(names, ph16)}
     phases32 = {nm: round(v / max(1, runs32), 4) for nm, v in zip(names, ph32)}
 

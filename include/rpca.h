@@ -166,6 +166,21 @@ rpca_status rpca_op_t_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t w,
 rpca_status rpca_op_qr(int32_t f64, int64_t m, int32_t nblk, int32_t l,
                        void* H, int64_t ld, void* stream);
 
+/* C (p x q, FP64, ldc) = X^T Y over m rows; X (m x p, ldx) and Y (m x q,
+ * ldy) FP32 device matrices.  kernel: 0 auto, 1 CUDA cores, 2 tensor cores
+ * (FP32-accurate TF32 x3).  p, q <= 256.  Synchronises `stream`. */
+rpca_status rpca_op_gram(int64_t m, int32_t p, int32_t q, const float* X,
+                         int64_t ldx, const float* Y, int64_t ldy, double* C,
+                         int64_t ldc, int32_t kernel, void* stream);
+
+/* Y (m x q, ldy) = beta Y + alpha X M; X (m x p, ldx) FP32, M (p x q, ldm)
+ * FP64, all device memory.  kernel as for rpca_op_gram.  p, q <= 256.
+ * Synchronises `stream`. */
+rpca_status rpca_op_apply(int64_t m, int32_t p, int32_t q, const float* X,
+                          int64_t ldx, const double* M, int64_t ldm,
+                          double alpha, double beta, float* Y, int64_t ldy,
+                          int32_t kernel, void* stream);
+
 /* Step 4 on T (n x w, ldt, FP32 or FP64 per f64): S[w] (FP64, device),
  * Vt (n x w, ldv, same type as T) and W (w x w FP64 row-major, device). */
 rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w,
@@ -184,8 +199,9 @@ uint64_t rpca_kernel_launches(void);
 /* Per-phase device times of a context created with RPCA_TIMING, summed
  * over the runs finished since the previous call (then reset).  Phases:
  * 0..i the streaming kernels of the Step-1 passes, i+1 the QR of H (Step 2),
- * i+2 the T pass (Step 3), i+3 Steps 4-6.  Writes min(cap, i+4) values (ms)
- * to ms (host), the run count to *runs (may be NULL); returns i+4, or 0
+ * i+2 the T pass (Step 3), i+3 Step 4 (QR of T and the small SVD), i+4 the
+ * products forming U and V (Steps 5-6).  Writes min(cap, i+5) values (ms)
+ * to ms (host), the run count to *runs (may be NULL); returns i+5, or 0
  * without RPCA_TIMING. */
 int32_t rpca_phase_times(rpca_ctx* c, double* ms, int32_t cap, int32_t* runs);
 

@@ -18,6 +18,8 @@
 // warps 2-5 TMEM drain / reduction / F flush.  Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cstdio>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -70,12 +72,13 @@ __device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t cta) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(cta));
   return r;
 }
+// Remote shared-memory load (no compiler barrier, so a batch of independent
+// loads is issued back to back and their latencies overlap).
 __device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr) {
   float4 v;
   asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(addr)
-               : "memory");
+               : "r"(addr));
   return v;
 }
 __device__ __forceinline__ void st_cluster_b64(uint32_t addr, uint32_t a, uint32_t b) {
@@ -299,13 +302,11 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         }
       }
       tc::tc_fence_before();
-      asm volatile("fence.acq_rel.cluster;" ::: "memory");
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&pempty[pb]);
       epi_bar();
-      if (e == 0) {
-        for (uint32_t c = 0; c < cs; ++c) tc::mbar_arrive_cluster(pready, c);
-      }
+      // one thread per destination CTA: the release-arrives run in parallel
+      if (e < (int)cs) tc::mbar_arrive_cluster(pready, (uint32_t)e);
       ok = tc::mbar_wait(pready, (uint32_t)(it & 1), p.dev_err, abort_flag, true);
       if (FUSED)
         ok = ok && tc::mbar_wait(&hfree[x], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag, true);
@@ -317,9 +318,14 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int rr = row0 + ch / CPR, chunk = ch % CPR, col = chunk * 4;
         const uint32_t off = (uint32_t)(rr * L * 4 + ((chunk ^ (rr & (CPR - 1))) * 16));
         float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (uint32_t c = 0; c < cs; ++c) {
-          float4 v = ld_cluster_f4(mapa(pst_a + off, c));
-          sacc.x += v.x; sacc.y += v.y; sacc.z += v.z; sacc.w += v.w;
+        for (uint32_t c0 = 0; c0 < cs; c0 += 8) {
+          float4 v[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (c0 + q < cs) v[q] = ld_cluster_f4(mapa(pst_a + off, c0 + q));
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (c0 + q < cs) { sacc.x += v[q].x; sacc.y += v[q].y; sacc.z += v[q].z; sacc.w += v[q].w; }
         }
         const int64_t grow = r0 + rr;
         float vv[4] = {sacc.x, sacc.y, sacc.z, sacc.w};
@@ -337,13 +343,11 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           for (uint32_t c = 0; c < cs; ++c) st_cluster_b64(mapa(hs_a + x * HS_BYTES + hoff, c), lo, hi);
         }
       }
-      asm volatile("fence.acq_rel.cluster;" ::: "memory");
       if (FUSED) asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
       epi_bar();
-      if (e == 0) {
-        for (uint32_t c = 0; c < cs; ++c) tc::mbar_arrive_cluster(pfree, c);
-        if (FUSED)
-          for (uint32_t c = 0; c < cs; ++c) tc::mbar_arrive_cluster(&hready[x], c);
+      if (e < (int)cs) {
+        tc::mbar_arrive_cluster(pfree, (uint32_t)e);
+        if (FUSED) tc::mbar_arrive_cluster(&hready[x], (uint32_t)e);
       }
     }
     // ---------------------------------------------------- flush F slab
@@ -443,6 +447,9 @@ bool launch_fused(const PassArgs& a, cudaStream_t st, uint32_t* dev_err, int cs)
   const int64_t npan = cdiv(a.m, FP_BM);
   const int ncl = (int)std::max<int64_t>(1, std::min<int64_t>(max_cl, npan));
   cfg.gridDim = dim3(cs * ncl);
+  if (getenv("RPCA_DEBUG"))
+    fprintf(stderr, "[rpca] fused L=%d NT=%d fused=%d cs=%d max_clusters=%d clusters=%d smem=%zu stages=%d\n", L,
+            NT, (int)FUSED, cs, max_cl, ncl, smem, p.nstages);
   RPCA_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, tmA, tmX, p));
   count_launch();
   return true;

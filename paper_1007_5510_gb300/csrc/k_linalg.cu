@@ -142,25 +142,30 @@ k_gemm_xm(int64_t m, int p, int q, const TC* __restrict__ X, int64_t ldx,
 }
 
 // --------------------------------------------------------------- Cholesky
-// One CTA.  G = R^T R (R upper), then Rinv by back substitution.
+// One CTA.  G = R^T R (R upper), then Rinv by back substitution, both in
+// shared memory (p <= 64) or global memory (larger p).
 // Pass `pass` (0..3) of a Cholesky-QR sequence on one block (qf: 4 words
 // private to the block: qf[0] = which passes needed a shift, qf[2], qf[3] =
 // whether passes 2 and 3 run).  A pivot below piv_rel * max(diag G) retries
 // with G + shift_rel * max(diag G) I (shifted Cholesky QR); passes 2-3 only
 // run after a shifted pass and otherwise leave identities (exact no-ops).
 __global__ void __launch_bounds__(256)
-k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ R,
-       double* __restrict__ Rinv, int pass, double piv_rel, double shift_rel, uint32_t* qf,
+k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Rout,
+       double* __restrict__ Rinvout, int pass, double piv_rel, double shift_rel, uint32_t* qf,
        uint32_t* dev_err) {
   const int tid = threadIdx.x;
   __shared__ int fail;
   __shared__ double dmax;
+  extern __shared__ double sm_chol[];
+  const bool in_smem = p <= 64;
+  double* R = in_smem ? sm_chol : Rout;
+  double* Rinv = in_smem ? sm_chol + p * p : Rinvout;
   const bool active = (pass < 2) || (qf[pass] != 0u);
   if (!active) {
     for (int e = tid; e < p * p; e += blockDim.x) {
       double v = (e / p == e % p) ? 1.0 : 0.0;
-      R[e] = v;
-      Rinv[e] = v;
+      Rout[e] = v;
+      Rinvout[e] = v;
     }
     if (tid == 0 && pass == 2) qf[3] = 0u;
     return;
@@ -205,8 +210,8 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ R,
       if (tid == 0) atomicOr(dev_err, DEV_ERR_BREAKDOWN);
       for (int e = tid; e < p * p; e += blockDim.x) {
         double v = (e / p == e % p) ? 1.0 : 0.0;
-        R[e] = v;
-        Rinv[e] = v;
+        Rout[e] = v;
+        Rinvout[e] = v;
       }
       return;
     }
@@ -222,19 +227,22 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ R,
     if (pass == 1) qf[2] = (qf[0] & 3u) ? 1u : 0u;
     if (pass == 2) qf[3] = ((qf[0] >> 1) & 3u) ? 1u : 0u;
   }
+  // Rinv = R^-1: rows from the bottom up, all columns in parallel
+  for (int e = tid; e < p * p; e += blockDim.x) Rinv[e] = 0.0;
   __syncthreads();
-  // Rinv: column c solves R x = e_c (upper triangular back substitution).
-  for (int c = tid; c < p; c += blockDim.x) {
-    for (int i = p - 1; i >= 0; --i) {
-      double v;
-      if (i > c) {
-        v = 0.0;
-      } else {
-        double sum = (i == c) ? 1.0 : 0.0;
-        for (int j = i + 1; j <= c; ++j) sum -= R[i * p + j] * Rinv[j * p + c];
-        v = sum / R[i * p + i];
-      }
-      Rinv[i * p + c] = v;
+  for (int i = p - 1; i >= 0; --i) {
+    const double rii = R[i * p + i];
+    for (int c = i + tid; c < p; c += blockDim.x) {
+      double sum = (i == c) ? 1.0 : 0.0;
+      for (int j = i + 1; j <= c; ++j) sum -= R[i * p + j] * Rinv[j * p + c];
+      Rinv[i * p + c] = sum / rii;
+    }
+    __syncthreads();
+  }
+  if (in_smem) {
+    for (int e = tid; e < p * p; e += blockDim.x) {
+      Rout[e] = R[e];
+      Rinvout[e] = Rinv[e];
     }
   }
 }
@@ -275,20 +283,24 @@ __global__ void k_mat_add(int rows, int cols, const double* __restrict__ src, in
 // ------------------------------------------------------------------ Jacobi
 // One-sided (Hestenes) Jacobi on the columns of B (w x w), one CTA of 1024
 // threads: rounds of a round-robin tournament, one warp per column pair.
-// Columns are stored contiguously (Bc[c*w + r] = B[r][c]); J accumulates the
-// rotations (J[c*w + r] = W[r][c]).
+// Columns are stored contiguously (Bc[c*w + r] = B[r][c]) and the rotations
+// are accumulated in J (Jc[c*w + r] = W[r][c]); both live in shared memory
+// when they fit (B alone otherwise, J in global memory).
 template <typename TJ>
 __global__ void __launch_bounds__(1024)
-k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc, TJ* __restrict__ Jc,
-         double tol, int max_sweeps, uint32_t* dev_err) {
+k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc_g, TJ* __restrict__ Jc_g, double tol,
+         int max_sweeps, uint32_t* dev_err) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const bool in_smem = ((size_t)w * w * sizeof(TJ) <= 160 * 1024);
-  TJ* Bw = in_smem ? reinterpret_cast<TJ*>(smem_raw) : Bc;
+  const size_t mat = (size_t)w * w * sizeof(TJ);
+  const bool b_smem = mat <= 200 * 1024;
+  const bool j_smem = 2 * mat <= 200 * 1024;
+  TJ* Bw = b_smem ? reinterpret_cast<TJ*>(smem_raw) : Bc_g;
+  TJ* Jw = j_smem ? reinterpret_cast<TJ*>(smem_raw) + (size_t)w * w : Jc_g;
   for (int e = tid; e < w * w; e += blockDim.x) {
     int c = e / w, r = e % w;
     Bw[e] = TJ(B[(int64_t)r * w + c]);
-    Jc[e] = TJ(r == c ? 1 : 0);
+    Jw[e] = TJ(r == c ? 1 : 0);
   }
   __shared__ float off_max;
   __syncthreads();
@@ -324,17 +336,15 @@ k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc, TJ* __restric
         TJ zeta = (be - al) / (TJ(2) * ga);
         TJ t = (zeta >= 0 ? TJ(1) : TJ(-1)) / (fabs(zeta) + sqrt(TJ(1) + zeta * zeta));
         TJ c = TJ(1) / sqrt(TJ(1) + t * t), s = c * t;
+        TJ* jp = Jw + (int64_t)pcol * w;
+        TJ* jq = Jw + (int64_t)qcol * w;
         for (int r = lane; r < w; r += 32) {
           TJ x = bp[r], y = bq[r];
           bp[r] = c * x - s * y;
           bq[r] = s * x + c * y;
-        }
-        TJ* jp = Jc + (int64_t)pcol * w;
-        TJ* jq = Jc + (int64_t)qcol * w;
-        for (int r = lane; r < w; r += 32) {
-          TJ x = jp[r], y = jq[r];
-          jp[r] = c * x - s * y;
-          jq[r] = s * x + c * y;
+          TJ u = jp[r], v = jq[r];
+          jp[r] = c * u - s * v;
+          jq[r] = s * u + c * v;
         }
       }
       __syncthreads();
@@ -345,6 +355,9 @@ k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc, TJ* __restric
     __syncthreads();
   }
   if (tid == 0 && sweep >= max_sweeps) atomicOr(dev_err, DEV_ERR_JACOBI);
+  if (tid == 0) dev_err[8] = (uint32_t)sweep;   // sweeps used (diagnostics)
+  if (j_smem)
+    for (int e = tid; e < w * w; e += blockDim.x) Jc_g[e] = Jw[e];
 }
 
 // Normalise the columns of J into W (FP64, row-major w x w).
@@ -397,6 +410,21 @@ __global__ void k_svd_finish(int w, const double* __restrict__ B64, const double
     W[(int64_t)r * w + d] = Win[e];
   }
   for (int c = threadIdx.x; c < w; c += blockDim.x) S[pos[c]] = sig[c];
+}
+
+// Y = beta Y + alpha X M, FP64 storage, FP32 arithmetic; one thread per
+// output element.
+__global__ void k_small_gemm_f32(int m, int p, int q, const double* __restrict__ X, int64_t ldx,
+                                 const double* __restrict__ M, int64_t ldm, double alpha, double beta,
+                                 double* __restrict__ Y, int64_t ldy) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * q) return;
+  int i = e / q, j = e % q;
+  float acc = 0.f;
+  for (int k = 0; k < p; ++k) acc = fmaf((float)X[(int64_t)i * ldx + k], (float)M[(int64_t)k * ldm + j], acc);
+  double y = alpha * (double)acc;
+  if (beta != 0.0) y += beta * Y[(int64_t)i * ldy + j];
+  Y[(int64_t)i * ldy + j] = y;
 }
 
 // ----------------------------------------------------------------- small ops
@@ -567,7 +595,13 @@ void gemm_xm(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, cons
 
 void chol_small(int p, const double* G, int64_t ldg, double* R, double* Rinv, int pass,
                 double piv_rel, double shift_rel, uint32_t* qf, uint32_t* dev_err, cudaStream_t st) {
-  k_chol<<<1, 256, 0, st>>>(p, G, ldg, R, Rinv, pass, piv_rel, shift_rel, qf, dev_err);
+  const size_t sm = p <= 64 ? (size_t)2 * p * p * sizeof(double) : 0;
+  static bool attr = false;
+  if (!attr) {
+    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
+    attr = true;
+  }
+  k_chol<<<1, 256, sm, st>>>(p, G, ldg, R, Rinv, pass, piv_rel, shift_rel, qf, dev_err);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
 }
@@ -605,27 +639,38 @@ void jacobi_svd(bool f64, int w, const double* B, double* S, double* Ub, double*
   double* W0 = work + 2 * (size_t)w * w;
   double* B64 = work + 3 * (size_t)w * w;
   if (f64) {
-    size_t smem = (size_t)w * w * sizeof(double) <= 160 * 1024 ? (size_t)w * w * sizeof(double) : 0;
-    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    const size_t mat = (size_t)w * w * sizeof(double);
+    const size_t smem = 2 * mat <= 200 * 1024 ? 2 * mat : (mat <= 200 * 1024 ? mat : 0);
+    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     k_jacobi<double><<<1, 1024, smem, st>>>(w, B, Bc, Jc, 4.0 * std::sqrt((double)w) * 1.11e-16, 60, dev_err);
     RPCA_CUDA_TRY(cudaGetLastError());
     k_jacobi_w<double><<<w, 128, 0, st>>>(w, Jc, W0);
   } else {
     float* Bc32 = reinterpret_cast<float*>(Bc);
     float* Jc32 = reinterpret_cast<float*>(Jc);
-    size_t smem = (size_t)w * w * sizeof(float) <= 160 * 1024 ? (size_t)w * w * sizeof(float) : 0;
-    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    const size_t mat = (size_t)w * w * sizeof(float);
+    const size_t smem = 2 * mat <= 200 * 1024 ? 2 * mat : (mat <= 200 * 1024 ? mat : 0);
+    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     k_jacobi<float><<<1, 1024, smem, st>>>(w, B, Bc32, Jc32, 4.0 * std::sqrt((double)w) * 5.96e-8, 40, dev_err);
     RPCA_CUDA_TRY(cudaGetLastError());
     k_jacobi_w<float><<<w, 128, 0, st>>>(w, Jc32, W0);
   }
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch(2);
-  // B64 = B W0 (FP64): singular values as column norms of B times unit
-  // approximate right singular vectors (second-order accurate).
-  gemm_xm(true, w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st, nullptr);
+  // B64 = B W0: singular values as column norms of B times unit approximate
+  // right singular vectors (second-order accurate).
+  if (f64) gemm_xm(true, w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st, nullptr);
+  else small_gemm_f32(w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st);
   size_t smem = (size_t)w * (sizeof(double) + sizeof(int));
   k_svd_finish<<<1, 256, smem, st>>>(w, B64, W0, S, Ub, W);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void small_gemm_f32(int m, int p, int q, const double* X, int64_t ldx, const double* M, int64_t ldm,
+                    double alpha, double beta, double* Y, int64_t ldy, cudaStream_t st) {
+  if (m <= 0 || q <= 0) return;
+  k_small_gemm_f32<<<grid1((int64_t)m * q), 256, 0, st>>>(m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
 }

@@ -1,0 +1,473 @@
+// Tall-skinny products of Step 2 (QR of H) and Steps 5-6 on tensor cores,
+// FP32-accurate.
+//   gram:   C (p x q, FP64) = X^T Y over all rows, X m x p, Y m x q.  The
+//           rows are the reduction (MN-major operands), done in BF16 with
+//           each FP32 value split exactly into three BF16 slices (six slice
+//           products); CTAs split the rows, each keeps its partial in TMEM
+//           and adds it to C once.
+//   apply:  Y (m x q) = beta Y + alpha X M, X m x p (K-major operand), M p x q
+//           (FP64 small matrix, resident in shared memory).  Every FP32
+//           operand x is carried as x (its TF32 truncation is what the MMA
+//           reads) plus x_lo = x - trunc_tf32(x) in a companion array:
+//               x y ~ trunc(x) trunc(y) + trunc(x) y_lo + x_lo trunc(y)
+//           (three kind::tf32 MMAs, ~2^-21 relative); Y_lo is written too.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cstdio>
+#include <cstdlib>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace rpca {
+namespace {
+
+constexpr int G_KSUB = 32;         // rows per Gram stage
+constexpr int G_THREADS = 128;
+
+__device__ __forceinline__ float tf32_trunc(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+__global__ void k_split_lo(int64_t rows, int cols, const float* __restrict__ X, int64_t ldx,
+                           float* __restrict__ Xlo, int64_t ldl) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t r = e / cols;
+  int c = (int)(e % cols);
+  float x = X[r * ldx + c];
+  Xlo[r * ldl + c] = x - tf32_trunc(x);
+}
+
+// ------------------------------------------------------------------ Gram
+// FP32 data split exactly into three BF16 slices, x = x1 + x2 + x3 (x1 =
+// RNE(x), x2 = RNE(x - x1), x3 = x - x1 - x2; each fits 8 significant bits),
+// so every slice product is exact in FP32 and
+//     x y ~ x1 y1 + x1 y2 + x2 y1 + x1 y3 + x2 y2 + x3 y1      (error ~2^-24)
+// Slices are stored as three BF16 matrices of rows x ldS (ldS = cols rounded
+// up to 64) so that TMA boxes of 64 columns tile them exactly.
+// Rows [rows, plane_rows) of each plane are zero so that a TMA box never
+// reads into the next plane.
+__global__ void k_slice3(int64_t rows, int64_t plane_rows, int cols, int ldS, const float* __restrict__ X,
+                         int64_t ldx, __nv_bfloat16* __restrict__ S, const uint32_t* __restrict__ active) {
+  if (active && *active == 0u) return;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= plane_rows * ldS) return;
+  int64_t r = e / ldS;
+  int c = (int)(e % ldS);
+  float x = (c < cols && r < rows) ? X[r * ldx + c] : 0.f;
+  __nv_bfloat16 b1 = __float2bfloat16_rn(x);
+  float r1 = x - __bfloat162float(b1);
+  __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+  float r2 = r1 - __bfloat162float(b2);
+  __nv_bfloat16 b3 = __float2bfloat16_rn(r2);
+  const int64_t plane = plane_rows * ldS;
+  S[e] = b1;
+  S[plane + e] = b2;
+  S[2 * plane + e] = b3;
+}
+
+// A operand: X columns [t*128, t*128+128) of each slice (MN-major, 2 boxes of
+// 64 columns), B operand: Y columns [0, npad) of each slice (MN-major).
+// Stage: X slices (3 x NXB boxes) then, unless X and Y coincide, Y slices
+// (3 x nybox boxes); boxes of G_KSUB rows x 64 BF16 columns.
+template <int NT, bool SAME>
+__global__ void __launch_bounds__(G_THREADS, 1)
+k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t m,
+              int64_t plane_rows, int p, int q, int npad, int nybox, int ngroup, int nstages,
+              uint32_t stage_bytes, double* __restrict__ C, int64_t ldc, uint32_t* __restrict__ dev_err,
+              const uint32_t* __restrict__ active) {
+  if (active && *active == 0u) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int NXB = NT * 2;                           // X boxes (64 cols each) per slice
+  constexpr uint32_t BOX = G_KSUB * 128;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * stage_bytes);
+  uint64_t* empty = full + nstages;
+  uint64_t* done = empty + nstages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int group = blockIdx.x;
+  const int64_t nsub = (m + G_KSUB - 1) / G_KSUB;
+  const int64_t my_subs = (nsub > group) ? (nsub - group + ngroup - 1) / ngroup : 0;
+  const uint32_t tcols = (NT * npad <= 32) ? 32 : (NT * npad <= 64) ? 64 : (NT * npad <= 128) ? 128
+                         : (NT * npad <= 256) ? 256 : 512;
+  if (tid == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, tcols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 0 && lane == 0) {
+    for (int64_t it = 0; it < my_subs; ++it) {
+      const int s = (int)(it % nstages);
+      if (!tc::mbar_wait(&empty[s], (uint32_t)(((it / nstages) & 1) ^ 1), dev_err, abort_flag)) break;
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      const int64_t r0 = (group + it * ngroup) * G_KSUB;
+      tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+      for (int sl = 0; sl < 3; ++sl) {
+        const int32_t y = (int32_t)(sl * plane_rows + r0);
+        for (int j = 0; j < NXB; ++j)
+          tc::tma_load_2d(st + (size_t)(sl * NXB + j) * BOX, &tmX, &full[s], 64 * j, y);
+        if (!SAME)
+          for (int j = 0; j < nybox; ++j)
+            tc::tma_load_2d(st + (size_t)(3 * NXB + sl * nybox + j) * BOX, &tmY, &full[s], 64 * j, y);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = tc::idesc_make(1u, 1u, 1u, 128u, (uint32_t)npad);
+    // slice pairs (a, b) with a + b <= 4 (1-based): (1,1) (1,2) (2,1) (1,3) (2,2) (3,1)
+    const int pa[6] = {0, 0, 1, 0, 1, 2};
+    const int pb[6] = {0, 1, 0, 2, 1, 0};
+    for (int64_t it = 0; it < my_subs; ++it) {
+      const int s = (int)(it % nstages);
+      if (!tc::mbar_wait(&full[s], (uint32_t)((it / nstages) & 1), dev_err, abort_flag)) break;
+      tc::tc_fence_after();
+      const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
+      const uint32_t ybase = SAME ? sa : sa + 3 * NXB * BOX;
+      const uint32_t ystride = SAME ? NXB * BOX : nybox * BOX;   // bytes between slices of Y
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+#pragma unroll
+        for (int kk = 0; kk < G_KSUB / 16; ++kk) {
+          const uint32_t ko = kk * 2048;
+          const uint32_t d = tmem + t * npad;
+#pragma unroll
+          for (int pr = 0; pr < 6; ++pr) {
+            const uint64_t ad = tc::sdesc_sw128(sa + pa[pr] * NXB * BOX + t * 2 * BOX + ko, BOX, 1024);
+            const uint64_t bd = tc::sdesc_sw128(ybase + pb[pr] * ystride + ko, BOX, 1024);
+            tc::mma_f16(d, ad, bd, idesc, (it > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+          }
+        }
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(done);
+  }
+  __syncwarp();
+  bool ok = (my_subs == 0) ? false : tc::mbar_wait(done, 0, dev_err, abort_flag);
+  ok = __all_sync(0xffffffffu, ok);
+  tc::tc_fence_after();
+  if (ok) {
+    for (int t = 0; t < NT; ++t) {
+      const int row = t * 128 + warp * 32 + lane;   // X column
+      for (int c16 = 0; c16 < npad; c16 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * npad + c16, v);
+        if (row < p) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c16 + j < q) atomicAdd(&C[(int64_t)row * ldc + c16 + j], (double)v[j]);
+        }
+      }
+    }
+  }
+  if (warp == 1 && lane == 0) {
+    volatile int never = 0;
+    tc::mbar_wait(done, 0, nullptr, &never);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, tcols);
+}
+
+// ----------------------------------------------------------------- apply
+// Y[r, :] = beta Y[r, :] + alpha X[r, :] M for 128-row tiles (persistent).
+// A operand: X tile, K-major (row-major X, K = p columns); each pipeline
+// stage holds one 32-column K box of the tile, hi and lo (2 x 16 KB).
+// B operand: M^T (N = q rows, K = p), hi and lo, K-major, resident in shared
+// memory: kb = ceil(p/32) boxes of nq rows x 32 columns.  TMEM holds two
+// accumulators (nq columns each) so the drain of one tile overlaps the MMAs
+// of the next.
+constexpr int A_THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+__global__ void __launch_bounds__(A_THREADS, 1)
+k_apply_tf32x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmXl, int64_t m,
+               int p, int q, int nq, int kb, int nstages, const float* __restrict__ Mt,
+               const float* __restrict__ Mtl, float alpha, float beta, float* Y, int64_t ldy, float* Ylo,
+               int64_t ldyl, uint32_t* __restrict__ dev_err, const uint32_t* __restrict__ active) {
+  if (active && *active == 0u) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr uint32_t XBOX = 128 * 128;           // 128 rows x 32 FP32
+  constexpr uint32_t STAGE = 2 * XBOX;           // hi + lo
+  const uint32_t mbox = (uint32_t)nq * 128;      // nq rows x 32 FP32
+  unsigned char* mh = smem;
+  unsigned char* ml = mh + (size_t)kb * mbox;
+  unsigned char* stages = ml + (size_t)kb * mbox;
+  uint64_t* full = reinterpret_cast<uint64_t*>(stages + (size_t)nstages * STAGE);
+  uint64_t* empty = full + nstages;
+  uint64_t* afull = empty + nstages;   // [2] accumulator ready
+  uint64_t* aempty = afull + 2;        // [2] accumulator drained
+  uint64_t* done = aempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntile = (m + 127) / 128;
+  const int64_t my_tiles = (ntile > blockIdx.x) ? (ntile - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t steps = my_tiles * kb;
+  const uint32_t tcols = (2 * nq <= 64) ? 64 : (2 * nq <= 128) ? 128 : (2 * nq <= 256) ? 256 : 512;
+
+  // resident M^T (hi, lo) in the K-major SW128 layout: element (n, k) of box
+  // k/32 at row n, 16-byte chunk (k%32)/4 XOR (n%8)
+  for (int e = tid; e < kb * nq * 32; e += blockDim.x) {
+    const int bx = e / (nq * 32), rem = e % (nq * 32), n = rem / 32, kk = rem % 32;
+    const int k = bx * 32 + kk;
+    const float vh = (n < q && k < p) ? Mt[(int64_t)n * p + k] : 0.f;
+    const float vl = (n < q && k < p) ? Mtl[(int64_t)n * p + k] : 0.f;
+    const uint32_t off = (uint32_t)bx * mbox + n * 128 + ((((kk >> 2) ^ (n & 7))) << 4) + (kk & 3) * 4;
+    *reinterpret_cast<float*>(mh + off) = vh;
+    *reinterpret_cast<float*>(ml + off) = vl;
+  }
+  tc::fence_proxy_async_smem();
+  if (tid == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int x = 0; x < 2; ++x) {
+      tc::mbar_init(&afull[x], 1);
+      tc::mbar_init(&aempty[x], 4);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, tcols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t g = 0;
+      for (; g < steps; ++g) {
+        const int s = (int)(g % nstages);
+        if (!tc::mbar_wait(&empty[s], (uint32_t)(((g / nstages) & 1) ^ 1), dev_err, abort_flag)) break;
+        unsigned char* st = stages + (size_t)s * STAGE;
+        const int64_t tl = g / kb;
+        const int bx = (int)(g % kb);
+        const int32_t r0 = (int32_t)((blockIdx.x + tl * gridDim.x) * 128);
+        tc::mbar_arrive_expect_tx(&full[s], STAGE);
+        tc::tma_load_2d(st, &tmX, &full[s], 32 * bx, r0);
+        tc::tma_load_2d(st + XBOX, &tmXl, &full[s], 32 * bx, r0);
+      }
+      for (int64_t h = (g > nstages ? g - nstages : 0); h < g; ++h) {
+        volatile int never = 0;
+        tc::mbar_wait(&full[h % nstages], (uint32_t)((h / nstages) & 1), nullptr, &never);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_make(2u, 0u, 0u, 128u, (uint32_t)nq);
+      const uint32_t mha = tc::smem_u32(mh), mla = tc::smem_u32(ml);
+      for (int64_t g = 0; g < steps; ++g) {
+        const int s = (int)(g % nstages);
+        const int64_t tl = g / kb;
+        const int bx = (int)(g % kb);
+        const int x = (int)(tl & 1);
+        if (!tc::mbar_wait(&full[s], (uint32_t)((g / nstages) & 1), dev_err, abort_flag)) break;
+        if (bx == 0 && !tc::mbar_wait(&aempty[x], (uint32_t)(((tl >> 1) & 1) ^ 1), dev_err, abort_flag)) break;
+        tc::tc_fence_after();
+        const uint32_t sa = tc::smem_u32(stages + (size_t)s * STAGE);
+        const uint32_t d = tmem + x * nq;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ah = tc::sdesc_sw128(sa + kk * 32, 16, 1024);
+          const uint64_t al = tc::sdesc_sw128(sa + XBOX + kk * 32, 16, 1024);
+          const uint64_t bh = tc::sdesc_sw128(mha + bx * mbox + kk * 32, 16, 1024);
+          const uint64_t bl = tc::sdesc_sw128(mla + bx * mbox + kk * 32, 16, 1024);
+          tc::mma_tf32(d, ah, bh, idesc, (bx > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_tf32(d, ah, bl, idesc, 1u);
+          tc::mma_tf32(d, al, bh, idesc, 1u);
+        }
+        tc::mma_commit(&empty[s]);
+        if (bx == kb - 1) tc::mma_commit(&afull[x]);
+      }
+      tc::mma_commit(done);
+    }
+  } else {
+    // drain through a per-warp staging tile so that rows are written with
+    // coalesced 128-byte segments (lane = column)
+    float* stg = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(tmem_slot) + 16) +
+                 (warp - 2) * 32 * 33;
+    const int rbase = 32 * (warp & 3);
+    for (int64_t tl = 0; tl < my_tiles; ++tl) {
+      const int x = (int)(tl & 1);
+      bool ok = tc::mbar_wait(&afull[x], (uint32_t)((tl >> 1) & 1), dev_err, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc::tc_fence_after();
+      const int64_t r0 = (blockIdx.x + tl * gridDim.x) * 128 + rbase;
+      for (int c32 = 0; c32 < nq; c32 += 32) {
+        float v[16];
+        tc::tmem_ld16(tmem + x * nq + ((uint32_t)rbase << 16) + c32, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stg[lane * 33 + j] = v[j];
+        if (c32 + 16 < nq) {
+          tc::tmem_ld16(tmem + x * nq + ((uint32_t)rbase << 16) + c32 + 16, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) stg[lane * 33 + 16 + j] = v[j];
+        }
+        __syncwarp();
+        const int c = c32 + lane;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int64_t r = r0 + rr;
+          if (r < m && c < q) {
+            float y = alpha * stg[rr * 33 + lane];
+            if (beta != 0.f) y += beta * Y[r * ldy + c];
+            Y[r * ldy + c] = y;
+            if (Ylo) Ylo[r * ldyl + c] = y - tf32_trunc(y);
+          }
+        }
+        __syncwarp();
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&aempty[x]);
+    }
+  }
+  __syncwarp();
+  if (warp == 1 && lane == 0) {
+    volatile int never = 0;
+    tc::mbar_wait(done, 0, nullptr, &never);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, tcols);
+}
+
+// M (p x q FP64, ldm) -> M^T hi (q x p FP32) and lo.
+__global__ void k_mt_split(int p, int q, const double* __restrict__ M, int64_t ldm, float* __restrict__ Mt,
+                           float* __restrict__ Mtl) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p * q) return;
+  int n = e / p, k = e % p;
+  double v = M[(int64_t)k * ldm + n];
+  float h = (float)v;
+  float hh = tf32_trunc(h);
+  Mt[e] = h;
+  Mtl[e] = (float)(v - (double)hh);
+}
+
+int g_sms_qr = 0;
+constexpr size_t kStageBytes = 4 * 32 * 33 * 4;   // apply epilogue staging
+
+}  // namespace
+
+// ====================================================================== host
+void split_lo(int64_t rows, int cols, const float* X, int64_t ldx, float* Xlo, int64_t ldl, cudaStream_t st) {
+  int64_t cnt = rows * cols;
+  if (cnt <= 0) return;
+  k_split_lo<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(rows, cols, X, ldx, Xlo, ldl);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void slice3(int64_t rows, int64_t plane_rows, int cols, const float* X, int64_t ldx, void* S, cudaStream_t st,
+            const uint32_t* active) {
+  const int ldS = (int)round_up(cols, 64);
+  int64_t cnt = plane_rows * ldS;
+  if (cnt <= 0) return;
+  k_slice3<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(rows, plane_rows, cols, ldS, X, ldx,
+                                                     static_cast<__nv_bfloat16*>(S), active);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* Y, int64_t ldy, double* C,
+             int64_t ldc, void* slices, size_t slice_bytes, cudaStream_t st, uint32_t* dev_err,
+             const uint32_t* active, bool reslice_x) {
+  if (p > 256 || q > 256 || m < 256 || !slices) return false;
+  const bool same = (X == Y && p == q && ldx == ldy);
+  const int npad = (int)round_up(q, 16);
+  const int NT = (p > 128) ? 2 : 1;
+  if (NT * npad > 512) return false;
+  if (same && npad > NT * 128) return false;
+  const int ldX = (int)round_up(p, 64), ldY = (int)round_up(q, 64);
+  const int64_t prow = round_up(m, G_KSUB);
+  const size_t need = (size_t)3 * prow * 2 * (ldX + (same ? 0 : ldY));
+  if (need > slice_bytes) return false;
+  __nv_bfloat16* SX = static_cast<__nv_bfloat16*>(slices);
+  __nv_bfloat16* SY = same ? SX : SX + (size_t)3 * prow * ldX;
+  CUtensorMap tX, tY;
+  if (!make_tmap_2d(&tX, SX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * prow, ldX, ldX, G_KSUB, 64)) return false;
+  if (!make_tmap_2d(&tY, SY, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * prow, ldY, ldY, G_KSUB, 64)) return false;
+  const int nybox = ldY / 64;
+  const uint32_t box = G_KSUB * 128;
+  const uint32_t stage_bytes = (uint32_t)(3 * NT * 2 + (same ? 0 : 3 * nybox)) * box;
+  const int nstages = (int)std::min<int64_t>(6, (200 * 1024) / stage_bytes);
+  if (nstages < 2) return false;
+  if (reslice_x || same) slice3(m, prow, p, X, ldx, SX, st, active);
+  if (!same) slice3(m, prow, q, Y, ldy, SY, st, active);
+  const size_t smem = 1024 + (size_t)nstages * stage_bytes + (2 * nstages + 1) * 8 + 16;
+  if (!g_sms_qr) g_sms_qr = num_sms();
+  const int ngroup = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, G_KSUB), g_sms_qr));
+  RPCA_CUDA_TRY(cudaMemset2DAsync(C, ldc * 8, 0, q * 8, p, st));
+  auto launch = [&](auto kern) {
+    RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<ngroup, G_THREADS, smem, st>>>(tX, tY, m, prow, p, q, npad, nybox, ngroup, nstages, stage_bytes, C,
+                                          ldc, dev_err, active);
+    RPCA_CUDA_TRY(cudaGetLastError());
+  };
+  if (NT == 2) {
+    if (same) launch(k_gram_bf16x3<2, true>);
+    else launch(k_gram_bf16x3<2, false>);
+  } else {
+    if (same) launch(k_gram_bf16x3<1, true>);
+    else launch(k_gram_bf16x3<1, false>);
+  }
+  count_launch();
+  return true;
+}
+
+bool apply_tc(int64_t m, int p, int q, const float* X, const float* Xlo, int64_t ldx, const double* M,
+              int64_t ldm, double alpha, double beta, float* Y, float* Ylo, int64_t ldy, float* scratch,
+              cudaStream_t st, uint32_t* dev_err, const uint32_t* active) {
+  if (p > 256 || q > 256 || m < 128) return false;
+  const int nq = (int)round_up(q, 16);
+  const int kb = (int)cdiv(p, 32);
+  const uint32_t mbox = (uint32_t)nq * 128;
+  const size_t mres = 2 * (size_t)kb * mbox;
+  const size_t stage = 2 * 128 * 128;
+  const size_t budget = 227 * 1024 - 1024 - 256 - kStageBytes;
+  if (mres + 2 * stage > budget || 2 * nq > 512) return false;
+  const int nstages = (int)std::min<size_t>(6, (budget - mres) / stage);
+  CUtensorMap tX, tXl;
+  if (!make_tmap_2d(&tX, X, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, m, p, ldx, 128, 32)) return false;
+  if (!make_tmap_2d(&tXl, Xlo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, m, p, ldx, 128, 32)) return false;
+  float* Mt = scratch;
+  float* Mtl = scratch + (size_t)p * q;
+  k_mt_split<<<(unsigned)cdiv((int64_t)p * q, 256), 256, 0, st>>>(p, q, M, ldm, Mt, Mtl);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  const size_t smem = 1024 + mres + (size_t)nstages * stage + (2 * nstages + 5) * 8 + 16 + kStageBytes;
+  RPCA_CUDA_TRY(cudaFuncSetAttribute(k_apply_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (!g_sms_qr) g_sms_qr = num_sms();
+  const int64_t ntile = cdiv(m, 128);
+  const unsigned grid = (unsigned)std::min<int64_t>(ntile, g_sms_qr);
+  k_apply_tf32x3<<<grid, A_THREADS, smem, st>>>(tX, tXl, m, p, q, nq, kb, nstages, Mt, Mtl, (float)alpha,
+                                                (float)beta, Y, ldy, Ylo, ldy, dev_err, active);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch(2);
+  return true;
+}
+
+}  // namespace rpca

@@ -70,6 +70,27 @@ void mat_add(int rows, int cols, const double* src, int64_t lds, double* dst, in
 void jacobi_svd(bool f64, int w, const double* B, double* S, double* Ub, double* W,
                 double* work, uint32_t* dev_err, cudaStream_t st);
 
+// ------------------------------------------- tensor-core tall products
+// FP32-accurate (TF32 x3) products on FP32 data carried with a remainder
+// array (x_lo = x - trunc_tf32(x), same layout and ld).  Return false when
+// the shape or alignment does not suit the tensor-core kernels.
+void split_lo(int64_t rows, int cols, const float* X, int64_t ldx, float* Xlo, int64_t ldl, cudaStream_t st);
+// C = X^T Y (FP64, overwritten); slices: device scratch of at least
+// 6 m (round_up(p,64) + round_up(q,64)) bytes.
+// reslice_x = false reuses the X slices of the previous call (same X).
+bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* Y, int64_t ldy, double* C,
+             int64_t ldc, void* slices, size_t slice_bytes, cudaStream_t st, uint32_t* dev_err,
+             const uint32_t* active = nullptr, bool reslice_x = true);
+// Y = beta Y + alpha X M (and Ylo); scratch: 2 p q floats of device memory.
+bool apply_tc(int64_t m, int p, int q, const float* X, const float* Xlo, int64_t ldx, const double* M,
+              int64_t ldm, double alpha, double beta, float* Y, float* Ylo, int64_t ldy, float* scratch,
+              cudaStream_t st, uint32_t* dev_err, const uint32_t* active = nullptr);
+
+// Y (m x q) = beta Y + alpha X M for small FP64 matrices, FP32 arithmetic
+// (for corrections whose own relative accuracy needs only FP32).
+void small_gemm_f32(int m, int p, int q, const double* X, int64_t ldx, const double* M, int64_t ldm,
+                    double alpha, double beta, double* Y, int64_t ldy, cudaStream_t st);
+
 // ----------------------------------------------------------------- small ops
 // s[j] = mean of (scaled) A[0:rows, j] in the compute type.
 void panel_mean(rpca_dtype dt, const void* A, int64_t lda, int64_t rows, int64_t n,

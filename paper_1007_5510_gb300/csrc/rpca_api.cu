@@ -103,25 +103,58 @@ struct QrScratch {
   double* Rinv = nullptr;  // l x l
   double* Racc = nullptr;  // l x l
   uint32_t* qf = nullptr;  // 4 words per block
+  float* mt = nullptr;     // 2 * 256 * 256 floats (tensor-core products)
+  void* slices = nullptr;  // BF16 slice scratch for tensor-core Grams
+  size_t slice_bytes = 0;
 };
+
+// Tensor-core (TF32 x3) tall products apply to FP32 data with at least this
+// many rows; Hlo is the remainder array of H (same layout).
+constexpr int64_t kTcMinRows = 8192;
+
+static void qr_gram(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, const void* Y, int64_t ldy,
+                    double* C, int64_t ldc, const QrScratch& s, cudaStream_t st, uint32_t* dev_err,
+                    const uint32_t* active = nullptr, bool reslice_x = true) {
+  if (!f64 && s.slices && m >= kTcMinRows &&
+      gram_tc(m, p, q, (const float*)X, ldx, (const float*)Y, ldy, C, ldc, s.slices, s.slice_bytes, st, dev_err,
+              active, reslice_x))
+    return;
+  gram(f64, m, p, q, X, ldx, Y, ldy, C, ldc, false, st, active);
+}
+
+static void qr_apply(bool f64, int64_t m, int p, int q, const void* X, const float* Xlo, int64_t ldx,
+                     const double* M, int64_t ldm, double alpha, double beta, void* Y, float* Ylo, int64_t ldy,
+                     const QrScratch& s, cudaStream_t st, uint32_t* dev_err, const uint32_t* active = nullptr) {
+  if (!f64 && Xlo && m >= kTcMinRows &&
+      apply_tc(m, p, q, (const float*)X, Xlo, ldx, M, ldm, alpha, beta, (float*)Y, Ylo, ldy, s.mt, st, dev_err,
+               active))
+    return;
+  gemm_xm(f64, m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy, st, active);
+  if (Ylo) split_lo(m, q, (const float*)Y, ldy, Ylo, ldy, st);
+}
 
 // E_out (w x w FP64, optional): Q^T Q - I of the stored Q, measured with an
 // FP64-accumulated Gram, so that consumers can apply the first-order
 // orthonormalisation Q (I - E/2) in FP64 without rewriting Q.
+// Hlo (optional, FP32 data only): remainder array of H, kept up to date.
 static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, double* R_out,
-                     double* E_out, const QrScratch& s, uint32_t* dev_err, cudaStream_t st) {
+                     double* E_out, const QrScratch& s, uint32_t* dev_err, cudaStream_t st,
+                     float* Hlo = nullptr) {
   const size_t es = f64 ? 8 : 4;
   const int w = nblk * l;
   const double piv_rel = f64 ? 1e-12 : 1e-5;
   const double shift_rel = f64 ? 1e-12 : 1e-5;
+  if (f64 || m < kTcMinRows) Hlo = nullptr;
+  if (Hlo) split_lo(m, w, (const float*)H, ld, Hlo, ld, st);
   if (R_out) RPCA_CUDA_TRY(cudaMemsetAsync(R_out, 0, (size_t)w * w * sizeof(double), st));
   for (int j = 0; j < nblk; ++j) {
     char* Hj = static_cast<char*>(H) + (size_t)j * l * es;
+    float* Hjlo = Hlo ? Hlo + (size_t)j * l : nullptr;
     const int jl = j * l;
     if (j > 0) {
       for (int rep = 0; rep < 2; ++rep) {
-        gram(f64, m, jl, l, H, ld, Hj, ld, s.C, l, false, st);
-        gemm_xm(f64, m, jl, l, H, ld, s.C, l, -1.0, 1.0, Hj, ld, st);
+        qr_gram(f64, m, jl, l, H, ld, Hj, ld, s.C, l, s, st, dev_err, nullptr, rep == 0);
+        qr_apply(f64, m, jl, l, H, Hlo, ld, s.C, l, -1.0, 1.0, Hj, Hjlo, ld, s, st, dev_err);
         if (R_out) mat_add(jl, l, s.C, l, R_out + jl, w, st);
       }
     }
@@ -129,17 +162,44 @@ static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, 
     if (R_out) set_identity(l, s.Racc, st);
     for (int pass = 0; pass < 4; ++pass) {
       const uint32_t* active = pass >= 2 ? qf + pass : nullptr;
-      gram(f64, m, l, l, Hj, ld, Hj, ld, s.Gm, l, false, st, active);
+      qr_gram(f64, m, l, l, Hj, ld, Hj, ld, s.Gm, l, s, st, dev_err, active);
       chol_small(l, s.Gm, l, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st);
-      gemm_xm(f64, m, l, l, Hj, ld, s.Rinv, l, 1.0, 0.0, Hj, ld, st, active);
+      qr_apply(f64, m, l, l, Hj, Hjlo, ld, s.Rinv, l, 1.0, 0.0, Hj, Hjlo, ld, s, st, dev_err, active);
       if (R_out) left_mul(l, s.Rk, s.Racc, st);
     }
     if (R_out) mat_add(l, l, s.Racc, l, R_out + (size_t)jl * w + jl, w, st);
   }
   if (E_out) {
-    gram(f64, m, w, w, H, ld, H, ld, E_out, w, false, st);
+    qr_gram(f64, m, w, w, H, ld, H, ld, E_out, w, s, st, dev_err);
     sub_identity(w, E_out, st);
   }
+}
+
+// Step 4 on T (n x w, ld w, compute type): T = Q_T R_T with Q_T from the
+// block QR (in place of T) and R_T = Q_T^T T_orig (FP64-accumulated Gram);
+// with E_T = Q_T^T Q_T - I the orthonormal basis is Q_T (I - E_T/2) to first
+// order and its triangular factor (I - E_T/2) R_T.  Then R_T' = Ub S W^T by
+// one-sided Jacobi.  Tc: n x w scratch (copy of T).
+static void svd_of_T(bool f64, int64_t n, int nblk, int l, void* T, void* Tc, float* Tlo, double* ET,
+                     double* RT, double* RT2, double* S, double* Ub, double* W, double* svdwork,
+                     const QrScratch& qs, uint32_t* dev_err, cudaStream_t st) {
+  const int w = nblk * l;
+  const size_t es = f64 ? 8 : 4;
+  RPCA_CUDA_TRY(cudaMemcpyAsync(Tc, T, (size_t)n * w * es, cudaMemcpyDeviceToDevice, st));
+  block_qr(f64, n, nblk, l, T, w, nullptr, ET, qs, dev_err, st, Tlo);
+  qr_gram(f64, n, w, w, T, w, Tc, w, RT, w, qs, st, dev_err);
+  copy_matrix(true, true, w, w, RT, w, RT2, w, st);
+  if (f64) gemm_xm(true, w, w, w, ET, w, RT, w, -0.5, 1.0, RT2, w, st);
+  else small_gemm_f32(w, w, w, ET, w, RT, w, -0.5, 1.0, RT2, w, st);
+  jacobi_svd(f64, w, RT2, S, Ub, W, svdwork, dev_err, st);
+}
+
+// Mk (w x k) = (I - E/2) M[:, :k]  (first-order orthonormalisation applied
+// to the small factor)
+static void fold_fixup(bool f64, int w, int k, const double* E, const double* M, double* Mk, cudaStream_t st) {
+  copy_matrix(true, true, w, k, M, w, Mk, k, st);
+  if (f64) gemm_xm(true, w, w, k, E, w, M, w, -0.5, 1.0, Mk, k, st);
+  else small_gemm_f32(w, w, k, E, w, M, w, -0.5, 1.0, Mk, k, st);
 }
 
 }  // namespace rpca
@@ -159,7 +219,7 @@ struct rpca_ctx {
   bool centered = false;
   std::string last_error;
 
-  DevBuf X, F, H, T, shift, corr, d, vtmp, q1, G64, small, err, At, tiles[2], work;
+  DevBuf X, F, H, T, Tc, shift, corr, d, vtmp, q1, G64, small, err, At, tiles[2], work, Hlo, Tlo, mt, slices;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   int64_t tile_rows = 0;
   QrScratch qs;
@@ -168,7 +228,8 @@ struct rpca_ctx {
   DevBuf T64;
   DevBuf outU, outV;
   // per-phase CUDA-event timing (RPCA_TIMING): phases 0..i are the fused
-  // passes' streaming kernels, i+1 the QR of H, i+2 the T pass, i+3 Steps 4-6
+  // passes' streaming kernels, i+1 the QR of H, i+2 the T pass, i+3 Step 4
+  // (QR of T and the small SVD), i+4 the products forming U and V
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   std::vector<double> phase_ms;
@@ -364,7 +425,8 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   }
   // Step 2: H = Q R (Q in place of H); Step 3: T = A_c^T Q
   c->tic(c->i + 1);
-  block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->E, c->qs, c->dev_err(), st);
+  block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->E, c->qs, c->dev_err(), st,
+           c->Hlo.as<float>());
   c->toc(c->i + 1);
   a.mode = MODE_T;
   a.p = c->w;
@@ -397,19 +459,21 @@ rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int
   // ((I + E_T/2) R_T) to first order; R_T' = Ub S W^T  =>  V~ = Q_T (I - E_T/2) Ub
   const int w = c->w, k = c->k;
   c->tic(c->i + 3);
-  block_qr(f64, c->n, c->i + 1, c->l, c->T.ptr, c->w, c->RT, c->ET, c->qs, c->dev_err(), st);
-  copy_matrix(true, true, w, w, c->RT, w, c->RT2, w, st);
-  gemm_xm(true, w, w, w, c->ET, w, c->RT, w, 0.5, 1.0, c->RT2, w, st);
-  jacobi_svd(f64, w, c->RT2, c->S, c->Ub, c->W, c->svdwork, c->dev_err(), st);
+  svd_of_T(f64, c->n, c->i + 1, c->l, c->T.ptr, c->Tc.ptr, c->Tlo.as<float>(), c->ET, c->RT, c->RT2, c->S, c->Ub,
+           c->W, c->svdwork, c->qs, c->dev_err(), st);
+  c->toc(c->i + 3);
+  c->tic(c->i + 4);
   // Steps 5-6: U = Q (I - E/2) W[:, :k], V = Q_T (I - E_T/2) Ub[:, :k]
   // (working orientation; swapped back when the problem was transposed)
-  copy_matrix(true, true, w, k, c->Ub, w, c->MV, k, st);
-  gemm_xm(true, w, w, k, c->ET, w, c->Ub, w, -0.5, 1.0, c->MV, k, st);
-  copy_matrix(true, true, w, k, c->W, w, c->MU, k, st);
-  gemm_xm(true, w, w, k, c->E, w, c->W, w, -0.5, 1.0, c->MU, k, st);
-  gemm_xm(f64, c->n, w, k, c->T.ptr, w, c->MV, k, 1.0, 0.0, c->outV.ptr, k, st);
-  gemm_xm(f64, c->m, w, k, c->H.ptr, w, c->MU, k, 1.0, 0.0, c->outU.ptr, k, st);
-  c->toc(c->i + 3);
+  fold_fixup(f64, w, k, c->ET, c->Ub, c->MV, st);
+  fold_fixup(f64, w, k, c->E, c->W, c->MU, st);
+  const bool tlo = c->Tlo.ptr && c->n >= kTcMinRows;
+  const bool hlo = c->Hlo.ptr && c->m >= kTcMinRows;
+  qr_apply(f64, c->n, w, k, c->T.ptr, tlo ? c->Tlo.as<float>() : nullptr, w, c->MV, k, 1.0, 0.0, c->outV.ptr,
+           nullptr, k, c->qs, st, c->dev_err());
+  qr_apply(f64, c->m, w, k, c->H.ptr, hlo ? c->Hlo.as<float>() : nullptr, w, c->MU, k, 1.0, 0.0, c->outU.ptr,
+           nullptr, k, c->qs, st, c->dev_err());
+  c->toc(c->i + 4);
   void* Uw = c->transposed ? V : U;
   int64_t ldUw = c->transposed ? ldv : ldu;
   void* Vw = c->transposed ? U : V;
@@ -469,6 +533,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->H.alloc((size_t)c->m * c->w * es);
   c->T.alloc((size_t)c->n * c->w * es);
   c->T64.alloc((size_t)c->n * c->w * sizeof(double));
+  c->Tc.alloc((size_t)c->n * c->w * es);
   c->shift.alloc((size_t)c->n * es);
   c->corr.alloc((size_t)256 * es);
   c->d.alloc((size_t)c->n * sizeof(double));
@@ -501,6 +566,18 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   RPCA_CUDA_TRY(cudaMemsetAsync(c->qs.qf, 0, 4 * 16 * sizeof(uint32_t), c->stream));
   if (c->transposed) c->At.alloc((size_t)c->m * c->n * dtype_bytes(p->dtype));
   if (!c->simt) c->work.alloc((size_t)c->m * round_up(c->w, 64) * 2 + 4096);
+  if (!c->f64) {
+    c->mt.alloc(2 * 256 * 256 * sizeof(float));
+    c->qs.mt = c->mt.as<float>();
+    if (!c->simt) {
+      c->Hlo.alloc((size_t)c->m * c->w * sizeof(float));
+      if (c->n >= kTcMinRows) c->Tlo.alloc((size_t)c->n * c->w * sizeof(float));
+      const size_t sb = (size_t)6 * (round_up(std::max(c->m, c->n), 32)) * (2 * round_up(c->w, 64));
+      c->slices.alloc(sb);
+      c->qs.slices = c->slices.ptr;
+      c->qs.slice_bytes = sb;
+    }
+  }
   if (c->host_a) {
     const size_t ab = dtype_bytes(p->dtype);
     int64_t tr = p->tile_rows > 0 ? p->tile_rows : std::max<int64_t>(128, (int64_t)((1ull << 30) / (c->n * ab)));
@@ -521,7 +598,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   RPCA_CUDA_TRY(cudaMemcpy(c->G64.ptr, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
   c->timing = (p->flags & RPCA_TIMING) != 0;
   if (c->timing) {
-    const int nph = c->i + 4;
+    const int nph = c->i + 5;
     c->ev.assign(2 * nph, nullptr);
     for (auto& e : c->ev) RPCA_CUDA_TRY(cudaEventCreate(&e));
     c->phase_ms.assign(nph, 0.0);
@@ -704,11 +781,72 @@ rpca_status rpca_op_qr(int32_t f64, int64_t m, int32_t nblk, int32_t l, void* H,
     qs.qf = reinterpret_cast<uint32_t*>(s);
     uint32_t* err = qs.qf + 4 * nblk;
     RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
-    block_qr(f64 != 0, m, nblk, l, H, ld, nullptr, nullptr, qs, err, st);
+    DevBuf hlo, mt, sl;
+    if (!f64 && m >= kTcMinRows) {
+      hlo.alloc((size_t)m * ld * sizeof(float));
+      mt.alloc(2 * 256 * 256 * sizeof(float));
+      qs.mt = mt.as<float>();
+      sl.alloc((size_t)6 * round_up(m, 32) * 2 * round_up((int64_t)nblk * l, 64));
+      qs.slices = sl.ptr;
+      qs.slice_bytes = sl.bytes;
+    }
+    block_qr(f64 != 0, m, nblk, l, H, ld, nullptr, nullptr, qs, err, st, hlo.as<float>());
     uint32_t flags = 0;
     RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     RPCA_CUDA_TRY(cudaStreamSynchronize(st));
     if (flags & DEV_ERR_BREAKDOWN) return RPCA_EBREAKDOWN;
+    return RPCA_OK;
+  });
+}
+
+rpca_status rpca_op_gram(int64_t m, int32_t p, int32_t q, const float* X, int64_t ldx, const float* Y,
+                          int64_t ldy, double* C, int64_t ldc, int32_t kernel, void* stream) {
+  return guarded(nullptr, [&] {
+    check_device();
+    if (m < 1 || p < 1 || q < 1 || p > 256 || q > 256 || ldx < p || ldy < q || ldc < q) throw Invalid("bad sizes");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevBuf xl, yl, err;
+    err.alloc(64 * sizeof(uint32_t));
+    RPCA_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, 64 * sizeof(uint32_t), st));
+    bool done = false;
+    if (kernel != 1) {
+      xl.alloc((size_t)6 * round_up(m, 32) * (round_up(p, 64) + round_up(q, 64)));
+      done = gram_tc(m, p, q, X, ldx, Y, ldy, C, ldc, xl.ptr, xl.bytes, st, err.as<uint32_t>());
+      if (!done && kernel == 2) throw Invalid("tensor-core Gram unsupported for this shape");
+    }
+    if (!done) gram(false, m, p, q, X, ldx, Y, ldy, C, ldc, false, st);
+    uint32_t flags = 0;
+    RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags & DEV_ERR_TIMEOUT) return RPCA_ETIMEOUT;
+    return RPCA_OK;
+  });
+}
+
+rpca_status rpca_op_apply(int64_t m, int32_t p, int32_t q, const float* X, int64_t ldx, const double* M,
+                          int64_t ldm, double alpha, double beta, float* Y, int64_t ldy, int32_t kernel,
+                          void* stream) {
+  return guarded(nullptr, [&] {
+    check_device();
+    if (m < 1 || p < 1 || q < 1 || p > 256 || q > 256 || ldx < p || ldy < q || ldm < q) throw Invalid("bad sizes");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevBuf xl, err, mt;
+    err.alloc(64 * sizeof(uint32_t));
+    mt.alloc(2 * 256 * 256 * sizeof(float));
+    RPCA_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, 64 * sizeof(uint32_t), st));
+    bool done = false;
+    if (kernel != 1) {
+      xl.alloc((size_t)m * ldx * sizeof(float));
+      split_lo(m, p, X, ldx, xl.as<float>(), ldx, st);
+      done = apply_tc(m, p, q, X, xl.as<float>(), ldx, M, ldm, alpha, beta, Y, nullptr, ldy, mt.as<float>(), st,
+                      err.as<uint32_t>());
+      if (!done && kernel == 2) throw Invalid("tensor-core apply unsupported for this shape");
+    }
+    if (!done) gemm_xm(false, m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy, st);
+    uint32_t flags = 0;
+    RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags & DEV_ERR_TIMEOUT) return RPCA_ETIMEOUT;
     return RPCA_OK;
   });
 }
@@ -745,13 +883,20 @@ rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w, const void* T, 
     qs.qf = reinterpret_cast<uint32_t*>(s);
     uint32_t* err = qs.qf + 4 * nblk;
     RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
-    block_qr(f64 != 0, n, nblk, l, Tq.ptr, w, RT, ET, qs, err, st);
-    copy_matrix(true, true, w, w, RT, w, RT2, w, st);
-    gemm_xm(true, w, w, w, ET, w, RT, w, 0.5, 1.0, RT2, w, st);
-    jacobi_svd(f64 != 0, w, RT2, S, Ub, W, work, err, st);
-    copy_matrix(true, true, w, w, Ub, w, MV, w, st);
-    gemm_xm(true, w, w, w, ET, w, Ub, w, -0.5, 1.0, MV, w, st);
-    gemm_xm(f64 != 0, n, w, w, Tq.ptr, w, MV, w, 1.0, 0.0, Vt, ldv, st);
+    DevBuf Tc, tlo, mt, sl;
+    Tc.alloc((size_t)n * w * es);
+    if (!f64 && n >= kTcMinRows) {
+      tlo.alloc((size_t)n * w * sizeof(float));
+      mt.alloc(2 * 256 * 256 * sizeof(float));
+      qs.mt = mt.as<float>();
+      sl.alloc((size_t)6 * round_up(n, 32) * 2 * round_up(w, 64));
+      qs.slices = sl.ptr;
+      qs.slice_bytes = sl.bytes;
+    }
+    svd_of_T(f64 != 0, n, nblk, l, Tq.ptr, Tc.ptr, tlo.as<float>(), ET, RT, RT2, S, Ub, W, work, qs, err, st);
+    fold_fixup(f64 != 0, w, w, ET, Ub, MV, st);
+    qr_apply(f64 != 0, n, w, w, Tq.ptr, (!f64 && n >= kTcMinRows) ? tlo.as<float>() : nullptr, w, MV, w, 1.0, 0.0,
+             Vt, nullptr, ldv, qs, st, err);
     uint32_t flags = 0;
     RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     RPCA_CUDA_TRY(cudaStreamSynchronize(st));

@@ -22,7 +22,7 @@ CENTER, HOST_A, SIMT, TIMING = 0x1, 0x2, 0x4, 0x8
 EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
            "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
            "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
-           "rpca_phase_times"]
+           "rpca_phase_times", "rpca_op_gram", "rpca_op_apply"]
 
 
 class RpcaError(RuntimeError):
@@ -88,6 +88,11 @@ def load_library(path=None):
     lib.rpca_kernel_launches.restype = u64
     lib.rpca_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(i32)]
     lib.rpca_phase_times.restype = i32
+    lib.rpca_op_gram.argtypes = [i64, i32, i32, vp, i64, vp, i64, vp, i64, i32, vp]
+    lib.rpca_op_gram.restype = st
+    lib.rpca_op_apply.argtypes = [i64, i32, i32, vp, i64, vp, i64, ctypes.c_double, ctypes.c_double, vp, i64,
+                                  i32, vp]
+    lib.rpca_op_apply.restype = st
     if path is None:
         _lib = lib
     return lib
@@ -272,6 +277,30 @@ def qr_inplace(H, nblk, l):
     f64 = 1 if H.dtype == torch.float64 else 0
     _check(load_library().rpca_op_qr(f64, H.shape[0], nblk, l, _ptr(H), H.stride(0), _stream_ptr()))
     return H
+
+
+def gram(X, Y=None, kernel=0):
+    """C = X^T Y (FP64) for FP32 device matrices."""
+    torch = _torch()
+    Y = X if Y is None else Y
+    m, pp = X.shape
+    q = Y.shape[1]
+    C = torch.empty(pp, q, dtype=torch.float64, device=X.device)
+    _check(load_library().rpca_op_gram(m, pp, q, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), _ptr(C),
+                                       C.stride(0), kernel, _stream_ptr()))
+    return C
+
+
+def apply(X, M, Y=None, alpha=1.0, beta=0.0, kernel=0):
+    """Y = beta Y + alpha X M (X FP32, M FP64)."""
+    torch = _torch()
+    m, pp = X.shape
+    q = M.shape[1]
+    if Y is None:
+        Y = torch.zeros(m, q, dtype=torch.float32, device=X.device)
+    _check(load_library().rpca_op_apply(m, pp, q, _ptr(X), X.stride(0), _ptr(M), M.stride(0), alpha, beta,
+                                        _ptr(Y), Y.stride(0), kernel, _stream_ptr()))
+    return Y
 
 
 def small_svd(T):
