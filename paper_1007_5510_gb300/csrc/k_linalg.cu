@@ -5,6 +5,8 @@
 //           triangular factor;
 //   Steps 5-6 and the centring corrections: tall x small products.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -171,10 +173,14 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
     return;
   }
   if (tid == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < p; ++i) mx = fmax(mx, G[(int64_t)i * ldg + i]);
-    dmax = mx;
+    dmax = 0.0;
     if (pass == 0) qf[0] = 0u;
+  }
+  __syncthreads();
+  for (int i = tid; i < p; i += blockDim.x) {
+    // diagonal entries are non-negative: their bit patterns order like integers
+    atomicMax(reinterpret_cast<unsigned long long*>(&dmax),
+              (unsigned long long)__double_as_longlong(fmax(G[(int64_t)i * ldg + i], 0.0)));
   }
   __syncthreads();
   bool shifted = false;
@@ -193,14 +199,19 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
         if (tid == 0) fail = 1;
         break;
       }
-      double rkk = sqrt(d);
+      const double rkk = sqrt(d);
+      const double irkk = 1.0 / rkk;
       __syncthreads();
-      for (int j = k + tid; j < p; j += blockDim.x) R[k * p + j] = (j == k) ? rkk : R[k * p + j] / rkk;
+      for (int j = k + tid; j < p; j += blockDim.x) R[k * p + j] = (j == k) ? rkk : R[k * p + j] * irkk;
       __syncthreads();
-      const int nt = p - k - 1;
-      for (int e = tid; e < nt * nt; e += blockDim.x) {
-        int i = k + 1 + e / nt, j = k + 1 + e % nt;
-        if (j >= i) R[i * p + j] -= R[k * p + i] * R[k * p + j];
+      // trailing update of the upper triangle, 16 x 16 thread tile (no
+      // index division in the loop)
+      {
+        const int ty = tid >> 4, tx = tid & 15;
+        for (int i = k + 1 + ty; i < p; i += 16) {
+          const double rki = R[k * p + i];
+          for (int j = i + tx; j < p; j += 16) R[i * p + j] -= rki * R[k * p + j];
+        }
       }
       __syncthreads();
     }
@@ -230,12 +241,22 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
   // Rinv = R^-1: rows from the bottom up, all columns in parallel
   for (int e = tid; e < p * p; e += blockDim.x) Rinv[e] = 0.0;
   __syncthreads();
-  for (int i = p - 1; i >= 0; --i) {
-    const double rii = R[i * p + i];
-    for (int c = i + tid; c < p; c += blockDim.x) {
-      double sum = (i == c) ? 1.0 : 0.0;
-      for (int j = i + 1; j <= c; ++j) sum -= R[i * p + j] * Rinv[j * p + c];
-      Rinv[i * p + c] = sum / rii;
+  // Rinv = R^-1 by right-looking back substitution on all columns at once:
+  // step k (from the bottom): row k of Rinv is final after scaling by
+  // 1/R[k][k]; then rows 0..k-1 receive -R[i][k] * row k.  Every update of a
+  // step is independent (no long dependent FP64 chains).
+  __shared__ double rdiag[256];
+  for (int i = tid; i < p && i < 256; i += blockDim.x) rdiag[i] = 1.0 / R[i * p + i];
+  for (int e = tid; e < p * p; e += blockDim.x) Rinv[e] = (e / p == e % p) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = p - 1; k >= 0; --k) {
+    const double rk = p <= 256 ? rdiag[k] : 1.0 / R[k * p + k];
+    for (int c = k + tid; c < p; c += blockDim.x) Rinv[k * p + c] *= rk;
+    __syncthreads();
+    const int ty = tid >> 4, tx = tid & 15;
+    for (int i = ty; i < k; i += 16) {
+      const double rik = R[i * p + k];
+      for (int c = k + tx; c < p; c += 16) Rinv[i * p + c] -= rik * Rinv[k * p + c];
     }
     __syncthreads();
   }
@@ -282,14 +303,31 @@ __global__ void k_mat_add(int rows, int cols, const double* __restrict__ src, in
 
 // ------------------------------------------------------------------ Jacobi
 // One-sided (Hestenes) Jacobi on the columns of B (w x w), one CTA of 1024
-// threads: rounds of a round-robin tournament, one warp per column pair.
-// Columns are stored contiguously (Bc[c*w + r] = B[r][c]) and the rotations
-// are accumulated in J (Jc[c*w + r] = W[r][c]); both live in shared memory
-// when they fit (B alone otherwise, J in global memory).
+// threads: rounds of a round-robin tournament; each warp handles up to PPW
+// column pairs of a round at once (interleaved for instruction-level
+// parallelism).  Columns are stored contiguously (Bc[c*w + r] = B[r][c]) and
+// the rotations are accumulated in J (Jc[c*w + r] = W[r][c]); B lives in
+// shared memory when it fits, J too when both fit.  On exit the columns y_j
+// of Bc are B W with W = J orthogonal.
+constexpr int PPW = 2;
+__device__ __forceinline__ void rot_params(float al, float be, float ga, float& c, float& s) {
+  const float zeta = __fdividef(be - al, 2.f * ga);
+  const float t = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+  c = rsqrtf(fmaf(t, t, 1.f));
+  s = c * t;
+}
+__device__ __forceinline__ void rot_params(double al, double be, double ga, double& c, double& s) {
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = c * t;
+}
 template <typename TJ>
 __global__ void __launch_bounds__(1024)
-k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc_g, TJ* __restrict__ Jc_g, double tol,
+k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc_g, TJ* __restrict__ Jc_g, double tol_in,
          int max_sweeps, uint32_t* dev_err) {
+  const TJ tol = TJ(tol_in);   // no FP64 in the inner loop of the FP32 variant
+  const long long t_start = clock64();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const size_t mat = (size_t)w * w * sizeof(TJ);
@@ -303,7 +341,21 @@ k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc_g, TJ* __restr
     Jw[e] = TJ(r == c ? 1 : 0);
   }
   __shared__ float off_max;
+  __shared__ double nmax2;
+  if (tid == 0) nmax2 = 0.0;
   __syncthreads();
+  // largest column norm^2: couplings below the rounding noise it induces
+  // (u * |b_max| * |b|) are not resolvable and do not trigger rotations
+  for (int c = warp; c < w; c += nw) {
+    TJ s2 = 0;
+    for (int r = lane; r < w; r += 32) s2 = fma(Bw[(int64_t)c * w + r], Bw[(int64_t)c * w + r], s2);
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0)
+      atomicMax(reinterpret_cast<unsigned long long*>(&nmax2), (unsigned long long)__double_as_longlong((double)s2));
+  }
+  __syncthreads();
+  const TJ unit = sizeof(TJ) == 8 ? TJ(1.11e-16) : TJ(5.96e-8);
+  const TJ noise = TJ(4) * unit * TJ(sqrt(nmax2));
   const int N = w + (w & 1);
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
@@ -311,40 +363,79 @@ k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc_g, TJ* __restr
     __syncthreads();
     float local_off = 0.f;
     for (int rnd = 0; rnd < N - 1; ++rnd) {
-      for (int pi = warp; pi < N / 2; pi += nw) {
-        int a, b;
-        if (pi == 0) { a = N - 1; b = rnd; }
-        else { a = (rnd + pi) % (N - 1); b = (rnd - pi + N - 1) % (N - 1); }
-        if (a >= w || b >= w) continue;
-        const int pcol = min(a, b), qcol = max(a, b);
-        TJ* bp = Bw + (int64_t)pcol * w;
-        TJ* bq = Bw + (int64_t)qcol * w;
-        TJ al = 0, be = 0, ga = 0;
+      for (int pb = warp; pb < N / 2; pb += nw * PPW) {
+        TJ* bp[PPW];
+        TJ* bq[PPW];
+        int pc[PPW], qc[PPW];
+        bool live[PPW];
+        TJ al[PPW], be[PPW], ga[PPW];
+#pragma unroll
+        for (int u = 0; u < PPW; ++u) {
+          const int pi = pb + u * nw;
+          int a = 0, b = 0;
+          live[u] = pi < N / 2;
+          if (live[u]) {
+            if (pi == 0) { a = N - 1; b = rnd; }
+            else {
+              a = rnd + pi;                      // rnd, pi < N - 1
+              if (a >= N - 1) a -= N - 1;
+              b = rnd - pi;
+              if (b < 0) b += N - 1;
+            }
+            live[u] = (a < w && b < w);
+          }
+          const int pcol = live[u] ? min(a, b) : 0, qcol = live[u] ? max(a, b) : 1;
+          pc[u] = pcol;
+          qc[u] = qcol;
+          bp[u] = Bw + (int64_t)pcol * w;
+          bq[u] = Bw + (int64_t)qcol * w;
+          al[u] = be[u] = ga[u] = TJ(0);
+        }
         for (int r = lane; r < w; r += 32) {
-          TJ x = bp[r], y = bq[r];
-          al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+#pragma unroll
+          for (int u = 0; u < PPW; ++u) {
+            if (!live[u]) continue;
+            TJ x = bp[u][r], y = bq[u][r];
+            al[u] = fma(x, x, al[u]); be[u] = fma(y, y, be[u]); ga[u] = fma(x, y, ga[u]);
+          }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+#pragma unroll
+          for (int u = 0; u < PPW; ++u) {
+            al[u] += __shfl_xor_sync(0xffffffffu, al[u], o);
+            be[u] += __shfl_xor_sync(0xffffffffu, be[u], o);
+            ga[u] += __shfl_xor_sync(0xffffffffu, ga[u], o);
+          }
         }
-        TJ nrm = sqrt(al * be);
-        if (nrm == TJ(0) || fabs(ga) <= tol * nrm) continue;
-        local_off = fmaxf(local_off, (float)(fabs(ga) / nrm));
-        TJ zeta = (be - al) / (TJ(2) * ga);
-        TJ t = (zeta >= 0 ? TJ(1) : TJ(-1)) / (fabs(zeta) + sqrt(TJ(1) + zeta * zeta));
-        TJ c = TJ(1) / sqrt(TJ(1) + t * t), s = c * t;
-        TJ* jp = Jw + (int64_t)pcol * w;
-        TJ* jq = Jw + (int64_t)qcol * w;
+        TJ cs[PPW], sn[PPW];
+        bool rot[PPW];
+#pragma unroll
+        for (int u = 0; u < PPW; ++u) {
+          const TJ nrm = sqrt(al[u] * be[u]);
+          rot[u] = live[u] && nrm > TJ(0) && fabs(ga[u]) > tol * nrm &&
+                   fabs(ga[u]) > noise * sqrt(fmax(al[u], be[u]));
+          cs[u] = TJ(1); sn[u] = TJ(0);
+          if (rot[u]) {
+            // any t gives an exactly orthogonal rotation through c, s below;
+            // an approximate t only slows convergence negligibly
+            local_off = fmaxf(local_off, (float)fabs(ga[u]) / (float)nrm);
+            rot_params(al[u], be[u], ga[u], cs[u], sn[u]);
+          }
+        }
         for (int r = lane; r < w; r += 32) {
-          TJ x = bp[r], y = bq[r];
-          bp[r] = c * x - s * y;
-          bq[r] = s * x + c * y;
-          TJ u = jp[r], v = jq[r];
-          jp[r] = c * u - s * v;
-          jq[r] = s * u + c * v;
+#pragma unroll
+          for (int u = 0; u < PPW; ++u) {
+            if (!rot[u]) continue;
+            TJ x = bp[u][r], y = bq[u][r];
+            bp[u][r] = cs[u] * x - sn[u] * y;
+            bq[u][r] = sn[u] * x + cs[u] * y;
+            TJ* jp = Jw + (int64_t)pc[u] * w;
+            TJ* jq = Jw + (int64_t)qc[u] * w;
+            TJ g = jp[r], h = jq[r];
+            jp[r] = cs[u] * g - sn[u] * h;
+            jq[r] = sn[u] * g + cs[u] * h;
+          }
         }
       }
       __syncthreads();
@@ -355,7 +446,10 @@ k_jacobi(int w, const double* __restrict__ B, TJ* __restrict__ Bc_g, TJ* __restr
     __syncthreads();
   }
   if (tid == 0 && sweep >= max_sweeps) atomicOr(dev_err, DEV_ERR_JACOBI);
-  if (tid == 0) dev_err[8] = (uint32_t)sweep;   // sweeps used (diagnostics)
+  if (tid == 0) {
+    dev_err[8] = (uint32_t)sweep;   // sweeps used (diagnostics)
+    dev_err[9] = (uint32_t)((clock64() - t_start) >> 10);   // kilocycles (diagnostics)
+  }
   if (j_smem)
     for (int e = tid; e < w * w; e += blockDim.x) Jc_g[e] = Jw[e];
 }
@@ -383,8 +477,9 @@ __global__ void k_jacobi_w(int w, const TJ* __restrict__ Jc, double* __restrict_
   for (int r = threadIdx.x; r < w; r += blockDim.x) W[(int64_t)r * w + c] = (double)Jc[(int64_t)c * w + r] * inv;
 }
 
-// B64 = R W already formed (row-major).  Singular values = column norms,
-// sorted descending; Ub = B64 / sigma; W permuted alike.  One CTA.
+// B64 = B W (W with unit columns).  Singular values = column norms of B64
+// (second-order accurate in the error of W), sorted descending; Ub = B64 /
+// sigma; W permuted alike.  One CTA.
 __global__ void k_svd_finish(int w, const double* __restrict__ B64, const double* __restrict__ Win,
                              double* __restrict__ S, double* __restrict__ Ub, double* __restrict__ W) {
   extern __shared__ double sig[];
@@ -411,6 +506,8 @@ __global__ void k_svd_finish(int w, const double* __restrict__ B64, const double
   }
   for (int c = threadIdx.x; c < w; c += blockDim.x) S[pos[c]] = sig[c];
 }
+
+
 
 // Y = beta Y + alpha X M, FP64 storage, FP32 arithmetic; one thread per
 // output element.
@@ -631,8 +728,9 @@ void mat_add(int rows, int cols, const double* src, int64_t lds, double* dst, in
   count_launch();
 }
 
-void jacobi_svd(bool f64, int w, const double* B, double* S, double* Ub, double* W, double* work,
+void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub, double* W, double* work,
                 uint32_t* dev_err, cudaStream_t st) {
+  (void)kk;   // all w triplets are formed
   // work layout (doubles): Bc [w*w], Jc [w*w], W0 [w*w], B64 [w*w]
   double* Bc = work;
   double* Jc = work + (size_t)w * w;
@@ -665,6 +763,12 @@ void jacobi_svd(bool f64, int w, const double* B, double* S, double* Ub, double*
   k_svd_finish<<<1, 256, smem, st>>>(w, B64, W0, S, Ub, W);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
+  if (getenv("RPCA_DEBUG")) {
+    uint32_t sw[2] = {0, 0};
+    cudaMemcpyAsync(sw, dev_err + 8, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    fprintf(stderr, "[rpca] jacobi w=%d sweeps=%u kcycles=%u\n", w, sw[0], sw[1]);
+  }
 }
 
 void small_gemm_f32(int m, int p, int q, const double* X, int64_t ldx, const double* M, int64_t ldm,

@@ -52,20 +52,27 @@ __global__ void k_split_lo(int64_t rows, int cols, const float* __restrict__ X, 
 __global__ void k_slice3(int64_t rows, int64_t plane_rows, int cols, int ldS, const float* __restrict__ X,
                          int64_t ldx, __nv_bfloat16* __restrict__ S, const uint32_t* __restrict__ active) {
   if (active && *active == 0u) return;
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= plane_rows * ldS) return;
-  int64_t r = e / ldS;
-  int c = (int)(e % ldS);
-  float x = (c < cols && r < rows) ? X[r * ldx + c] : 0.f;
-  __nv_bfloat16 b1 = __float2bfloat16_rn(x);
-  float r1 = x - __bfloat162float(b1);
-  __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
-  float r2 = r1 - __bfloat162float(b2);
-  __nv_bfloat16 b3 = __float2bfloat16_rn(r2);
+  // four consecutive columns per thread, 8-byte stores per plane
+  const int64_t e4 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per_row = ldS / 4;
+  if (e4 >= plane_rows * per_row) return;
+  const int64_t r = e4 / per_row;
+  const int c0 = (int)(e4 % per_row) * 4;
+  __nv_bfloat16 o1[4], o2[4], o3[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = c0 + q;
+    float x = (c < cols && r < rows) ? X[r * ldx + c] : 0.f;
+    o1[q] = __float2bfloat16_rn(x);
+    float r1 = x - __bfloat162float(o1[q]);
+    o2[q] = __float2bfloat16_rn(r1);
+    o3[q] = __float2bfloat16_rn(r1 - __bfloat162float(o2[q]));
+  }
   const int64_t plane = plane_rows * ldS;
-  S[e] = b1;
-  S[plane + e] = b2;
-  S[2 * plane + e] = b3;
+  const int64_t e = r * ldS + c0;
+  *reinterpret_cast<uint2*>(S + e) = *reinterpret_cast<uint2*>(o1);
+  *reinterpret_cast<uint2*>(S + plane + e) = *reinterpret_cast<uint2*>(o2);
+  *reinterpret_cast<uint2*>(S + 2 * plane + e) = *reinterpret_cast<uint2*>(o3);
 }
 
 // A operand: X columns [t*128, t*128+128) of each slice (MN-major, 2 boxes of
@@ -329,11 +336,21 @@ k_apply_tf32x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         }
         __syncwarp();
         const int c = c32 + lane;
+        float yold[32];
+        if (beta != 0.f) {
+          // issue all loads of the old values before any store
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t r = r0 + rr;
+            yold[rr] = (r < m && c < q) ? Y[r * ldy + c] : 0.f;
+          }
+        }
+#pragma unroll 4
         for (int rr = 0; rr < 32; ++rr) {
           const int64_t r = r0 + rr;
           if (r < m && c < q) {
             float y = alpha * stg[rr * 33 + lane];
-            if (beta != 0.f) y += beta * Y[r * ldy + c];
+            if (beta != 0.f) y += beta * yold[rr];
             Y[r * ldy + c] = y;
             if (Ylo) Ylo[r * ldyl + c] = y - tf32_trunc(y);
           }
@@ -385,7 +402,7 @@ void split_lo(int64_t rows, int cols, const float* X, int64_t ldx, float* Xlo, i
 void slice3(int64_t rows, int64_t plane_rows, int cols, const float* X, int64_t ldx, void* S, cudaStream_t st,
             const uint32_t* active) {
   const int ldS = (int)round_up(cols, 64);
-  int64_t cnt = plane_rows * ldS;
+  int64_t cnt = plane_rows * ldS / 4;
   if (cnt <= 0) return;
   k_slice3<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(rows, plane_rows, cols, ldS, X, ldx,
                                                      static_cast<__nv_bfloat16*>(S), active);

@@ -66,8 +66,9 @@ void mat_add(int rows, int cols, const double* src, int64_t lds, double* dst, in
              cudaStream_t st);
 // One-sided Jacobi SVD of a w x w FP64 matrix B (row-major): B = Ub S W^T,
 // S descending.  FP32 sweeps with an FP64 finish (f64 = false) or FP64.
-// work: 4 w^2 doubles.
-void jacobi_svd(bool f64, int w, const double* B, double* S, double* Ub, double* W,
+// Singular triplets of B (w x w FP64 row-major): S descending, Ub, W
+// (row-major w x w, ld w); callers use the leading kk.  work: 4 w^2 doubles.
+void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub, double* W,
                 double* work, uint32_t* dev_err, cudaStream_t st);
 
 // ------------------------------------------- tensor-core tall products

@@ -180,7 +180,7 @@ static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, 
 // with E_T = Q_T^T Q_T - I the orthonormal basis is Q_T (I - E_T/2) to first
 // order and its triangular factor (I - E_T/2) R_T.  Then R_T' = Ub S W^T by
 // one-sided Jacobi.  Tc: n x w scratch (copy of T).
-static void svd_of_T(bool f64, int64_t n, int nblk, int l, void* T, void* Tc, float* Tlo, double* ET,
+static void svd_of_T(bool f64, int64_t n, int nblk, int l, int kk, void* T, void* Tc, float* Tlo, double* ET,
                      double* RT, double* RT2, double* S, double* Ub, double* W, double* svdwork,
                      const QrScratch& qs, uint32_t* dev_err, cudaStream_t st) {
   const int w = nblk * l;
@@ -191,7 +191,7 @@ static void svd_of_T(bool f64, int64_t n, int nblk, int l, void* T, void* Tc, fl
   copy_matrix(true, true, w, w, RT, w, RT2, w, st);
   if (f64) gemm_xm(true, w, w, w, ET, w, RT, w, -0.5, 1.0, RT2, w, st);
   else small_gemm_f32(w, w, w, ET, w, RT, w, -0.5, 1.0, RT2, w, st);
-  jacobi_svd(f64, w, RT2, S, Ub, W, svdwork, dev_err, st);
+  jacobi_svd(f64, w, kk, RT2, S, Ub, W, svdwork, dev_err, st);
 }
 
 // Mk (w x k) = (I - E/2) M[:, :k]  (first-order orthonormalisation applied
@@ -459,7 +459,7 @@ rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int
   // ((I + E_T/2) R_T) to first order; R_T' = Ub S W^T  =>  V~ = Q_T (I - E_T/2) Ub
   const int w = c->w, k = c->k;
   c->tic(c->i + 3);
-  svd_of_T(f64, c->n, c->i + 1, c->l, c->T.ptr, c->Tc.ptr, c->Tlo.as<float>(), c->ET, c->RT, c->RT2, c->S, c->Ub,
+  svd_of_T(f64, c->n, c->i + 1, c->l, c->k, c->T.ptr, c->Tc.ptr, c->Tlo.as<float>(), c->ET, c->RT, c->RT2, c->S, c->Ub,
            c->W, c->svdwork, c->qs, c->dev_err(), st);
   c->toc(c->i + 3);
   c->tic(c->i + 4);
@@ -893,7 +893,7 @@ rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w, const void* T, 
       qs.slices = sl.ptr;
       qs.slice_bytes = sl.bytes;
     }
-    svd_of_T(f64 != 0, n, nblk, l, Tq.ptr, Tc.ptr, tlo.as<float>(), ET, RT, RT2, S, Ub, W, work, qs, err, st);
+    svd_of_T(f64 != 0, n, nblk, l, w, Tq.ptr, Tc.ptr, tlo.as<float>(), ET, RT, RT2, S, Ub, W, work, qs, err, st);
     fold_fixup(f64 != 0, w, w, ET, Ub, MV, st);
     qr_apply(f64 != 0, n, w, w, Tq.ptr, (!f64 && n >= kTcMinRows) ? tlo.as<float>() : nullptr, w, MV, w, 1.0, 0.0,
              Vt, nullptr, ldv, qs, st, err);
