@@ -205,6 +205,42 @@ uint64_t rpca_kernel_launches(void);
  * without RPCA_TIMING. */
 int32_t rpca_phase_times(rpca_ctx* c, double* ms, int32_t cap, int32_t* runs);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free fused pass.  The paper has no counterpart to this call: */
+/* it exists for callers that must not allocate device memory per call.   */
+/* ---------------------------------------------------------------------- */
+
+/* Limits of the fixed scratch: X^T in BF16 for up to RPCA_NOALLOC_MAX_P
+ * columns and RPCA_NOALLOC_MAX_N rows, then 64 error words (512 KiB + 256 B
+ * per device in total); 4096 is also the widest A the tensor-core fused
+ * pass takes. */
+#define RPCA_NOALLOC_MAX_N 4096
+#define RPCA_NOALLOC_MAX_P 64
+#define RPCA_NOALLOC_SCRATCH_BYTES (64 * 4096 * 2 + 256)
+
+/* The tensor-core fused pass of rpca_op_fused_pass (dtype RPCA_BF16,
+ * kernel 2, no shift or column scale) with its scratch in a fixed device
+ * array of RPCA_NOALLOC_SCRATCH_BYTES instead of a per-call allocation;
+ * the call allocates no device memory.
+ *   H[:, 0:p] = A X  (m x p FP32, ldh),  F = A^T bf16(H)  (n x p FP32, ldf;
+ *   overwritten; skipped if F is NULL)
+ * A: m x n BF16 row-major (lda elements; base 16-byte aligned, lda*2 a
+ * multiple of 16).  X: n x p FP32 (ldx).  All device memory, owned by the
+ * caller.  Returns RPCA_EINVAL for n > RPCA_NOALLOC_MAX_N,
+ * p > RPCA_NOALLOC_MAX_P, bad sizes, NULL A/X/H or a layout the tensor-core
+ * pass does not take; RPCA_ENODEV without a GPU; RPCA_ETIMEOUT if a bounded
+ * wait inside the kernel expired.  Synchronises `stream`.
+ * The scratch address is looked up (cudaGetSymbolAddress) on the first
+ * call on each device, with that device current: make that first call
+ * before any stream capture.  The error words are cleared on `stream` at
+ * the start of every call.  Calls that overlap in time on one device (other
+ * streams or host threads) share the scratch and race: serialise them. */
+rpca_status rpca_op_fused_pass_noalloc(int64_t m, int64_t n, int32_t p,
+                                       const void* A, int64_t lda,
+                                       const float* X, int64_t ldx, float* H,
+                                       int64_t ldh, float* F, int64_t ldf,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ CENTER, HOST_A, SIMT, TIMING = 0x1, 0x2, 0x4, 0x8
 EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
            "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
            "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
-           "rpca_phase_times", "rpca_op_gram", "rpca_op_apply"]
+           "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc"]
 
 
 class RpcaError(RuntimeError):
@@ -93,6 +93,8 @@ def load_library(path=None):
     lib.rpca_op_apply.argtypes = [i64, i32, i32, vp, i64, vp, i64, ctypes.c_double, ctypes.c_double, vp, i64,
                                   i32, vp]
     lib.rpca_op_apply.restype = st
+    lib.rpca_op_fused_pass_noalloc.argtypes = [i64, i64, i32, vp, i64, vp, i64, vp, i64, vp, i64, vp]
+    lib.rpca_op_fused_pass_noalloc.restype = st
     if path is None:
         _lib = lib
     return lib
@@ -255,6 +257,22 @@ def fused_pass(A, X, shift=None, col_scale=None, with_f=True, kernel=0):
         dtype_code(A), m, n, p, _ptr(A), A.stride(0), _ptr(col_scale), _ptr(shift), _ptr(X),
         X.stride(0), _ptr(H), H.stride(0), _ptr(F), (F.stride(0) if F is not None else 0),
         kernel, _stream_ptr()))
+    return H, F
+
+
+def fused_pass_noalloc(A, X, H=None, F=None, with_f=True):
+    """The tensor-core fused pass (BF16 A, FP32 X) through the entry point
+    that allocates no device memory; H and F may be passed preallocated."""
+    torch = _torch()
+    m, n = A.shape
+    p = X.shape[1]
+    if H is None:
+        H = torch.empty(m, p, dtype=torch.float32, device=A.device)
+    if F is None and with_f:
+        F = torch.empty(n, p, dtype=torch.float32, device=A.device)
+    _check(load_library().rpca_op_fused_pass_noalloc(
+        m, n, p, _ptr(A), A.stride(0), _ptr(X), X.stride(0), _ptr(H), H.stride(0), _ptr(F),
+        (F.stride(0) if F is not None else 0), _stream_ptr()))
     return H, F
 
 

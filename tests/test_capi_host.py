@@ -68,3 +68,21 @@ def test_strerror(lib):
     for code in rpca.STATUS:
         assert lib.rpca_strerror(code)
     assert lib.rpca_last_error(None) == b""
+
+
+@pytest.mark.parametrize("n,p", [(4097, 16), (1000, 65), (0, 16), (1000, 0)])
+def test_noalloc_rejects_sizes_beyond_its_scratch(lib, n, p):
+    """Sizes outside the fixed scratch are refused on the host, before any
+    device work (the dummy pointers are never dereferenced)."""
+    d = ctypes.c_void_p(256)
+    assert lib.rpca_op_fused_pass_noalloc(4096, n, p, d, max(n, 1), d, max(p, 1), d, max(p, 1), d,
+                                          max(p, 1), None) == -1
+
+
+def test_noalloc_without_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present; the GPU test covers this entry")
+    lib = rpca.load_library()
+    d = ctypes.c_void_p(256)
+    assert lib.rpca_op_fused_pass_noalloc(4096, 1000, 16, d, 1000, d, 16, d, 16, d, 16, None) == -4
