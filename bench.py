@@ -305,7 +305,7 @@ def spectral_errors(A, outs, labels, iters=30, nvec=4):
             z = A.T @ y - V @ (Sf[:, None] * (U.T @ y))
             nz = torch.linalg.norm(z, dim=0)
             est = float(torch.sqrt(nz.max() / torch.linalg.norm(x, dim=0)[nz.argmax()]))
-            x = torch.linalg.qr(z)[0]
+            x = torch.linalg.qr(z.cpu())[0].to(z.device)   # n x nvec: small
         res["spectral_error_" + lab] = est
     if len(labels) == 2:
         res["spectral_error_ratio_bf16_over_f32"] = res["spectral_error_bf16"] / res["spectral_error_f32"]

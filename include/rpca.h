@@ -87,7 +87,9 @@ typedef struct {
   rpca_dtype dtype;       /* storage type of A */
   uint32_t flags;         /* RPCA_* flags above */
   int64_t tile_rows;      /* RPCA_HOST_A: rows per streamed tile (0: 1 GiB) */
-  void* stream;           /* cudaStream_t for all work; NULL: library stream */
+  void* stream;           /* cudaStream_t for all work; NULL: the default
+                             (legacy) stream, ordered after the caller's
+                             default-stream work */
 } rpca_problem;
 
 typedef struct {

@@ -746,15 +746,19 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
   } else {
     float* Bc32 = reinterpret_cast<float*>(Bc);
     float* Jc32 = reinterpret_cast<float*>(Jc);
-    const size_t mat = (size_t)w * w * sizeof(float);
-    const size_t smem = 2 * mat <= 200 * 1024 ? 2 * mat : (mat <= 200 * 1024 ? mat : 0);
-    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_jacobi<float><<<1, 1024, smem, st>>>(w, B, Bc32, Jc32, 4.0 * std::sqrt((double)w) * 5.96e-8, 40, dev_err);
-    RPCA_CUDA_TRY(cudaGetLastError());
+    const double tol = 4.0 * std::sqrt((double)w) * 5.96e-8;
+    if (getenv("RPCA_JACOBI_SINGLE") || !jacobi_cluster_f32(w, B, Jc32, tol, 40, dev_err, st)) {
+      const size_t mat = (size_t)w * w * sizeof(float);
+      const size_t smem = 2 * mat <= 200 * 1024 ? 2 * mat : (mat <= 200 * 1024 ? mat : 0);
+      RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      k_jacobi<float><<<1, 1024, smem, st>>>(w, B, Bc32, Jc32, tol, 40, dev_err);
+      RPCA_CUDA_TRY(cudaGetLastError());
+      count_launch();
+    }
     k_jacobi_w<float><<<w, 128, 0, st>>>(w, Jc32, W0);
   }
   RPCA_CUDA_TRY(cudaGetLastError());
-  count_launch(2);
+  count_launch(f64 ? 2 : 1);
   // B64 = B W0: singular values as column norms of B times unit approximate
   // right singular vectors (second-order accurate).
   if (f64) gemm_xm(true, w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st, nullptr);

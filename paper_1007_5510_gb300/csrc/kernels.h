@@ -68,6 +68,11 @@ void mat_add(int rows, int cols, const double* src, int64_t lds, double* dst, in
 // S descending.  FP32 sweeps with an FP64 finish (f64 = false) or FP64.
 // Singular triplets of B (w x w FP64 row-major): S descending, Ub, W
 // (row-major w x w, ld w); callers use the leading kk.  work: 4 w^2 doubles.
+// Step 4's one-sided Jacobi (FP32) on a thread-block cluster: J (w x w,
+// column-major FP32) with B J having orthogonal columns.  False when the
+// shape or the device does not admit the cluster.
+bool jacobi_cluster_f32(int w, const double* B, float* Jc, double tol, int max_sweeps, uint32_t* dev_err,
+                        cudaStream_t st);
 void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub, double* W,
                 double* work, uint32_t* dev_err, cudaStream_t st);
 

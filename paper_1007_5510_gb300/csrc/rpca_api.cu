@@ -214,7 +214,6 @@ struct rpca_ctx {
   int k = 0, l = 0, i = 0, w = 0;
   int64_t ldx = 0;        // ld of X and F (compute type)
   cudaStream_t stream = nullptr, copy_stream = nullptr;
-  bool own_stream = false;
   int next_pass = 0;
   bool centered = false;
   std::string last_error;
@@ -249,7 +248,6 @@ struct rpca_ctx {
       if (ev_used[t]) cudaEventDestroy(ev_used[t]);
     }
     if (copy_stream) cudaStreamDestroy(copy_stream);
-    if (own_stream && stream) cudaStreamDestroy(stream);
   }
   size_t cbytes() const { return f64 ? 8 : 4; }
   uint32_t* dev_err() const { return err.as<uint32_t>(); }
@@ -522,12 +520,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->w = (p->i + 1) * p->l;
   c->ldx = c->l + 1;
   const size_t es = c->cbytes();
-  if (p->stream) {
-    c->stream = static_cast<cudaStream_t>(p->stream);
-  } else {
-    RPCA_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-    c->own_stream = true;
-  }
+  c->stream = static_cast<cudaStream_t>(p->stream);  // NULL: the legacy default stream
   c->X.alloc((size_t)c->n * c->ldx * es);
   c->F.alloc((size_t)c->n * c->ldx * es);
   c->H.alloc((size_t)c->m * c->w * es);

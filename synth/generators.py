@@ -114,7 +114,8 @@ def lowrank_torch(m, n, sigma, seed, device, dtype=None, offset_std=0.0,
                   noise_std=0.0, chunk_rows=1 << 17):
     """Same construction as lowrank_np, generated with torch on ``device``:
     the tall Q factor by Cholesky QR twice (FP64 Gram), the n-side one by
-    torch.linalg.qr, the product in FP32 row chunks.  Returns ``dtype``
+    torch.linalg.qr, the product in FP32 row chunks.  The small
+    factorisations run on the CPU, so the device needs no solver library.  Returns ``dtype``
     (FP32 default).  Different random stream from lowrank_np."""
     torch = _torch()
     dtype = torch.float32 if dtype is None else dtype
@@ -129,11 +130,11 @@ def lowrank_torch(m, n, sigma, seed, device, dtype=None, offset_std=0.0,
         for r0 in range(0, m, chunk_rows):
             blk = U0[r0:r0 + chunk_rows].double()
             Gm += blk.T @ blk
-        L = torch.linalg.cholesky(Gm)
-        Rinv = torch.linalg.inv(L.T).float()
+        L = torch.linalg.cholesky(Gm.cpu())
+        Rinv = torch.linalg.inv(L.T).float().to(device)
         for r0 in range(0, m, chunk_rows):
             U0[r0:r0 + chunk_rows] = U0[r0:r0 + chunk_rows] @ Rinv
-    Qv, Rv = torch.linalg.qr(Zv)
+    Qv, Rv = (t.to(device) for t in torch.linalg.qr(Zv.cpu()))
     Qv = Qv * torch.where(torch.diagonal(Rv) < 0, -1.0, 1.0)[None, :]
     B = (Qv * sig[None, :]).T.contiguous().float()     # r x n
     A = torch.empty(m, n, dtype=dtype, device=device)

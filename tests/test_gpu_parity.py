@@ -367,3 +367,21 @@ def test_block_qr_tensor_cores_unaligned_blocks():
     assert np.abs(Q.T @ Q - np.eye(nblk * l)).max() < 1e-5
     Qo, _, _ = ro.pivoted_qr(H)
     assert est.max_principal_angle(Q, Qo) < 1e-4
+
+
+def test_pca_ordered_after_callers_default_stream_work():
+    """A context built on the caller's default stream must run after work the
+    caller queued there: A arrives by an asynchronous pinned copy issued just
+    before the PCA (a library-private stream would read a half-copied A)."""
+    m, n, k, l, i = 200_000, 512, 8, 10, 1
+    rng = np.random.default_rng(17)
+    A = gen.lowrank_np(2000, n, 0.8 ** np.arange(n), seed=4)
+    A = np.tile(A, (m // 2000, 1)).astype(np.float32) + 1e-4 * rng.standard_normal((m, n)).astype(np.float32)
+    Ah = torch.from_numpy(A).pin_memory()
+    ref = R().pca(_tt(A), k, l, i, seed=3)
+    Ad = torch.zeros(m, n, device="cuda")
+    torch.cuda.synchronize()
+    Ad.copy_(Ah, non_blocking=True)
+    U, S, V = R().pca(Ad, k, l, i, seed=3)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(S.cpu().numpy() - ref[1].cpu().numpy()) / ref[1].cpu().numpy()) < 1e-5
