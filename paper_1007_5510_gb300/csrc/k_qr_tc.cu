@@ -3,8 +3,9 @@
 //   gram:   C (p x q, FP64) = X^T Y over all rows, X m x p, Y m x q.  The
 //           rows are the reduction (MN-major operands), done in BF16 with
 //           each FP32 value split exactly into three BF16 slices (six slice
-//           products); CTAs split the rows, each keeps its partial in TMEM
-//           and adds it to C once.
+//           products); CTAs split the rows and 64-column groups of C,
+//           accumulate 128-row chunks in TMEM and sum the chunks in FP32
+//           registers, adding to C once.
 //   apply:  Y (m x q) = beta Y + alpha X M, X m x p (K-major operand), M p x q
 //           (FP64 small matrix, resident in shared memory).  Every FP32
 //           operand x is carried as x (its TF32 truncation is what the MMA
@@ -24,7 +25,6 @@ namespace rpca {
 namespace {
 
 constexpr int G_KSUB = 32;         // rows per Gram stage
-constexpr int G_THREADS = 128;
 
 __device__ __forceinline__ float tf32_trunc(float x) {
   return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
@@ -76,14 +76,29 @@ __global__ void k_slice3(int64_t rows, int64_t plane_rows, int cols, int ldS, co
 }
 
 // A operand: X columns [t*128, t*128+128) of each slice (MN-major, 2 boxes of
-// 64 columns), B operand: Y columns [0, npad) of each slice (MN-major).
-// Stage: X slices (3 x NXB boxes) then, unless X and Y coincide, Y slices
-// (3 x nybox boxes); boxes of G_KSUB rows x 64 BF16 columns.
+// 64 columns); B operand: the 64 columns [64g, 64g+64) of Y of this CTA's
+// column group g = blockIdx.y (MN-major, one box per slice).  A stage holds
+// the X slices (3 x NXB boxes) and, unless X and Y coincide, the three Y
+// boxes of the group; boxes are G_KSUB rows x 64 BF16 columns.
+//
+// Accuracy: the tensor cores add each product into the FP32 accumulator
+// with rounding relative to the accumulator's magnitude, so a long run of
+// same-sign products (the diagonal of X^T X) drifts by a few ulp per step.
+// TMEM therefore only ever accumulates one chunk of G_DRAIN subtiles
+// (128 rows, a bias of ~1e-6 relative); two TMEM buffers alternate, and the
+// epilogue warps add each finished chunk into per-thread FP32 sums on the
+// CUDA cores (round-to-nearest, so the few hundred chunk partials of a CTA
+// add without drift), which go to C in FP64 once at the end.
+constexpr int G_DRAIN = 4;                   // subtiles per TMEM chunk
+
+constexpr int G_EC = 32;                     // C columns per epilogue thread
+constexpr int G_EPI_WARPS_PER_T = 4 * (64 / G_EC);
+
 template <int NT, bool SAME>
-__global__ void __launch_bounds__(G_THREADS, 1)
+__global__ void __launch_bounds__(64 + 32 * G_EPI_WARPS_PER_T * NT, 1)
 k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t m,
-              int64_t plane_rows, int p, int q, int npad, int nybox, int ngroup, int nstages,
-              uint32_t stage_bytes, double* __restrict__ C, int64_t ldc, uint32_t* __restrict__ dev_err,
+              int64_t plane_rows, int p, int q, int ngroup, int nstages, uint32_t stage_bytes,
+              double* __restrict__ C, int64_t ldc, uint32_t* __restrict__ dev_err,
               const uint32_t* __restrict__ active) {
   if (active && *active == 0u) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -91,105 +106,135 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int NXB = NT * 2;                           // X boxes (64 cols each) per slice
   constexpr uint32_t BOX = G_KSUB * 128;
+  constexpr int NEPI = G_EPI_WARPS_PER_T * NT;          // epilogue warps
+  constexpr uint32_t TCOLS = NT == 1 ? 128 : 256;       // 2 buffers x NT x 64 columns
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * stage_bytes);
   uint64_t* empty = full + nstages;
-  uint64_t* done = empty + nstages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* tfull = empty + nstages;                    // [2]
+  uint64_t* tfree = tfull + 2;                          // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfree + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int group = blockIdx.x;
+  const int group = blockIdx.x, cg = blockIdx.y;
   const int64_t nsub = (m + G_KSUB - 1) / G_KSUB;
   const int64_t my_subs = (nsub > group) ? (nsub - group + ngroup - 1) / ngroup : 0;
-  const uint32_t tcols = (NT * npad <= 32) ? 32 : (NT * npad <= 64) ? 64 : (NT * npad <= 128) ? 128
-                         : (NT * npad <= 256) ? 256 : 512;
+  const int64_t nchunk = (my_subs + G_DRAIN - 1) / G_DRAIN;
   if (tid == 0) {
     for (int s = 0; s < nstages; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tfree[b], NEPI);
+    }
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, tcols);
+    tc::tmem_alloc(tmem_slot, TCOLS);
     tc::tmem_relinquish();
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  if (warp == 0 && lane == 0) {
-    for (int64_t it = 0; it < my_subs; ++it) {
-      const int s = (int)(it % nstages);
-      if (!tc::mbar_wait(&empty[s], (uint32_t)(((it / nstages) & 1) ^ 1), dev_err, abort_flag)) break;
-      unsigned char* st = smem + (size_t)s * stage_bytes;
-      const int64_t r0 = (group + it * ngroup) * G_KSUB;
-      tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
-      for (int sl = 0; sl < 3; ++sl) {
-        const int32_t y = (int32_t)(sl * plane_rows + r0);
-        for (int j = 0; j < NXB; ++j)
-          tc::tma_load_2d(st + (size_t)(sl * NXB + j) * BOX, &tmX, &full[s], 64 * j, y);
-        if (!SAME)
-          for (int j = 0; j < nybox; ++j)
-            tc::tma_load_2d(st + (size_t)(3 * NXB + sl * nybox + j) * BOX, &tmY, &full[s], 64 * j, y);
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int64_t it = 0; it < my_subs; ++it) {
+        const int s = (int)(it % nstages);
+        if (!tc::mbar_wait(&empty[s], (uint32_t)(((it / nstages) & 1) ^ 1), dev_err, abort_flag)) break;
+        unsigned char* st = smem + (size_t)s * stage_bytes;
+        const int64_t r0 = (group + it * ngroup) * G_KSUB;
+        tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+        for (int sl = 0; sl < 3; ++sl) {
+          const int32_t y = (int32_t)(sl * plane_rows + r0);
+          for (int j = 0; j < NXB; ++j)
+            tc::tma_load_2d(st + (size_t)(sl * NXB + j) * BOX, &tmX, &full[s], 64 * j, y);
+          if (!SAME) tc::tma_load_2d(st + (size_t)(3 * NXB + sl) * BOX, &tmY, &full[s], 64 * cg, y);
+        }
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = tc::idesc_make(1u, 1u, 1u, 128u, (uint32_t)npad);
-    // slice pairs (a, b) with a + b <= 4 (1-based): (1,1) (1,2) (2,1) (1,3) (2,2) (3,1)
-    const int pa[6] = {0, 0, 1, 0, 1, 2};
-    const int pb[6] = {0, 1, 0, 2, 1, 0};
-    for (int64_t it = 0; it < my_subs; ++it) {
-      const int s = (int)(it % nstages);
-      if (!tc::mbar_wait(&full[s], (uint32_t)((it / nstages) & 1), dev_err, abort_flag)) break;
-      tc::tc_fence_after();
-      const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
-      const uint32_t ybase = SAME ? sa : sa + 3 * NXB * BOX;
-      const uint32_t ystride = SAME ? NXB * BOX : nybox * BOX;   // bytes between slices of Y
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_make(1u, 1u, 1u, 128u, 64u);
+      // slice pairs (a, b) with a + b <= 4 (1-based): (1,1) (1,2) (2,1) (1,3) (2,2) (3,1),
+      // 0-based, one nibble per pair
+      constexpr uint32_t PA = 0x210100u, PB = 0x012010u;
+      int64_t it = 0;
+      bool ok = true;
+      for (int64_t c = 0; c < nchunk && ok; ++c) {
+        const int b = (int)(c & 1);
+        if (!tc::mbar_wait(&tfree[b], (uint32_t)(((c >> 1) & 1) ^ 1), dev_err, abort_flag)) break;
+        tc::tc_fence_after();
+        const int64_t it_end = (it + G_DRAIN < my_subs) ? it + G_DRAIN : my_subs;
+        for (bool first = true; it < it_end; ++it, first = false) {
+          const int s = (int)(it % nstages);
+          if (!tc::mbar_wait(&full[s], (uint32_t)((it / nstages) & 1), dev_err, abort_flag)) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
+          const uint32_t ybase = SAME ? sa + cg * BOX : sa + 3 * NXB * BOX;
+          const uint32_t ystride = SAME ? NXB * BOX : BOX;   // bytes between slices of Y
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
+          for (int t = 0; t < NT; ++t) {
+            const uint32_t d = tmem + (uint32_t)(b * NT + t) * 64u;
 #pragma unroll
-        for (int kk = 0; kk < G_KSUB / 16; ++kk) {
-          const uint32_t ko = kk * 2048;
-          const uint32_t d = tmem + t * npad;
-#pragma unroll
-          for (int pr = 0; pr < 6; ++pr) {
-            const uint64_t ad = tc::sdesc_sw128(sa + pa[pr] * NXB * BOX + t * 2 * BOX + ko, BOX, 1024);
-            const uint64_t bd = tc::sdesc_sw128(ybase + pb[pr] * ystride + ko, BOX, 1024);
-            tc::mma_f16(d, ad, bd, idesc, (it > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+            for (int kk = 0; kk < G_KSUB / 16; ++kk) {
+              const uint32_t ko = kk * 2048;
+#pragma unroll 1
+              for (int pr = 0; pr < 6; ++pr) {
+                const uint32_t a = (PA >> (4 * pr)) & 0xFu, bsl = (PB >> (4 * pr)) & 0xFu;
+                const uint64_t ad = tc::sdesc_sw128(sa + a * NXB * BOX + t * 2 * BOX + ko, BOX, 1024);
+                const uint64_t bd = tc::sdesc_sw128(ybase + bsl * ystride + ko, BOX, 1024);
+                tc::mma_f16(d, ad, bd, idesc, (!first || kk > 0 || pr > 0) ? 1u : 0u);
+              }
+            }
           }
+          tc::mma_commit(&empty[s]);
         }
+        tc::mma_commit(&tfull[b]);
       }
-      tc::mma_commit(&empty[s]);
     }
-    tc::mma_commit(done);
-  }
-  __syncwarp();
-  bool ok = (my_subs == 0) ? false : tc::mbar_wait(done, 0, dev_err, abort_flag);
-  ok = __all_sync(0xffffffffu, ok);
-  tc::tc_fence_after();
-  if (ok) {
-    for (int t = 0; t < NT; ++t) {
-      const int row = t * 128 + warp * 32 + lane;   // X column
-      for (int c16 = 0; c16 < npad; c16 += 16) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * npad + c16, v);
-        if (row < p) {
+  } else {
+    // epilogue: warp 2 + e reads TMEM lane quadrant (warp % 4) of tile
+    // t = e / G_EPI_WARPS_PER_T, columns [cs, cs + G_EC) of the 64-wide group
+    const int e = warp - 2;
+    const int t = e / G_EPI_WARPS_PER_T;
+    const int cs = ((e % G_EPI_WARPS_PER_T) >> 2) * G_EC;
+    const int quad = warp & 3;
+    const int row = t * 128 + quad * 32 + lane;        // X column = row of C
+    float acc[G_EC];
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c16 + j < q) atomicAdd(&C[(int64_t)row * ldc + c16 + j], (double)v[j]);
-        }
+    for (int j = 0; j < G_EC; ++j) acc[j] = 0.f;
+    bool ok = true;
+    for (int64_t c = 0; c < nchunk; ++c) {
+      const int b = (int)(c & 1);
+      ok = tc::mbar_wait(&tfull[b], (uint32_t)((c >> 1) & 1), dev_err, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc::tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NT + t) * 64u + cs;
+#pragma unroll
+      for (int piece = 0; piece < G_EC / 16; ++piece) {
+        float v[16];
+        tc::tmem_ld16(taddr + 16 * piece, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[16 * piece + j] += v[j];
       }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tfree[b]);
     }
-  }
-  if (warp == 1 && lane == 0) {
-    volatile int never = 0;
-    tc::mbar_wait(done, 0, nullptr, &never);
+    if (ok && row < p) {
+      const int c0 = cg * 64 + cs;
+#pragma unroll
+      for (int j = 0; j < G_EC; ++j)
+        if (c0 + j < q) atomicAdd(&C[(int64_t)row * ldc + c0 + j], (double)acc[j]);
+    }
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, tcols);
+  if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
 }
 
 // ----------------------------------------------------------------- apply
@@ -415,10 +460,8 @@ bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* 
              const uint32_t* active, bool reslice_x) {
   if (p > 256 || q > 256 || m < 256 || !slices) return false;
   const bool same = (X == Y && p == q && ldx == ldy);
-  const int npad = (int)round_up(q, 16);
   const int NT = (p > 128) ? 2 : 1;
-  if (NT * npad > 512) return false;
-  if (same && npad > NT * 128) return false;
+  const int ncg = (int)cdiv(q, 64);                  // 64-column groups of C
   const int ldX = (int)round_up(p, 64), ldY = (int)round_up(q, 64);
   const int64_t prow = round_up(m, G_KSUB);
   const size_t need = (size_t)3 * prow * 2 * (ldX + (same ? 0 : ldY));
@@ -428,21 +471,21 @@ bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* 
   CUtensorMap tX, tY;
   if (!make_tmap_2d(&tX, SX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * prow, ldX, ldX, G_KSUB, 64)) return false;
   if (!make_tmap_2d(&tY, SY, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * prow, ldY, ldY, G_KSUB, 64)) return false;
-  const int nybox = ldY / 64;
   const uint32_t box = G_KSUB * 128;
-  const uint32_t stage_bytes = (uint32_t)(3 * NT * 2 + (same ? 0 : 3 * nybox)) * box;
+  const uint32_t stage_bytes = (uint32_t)(3 * NT * 2 + (same ? 0 : 3)) * box;
   const int nstages = (int)std::min<int64_t>(6, (200 * 1024) / stage_bytes);
   if (nstages < 2) return false;
   if (reslice_x || same) slice3(m, prow, p, X, ldx, SX, st, active);
   if (!same) slice3(m, prow, q, Y, ldy, SY, st, active);
-  const size_t smem = 1024 + (size_t)nstages * stage_bytes + (2 * nstages + 1) * 8 + 16;
+  const size_t smem = 1024 + (size_t)nstages * stage_bytes + (2 * nstages + 4) * 8 + 16;
   if (!g_sms_qr) g_sms_qr = num_sms();
-  const int ngroup = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, G_KSUB), g_sms_qr));
+  const int ngroup =
+      (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, G_KSUB), std::max(1, g_sms_qr / ncg)));
   RPCA_CUDA_TRY(cudaMemset2DAsync(C, ldc * 8, 0, q * 8, p, st));
   auto launch = [&](auto kern) {
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<ngroup, G_THREADS, smem, st>>>(tX, tY, m, prow, p, q, npad, nybox, ngroup, nstages, stage_bytes, C,
-                                          ldc, dev_err, active);
+    kern<<<dim3(ngroup, ncg), 64 + 32 * G_EPI_WARPS_PER_T * NT, smem, st>>>(tX, tY, m, prow, p, q, ngroup, nstages, stage_bytes, C,
+                                                         ldc, dev_err, active);
     RPCA_CUDA_TRY(cudaGetLastError());
   };
   if (NT == 2) {

@@ -333,6 +333,23 @@ def test_gram_tensor_cores(m, p, q, same):
     assert _rel(C, Co) < 1e-5
 
 
+@pytest.mark.parametrize("p", [60, 180])
+def test_gram_tensor_cores_long_same_sign_sums(p):
+    """Two million rows: every diagonal entry of X^T X is a sum of positive
+    products, where an accumulator that rounds relative to its own size
+    drifts.  Each diagonal entry must hold to 2e-6 of itself (the orthogonality
+    of Q is read from this Gram)."""
+    m = 2_000_000
+    rng = np.random.default_rng(p)
+    X = (rng.standard_normal((m, p)) / np.sqrt(m)).astype(np.float32)
+    C = R().gram(_tt(X), kernel=2).cpu().numpy()
+    X64 = X.astype(np.float64)
+    d = np.einsum("ij,ij->j", X64, X64)
+    assert np.max(np.abs(np.diag(C) - d) / d) < 2e-6
+    Co = X64.T @ X64
+    assert _rel(C, Co) < 2e-6
+
+
 @pytest.mark.parametrize("m,p,q", [(20_000, 20, 20), (20_000, 60, 60), (30_001, 180, 50), (9000, 120, 60)])
 @pytest.mark.parametrize("beta", [0.0, 1.0])
 def test_apply_tensor_cores(m, p, q, beta):
