@@ -97,7 +97,7 @@ constexpr int G_EPI_WARPS_PER_T = 4 * (64 / G_EC);
 template <int NT, bool SAME>
 __global__ void __launch_bounds__(64 + 32 * G_EPI_WARPS_PER_T * NT, 1)
 k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t m,
-              int64_t plane_rows, int p, int q, int ngroup, int nstages, uint32_t stage_bytes,
+              int64_t plane_rows, int x0, int y0, int p, int q, int ngroup, int nstages, uint32_t stage_bytes,
               double* __restrict__ C, int64_t ldc, uint32_t* __restrict__ dev_err,
               const uint32_t* __restrict__ active) {
   if (active && *active == 0u) return;
@@ -150,8 +150,8 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         for (int sl = 0; sl < 3; ++sl) {
           const int32_t y = (int32_t)(sl * plane_rows + r0);
           for (int j = 0; j < NXB; ++j)
-            tc::tma_load_2d(st + (size_t)(sl * NXB + j) * BOX, &tmX, &full[s], 64 * j, y);
-          if (!SAME) tc::tma_load_2d(st + (size_t)(3 * NXB + sl) * BOX, &tmY, &full[s], 64 * cg, y);
+            tc::tma_load_2d(st + (size_t)(sl * NXB + j) * BOX, &tmX, &full[s], x0 + 64 * j, y);
+          if (!SAME) tc::tma_load_2d(st + (size_t)(3 * NXB + sl) * BOX, &tmY, &full[s], y0 + 64 * cg, y);
         }
       }
     }
@@ -484,8 +484,42 @@ bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* 
   RPCA_CUDA_TRY(cudaMemset2DAsync(C, ldc * 8, 0, q * 8, p, st));
   auto launch = [&](auto kern) {
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<dim3(ngroup, ncg), 64 + 32 * G_EPI_WARPS_PER_T * NT, smem, st>>>(tX, tY, m, prow, p, q, ngroup, nstages, stage_bytes, C,
-                                                         ldc, dev_err, active);
+    kern<<<dim3(ngroup, ncg), 64 + 32 * G_EPI_WARPS_PER_T * NT, smem, st>>>(
+        tX, tY, m, prow, 0, 0, p, q, ngroup, nstages, stage_bytes, C, ldc, dev_err, active);
+    RPCA_CUDA_TRY(cudaGetLastError());
+  };
+  if (NT == 2) {
+    if (same) launch(k_gram_bf16x3<2, true>);
+    else launch(k_gram_bf16x3<2, false>);
+  } else {
+    if (same) launch(k_gram_bf16x3<1, true>);
+    else launch(k_gram_bf16x3<1, false>);
+  }
+  count_launch();
+  return true;
+}
+
+bool gram_slices(int64_t m, int64_t plane_rows, const void* S, int lds, int x0, int p, int y0, int q, double* C,
+                 int64_t ldc, cudaStream_t st, uint32_t* dev_err, const uint32_t* active) {
+  if (p > 256 || q > 256 || (x0 & 63) || (y0 & 63) || plane_rows % G_KSUB) return false;
+  const bool same = (x0 == y0 && p == q);
+  const int NT = (p > 128) ? 2 : 1;
+  const int ncg = (int)cdiv(q, 64);
+  CUtensorMap tS;
+  if (!make_tmap_2d(&tS, S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * plane_rows, lds, lds, G_KSUB, 64)) return false;
+  const uint32_t box = G_KSUB * 128;
+  const uint32_t stage_bytes = (uint32_t)(3 * NT * 2 + (same ? 0 : 3)) * box;
+  const int nstages = (int)std::min<int64_t>(6, (200 * 1024) / stage_bytes);
+  if (nstages < 2) return false;
+  const size_t smem = 1024 + (size_t)nstages * stage_bytes + (2 * nstages + 4) * 8 + 16;
+  if (!g_sms_qr) g_sms_qr = num_sms();
+  const int ngroup =
+      (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, G_KSUB), std::max(1, g_sms_qr / ncg)));
+  RPCA_CUDA_TRY(cudaMemset2DAsync(C, ldc * 8, 0, q * 8, p, st));
+  auto launch = [&](auto kern) {
+    RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<dim3(ngroup, ncg), 64 + 32 * G_EPI_WARPS_PER_T * NT, smem, st>>>(
+        tS, tS, m, plane_rows, x0, y0, p, q, ngroup, nstages, stage_bytes, C, ldc, dev_err, active);
     RPCA_CUDA_TRY(cudaGetLastError());
   };
   if (NT == 2) {

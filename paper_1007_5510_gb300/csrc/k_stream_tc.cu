@@ -75,7 +75,7 @@ template <int NT, typename TF>
 __global__ void __launch_bounds__(TP_THREADS, 1)
 k_tpass_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmQ, int64_t m,
              int64_t n, int w, int npad, int nqbox, int nslab, int ngroup, int nstages, uint32_t stage_bytes,
-             TF* __restrict__ T, int64_t ldt, uint32_t* __restrict__ dev_err) {
+             TF* __restrict__ T, int64_t ldt, int qblk, uint32_t* __restrict__ dev_err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t a_bytes = NT * 2 * TP_KSUB * 128;
@@ -168,8 +168,15 @@ k_tpass_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * npad + c16, v);
         if (row < n) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (c16 + q < w) atomicAdd(&T[row * ldt + c16 + q], (TF)v[q]);
+          for (int q = 0; q < 16; ++q) {
+            const int c = c16 + q;
+            if (qblk > 0) {
+              // block-padded Q: column c is column (c/64)*qblk + c%64 of T
+              if ((c & 63) < qblk) atomicAdd(&T[row * ldt + (c >> 6) * qblk + (c & 63)], (TF)v[q]);
+            } else if (c < w) {
+              atomicAdd(&T[row * ldt + c], (TF)v[q]);
+            }
+          }
         }
       }
     }
@@ -187,19 +194,24 @@ int g_num_sms = 0;
 static bool tpass_bf16(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   if (a.dtype != RPCA_BF16 || a.mode != MODE_T) return false;
   if (a.shift || a.scale) return false;
-  if (a.p > 256 || !a.work) return false;
-  const int npad = (int)round_up(a.p, 16);
-  const int wq = (int)round_up(a.p, 64);            // Q16 columns (box multiple)
-  if ((size_t)a.m * wq * 2 > a.work_bytes) return false;
+  if (a.p > 256) return false;
+  const bool pre = a.q16 != nullptr;                 // Q already BF16, block-padded
+  if (!pre && !a.work) return false;
+  const int wq = pre ? (int)a.q16_ld : (int)round_up(a.p, 64);   // Q16 columns (box multiple)
+  if (wq > 256 || wq % 64) return false;
+  const int npad = pre ? wq : (int)round_up(a.p, 16);
+  if (!pre && (size_t)a.m * wq * 2 > a.work_bytes) return false;
   const int NT = (npad <= 256 && 2 * npad <= 512) ? 2 : 1;
   CUtensorMap tmA, tmQ;
   if (!make_tmap_2d(&tmA, a.A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.m, a.n, a.lda, TP_KSUB, 64)) return false;
-  __nv_bfloat16* Q16 = static_cast<__nv_bfloat16*>(a.work);
+  const __nv_bfloat16* Q16 = pre ? static_cast<const __nv_bfloat16*>(a.q16) : static_cast<__nv_bfloat16*>(a.work);
   if (!make_tmap_2d(&tmQ, Q16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.m, wq, wq, TP_KSUB, 64)) return false;
+  const int qblk = pre ? a.q_blk : 0;
   // Q -> BF16 (zero-padded)
-  {
+  if (!pre) {
     int64_t cnt = a.m * wq;
-    k_q_to_bf16<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(a.m, a.p, wq, static_cast<const float*>(a.H), a.ldh, Q16);
+    k_q_to_bf16<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(a.m, a.p, wq, static_cast<const float*>(a.H), a.ldh,
+                                                          static_cast<__nv_bfloat16*>(a.work));
     RPCA_CUDA_TRY(cudaGetLastError());
     count_launch();
   }
@@ -219,12 +231,12 @@ static bool tpass_bf16(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
     auto kern = NT == 2 ? k_tpass_bf16<2, double> : k_tpass_bf16<1, double>;
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, TP_THREADS, smem, st>>>(tmA, tmQ, a.m, a.n, a.p, npad, nqbox, nslab, ngroup, nstages,
-                                          stage_bytes, static_cast<double*>(a.F), a.ldf, dev_err);
+                                          stage_bytes, static_cast<double*>(a.F), a.ldf, qblk, dev_err);
   } else {
     auto kern = NT == 2 ? k_tpass_bf16<2, float> : k_tpass_bf16<1, float>;
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, TP_THREADS, smem, st>>>(tmA, tmQ, a.m, a.n, a.p, npad, nqbox, nslab, ngroup, nstages,
-                                          stage_bytes, static_cast<float*>(a.F), a.ldf, dev_err);
+                                          stage_bytes, static_cast<float*>(a.F), a.ldf, qblk, dev_err);
   }
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();

@@ -27,6 +27,12 @@ struct PassArgs {
   bool f_f64 = false;            // MODE_T: F is an FP64 accumulator
   void* work = nullptr;          // device scratch for the tensor-core path
   size_t work_bytes = 0;
+  // MODE_T on tensor cores: Q already in BF16 (q16, ld q16_ld), block-padded
+  // (block b of q_blk columns at columns [64b, 64b + q_blk)); T columns are
+  // written in compact numbering.
+  const void* q16 = nullptr;
+  int64_t q16_ld = 0;
+  int q_blk = 0;
 };
 
 void launch_pass_simt(const PassArgs& a, cudaStream_t st);
@@ -73,6 +79,27 @@ void mat_add(int rows, int cols, const double* src, int64_t lds, double* dst, in
 // shape or the device does not admit the cluster.
 bool jacobi_cluster_f32(int w, const double* B, float* Jc, double tol, int max_sweeps, uint32_t* dev_err,
                         cudaStream_t st);
+// ---------------------------------------------- H in three BF16 slices
+// (k_qr_slices.cu): planes of plane_rows x (nblk*64) BF16, block-padded.
+void slice_blocks(int64_t m, int64_t plane_rows, int nblk, int l, const float* H, int64_t ld, void* S,
+                  cudaStream_t st);
+void unslice_blocks(int64_t m, int64_t plane_rows, int nblk, int l, const void* S, float* H, int64_t ld,
+                    cudaStream_t st);
+void col_sums_slices(int64_t m, int64_t plane_rows, int nblk, int l, const void* S, double* out, cudaStream_t st);
+// E (w x w, compact) from C with block-padded indices (ld ldc)
+void compact_sq(int nblk, int l, const double* C, int64_t ldc, double* E, cudaStream_t st);
+// C (p x q FP64, ldc) = X^T Y, X = columns [x0, x0+p), Y = [y0, y0+q) of the
+// slices (x0, y0 multiples of 64)
+bool gram_slices(int64_t m, int64_t plane_rows, const void* S, int lds, int x0, int p, int y0, int q, double* C,
+                 int64_t ldc, cudaStream_t st, uint32_t* dev_err, const uint32_t* active);
+// Y = beta Y + X (alpha M): X = nkb 64-column boxes at x0, Y = the 64 columns
+// at y0 (slices, rewritten when write_slices), M krows x q FP64 (ldm) with
+// row remap rl (block-padded K when rl > 0); optional FP32 copy Yf
+// (columns < qf, ldf).  mt: scratch of 3 * 64 * 192 BF16.
+bool apply_slices(int64_t m, int64_t plane_rows, void* S, int lds, int x0, int nkb, int y0, const double* M,
+                  int krows, int q, int64_t ldm, double alpha, int rl, bool beta, bool write_slices, float* Yf,
+                  int64_t ldf, int qf, void* mt, cudaStream_t st, uint32_t* dev_err, const uint32_t* active);
+
 void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub, double* W,
                 double* work, uint32_t* dev_err, cudaStream_t st);
 

@@ -106,7 +106,18 @@ struct QrScratch {
   float* mt = nullptr;     // 2 * 256 * 256 floats (tensor-core products)
   void* slices = nullptr;  // BF16 slice scratch for tensor-core Grams
   size_t slice_bytes = 0;
+  double* G64 = nullptr;   // 64 x 64   (sliced QR: Gram of one padded block)
+  double* C64 = nullptr;   // 192 x 64  (sliced QR: projection coefficients)
+  double* Cfull = nullptr; // 192 x 192 (sliced QR: Q^T Q with padded indices)
 };
+
+// Step 2 on H held in three BF16 slices (k_qr_slices.cu) applies to FP32 H
+// with at least kTcMinRows rows, 40 <= l <= 64 (blocks padded to 64
+// columns), at most three blocks and k <= 64.
+static bool sliced_ok(bool f64, int64_t m, int nblk, int l, int k) {
+  return !f64 && m >= 8192 && l >= 40 && l <= 64 && nblk >= 1 && nblk <= 3 && k <= 64;
+}
+constexpr size_t kSliceScratchDoubles = 64 * 64 + 192 * 64 + 192 * 192;
 
 // Tensor-core (TF32 x3) tall products apply to FP32 data with at least this
 // many rows; Hlo is the remainder array of H (same layout).
@@ -175,6 +186,45 @@ static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, 
   }
 }
 
+// Step 2 with H held in three exact BF16 slices (S: 3 planes of prow x nblk*64,
+// block j at columns [64j, 64j + l)): block Gram-Schmidt twice and Cholesky
+// QR (up to four passes) per block as in block_qr, Gram matrices and
+// Cholesky factors in FP64, every tall product on tensor cores reading and
+// writing the slices.  E_out (compact w x w) = Q^T Q - I.  fp32_out: Q is
+// also written back to H in FP32.
+static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, void* S, int64_t prow, double* E_out,
+                            bool fp32_out, const QrScratch& s, uint32_t* dev_err, cudaStream_t st) {
+  const int lds = nblk * 64;
+  const double piv_rel = 1e-5, shift_rel = 1e-5;
+  auto need = [](bool ok) {
+    if (!ok) throw Invalid("sliced tensor-core QR: unsupported shape");
+  };
+  slice_blocks(m, prow, nblk, l, H, ld, S, st);
+  for (int j = 0; j < nblk; ++j) {
+    if (j > 0) {
+      for (int rep = 0; rep < 2; ++rep) {
+        need(gram_slices(m, prow, S, lds, 0, 64 * j, 64 * j, 64, s.C64, 64, st, dev_err, nullptr));
+        need(apply_slices(m, prow, S, lds, 0, j, 64 * j, s.C64, 64 * j, 64, 64, -1.0, 0, true, true, nullptr, 0, 0,
+                          s.mt, st, dev_err, nullptr));
+      }
+    }
+    uint32_t* qf = s.qf + 4 * j;
+    for (int pass = 0; pass < 4; ++pass) {
+      const uint32_t* active = pass >= 2 ? qf + pass : nullptr;
+      need(gram_slices(m, prow, S, lds, 64 * j, 64, 64 * j, 64, s.G64, 64, st, dev_err, active));
+      chol_small(l, s.G64, 64, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st);
+      need(apply_slices(m, prow, S, lds, 64 * j, 1, 64 * j, s.Rinv, l, l, l, 1.0, l, false, true, nullptr, 0, 0,
+                        s.mt, st, dev_err, active));
+    }
+  }
+  if (E_out) {
+    need(gram_slices(m, prow, S, lds, 0, lds, 0, lds, s.Cfull, lds, st, dev_err, nullptr));
+    compact_sq(nblk, l, s.Cfull, lds, E_out, st);
+    sub_identity(nblk * l, E_out, st);
+  }
+  if (fp32_out) unslice_blocks(m, prow, nblk, l, S, H, ld, st);
+}
+
 // Step 4 on T (n x w, ld w, compute type): T = Q_T R_T with Q_T from the
 // block QR (in place of T) and R_T = Q_T^T T_orig (FP64-accumulated Gram);
 // with E_T = Q_T^T Q_T - I the orthonormal basis is Q_T (I - E_T/2) to first
@@ -219,6 +269,10 @@ struct rpca_ctx {
   std::string last_error;
 
   DevBuf X, F, H, T, Tc, shift, corr, d, vtmp, q1, G64, small, err, At, tiles[2], work, Hlo, Tlo, mt, slices;
+  // H in three BF16 slices for the tensor-core QR (sliced_ok)
+  bool sliced = false;
+  int64_t hs_rows = 0;
+  DevBuf Hs, sq;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   int64_t tile_rows = 0;
   QrScratch qs;
@@ -292,6 +346,16 @@ void validate(const rpca_problem* p) {
 }
 
 // One streamed pass over the working matrix (device-resident or tiles).
+// Will the T pass run on the BF16 tensor-core kernel (TMA-aligned A, no
+// centring shift or column scale)?
+bool tpass_bf16_ok(const rpca_ctx* c, const rpca_matrix* Am) {
+  if (c->prob.dtype != RPCA_BF16 || c->centered || c->simt || Am->col_scale) return false;
+  if (c->host_a) return (c->n * 2) % 16 == 0;
+  const void* A = c->transposed ? c->At.ptr : Am->data;
+  const int64_t lda = c->transposed ? c->n : Am->ld;
+  return (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda * 2) % 16 == 0 && c->w <= 192;
+}
+
 void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
   const size_t ab = dtype_bytes(c->prob.dtype);
   a.work = c->work.ptr;
@@ -301,6 +365,7 @@ void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
     a.lda = c->transposed ? c->n : Am->ld;
     a.m = c->m;
     if (!(c->simt) && launch_pass_tc(a, c->stream, c->dev_err())) return;
+    if (a.q16) throw Invalid("T pass: tensor-core kernel refused its BF16 operand");
     launch_pass_simt(a, c->stream);
     return;
   }
@@ -328,9 +393,11 @@ void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
     ta.lda = c->n;
     ta.m = rows;
     ta.H = static_cast<char*>(a.H) + (size_t)r0 * a.ldh * es;
+    if (a.q16) ta.q16 = static_cast<const __nv_bfloat16*>(a.q16) + (size_t)r0 * a.q16_ld;
     ta.accumulate_f = true;
     if (!(c->simt) && launch_pass_tc(ta, c->stream, c->dev_err())) {
     } else {
+      if (ta.q16) throw Invalid("T pass: tensor-core kernel refused its BF16 operand");
       launch_pass_simt(ta, c->stream);
     }
     RPCA_CUDA_TRY(cudaEventRecord(c->ev_used[b], c->stream));
@@ -422,14 +489,26 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
     return RPCA_MORE;
   }
   // Step 2: H = Q R (Q in place of H); Step 3: T = A_c^T Q
+  // The BF16 tensor-core T pass reads slice 1 of the sliced Q (= RNE_bf16(Q));
+  // every other T pass reads Q in FP32.
+  const bool t16 = c->sliced && tpass_bf16_ok(c, Am);
   c->tic(c->i + 1);
-  block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->E, c->qs, c->dev_err(), st,
-           c->Hlo.as<float>());
+  if (c->sliced)
+    block_qr_sliced(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows, c->E, !t16, c->qs,
+                    c->dev_err(), st);
+  else
+    block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->E, c->qs, c->dev_err(), st,
+             c->Hlo.as<float>());
   c->toc(c->i + 1);
   a.mode = MODE_T;
   a.p = c->w;
   a.H = c->H.ptr;
   a.ldh = c->w;
+  if (t16) {
+    a.q16 = c->Hs.ptr;
+    a.q16_ld = (c->i + 1) * 64;
+    a.q_blk = c->l;
+  }
   a.F = c->T64.ptr;   // FP64 accumulation across row blocks
   a.ldf = c->w;
   a.f_f64 = true;
@@ -469,8 +548,15 @@ rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int
   const bool hlo = c->Hlo.ptr && c->m >= kTcMinRows;
   qr_apply(f64, c->n, w, k, c->T.ptr, tlo ? c->Tlo.as<float>() : nullptr, w, c->MV, k, 1.0, 0.0, c->outV.ptr,
            nullptr, k, c->qs, st, c->dev_err());
-  qr_apply(f64, c->m, w, k, c->H.ptr, hlo ? c->Hlo.as<float>() : nullptr, w, c->MU, k, 1.0, 0.0, c->outU.ptr,
-           nullptr, k, c->qs, st, c->dev_err());
+  if (c->sliced) {
+    // U = Q M_U with Q in slices (block-padded rows of M_U)
+    if (!apply_slices(c->m, c->hs_rows, c->Hs.ptr, (c->i + 1) * 64, 0, c->i + 1, 0, c->MU, w, k, k, 1.0, c->l,
+                      false, false, c->outU.as<float>(), k, k, c->qs.mt, st, c->dev_err(), nullptr))
+      throw Invalid("sliced tensor-core product U = Q M: unsupported shape");
+  } else {
+    qr_apply(f64, c->m, w, k, c->H.ptr, hlo ? c->Hlo.as<float>() : nullptr, w, c->MU, k, 1.0, 0.0, c->outU.ptr,
+             nullptr, k, c->qs, st, c->dev_err());
+  }
   c->toc(c->i + 4);
   void* Uw = c->transposed ? V : U;
   int64_t ldUw = c->transposed ? ldv : ldu;
@@ -563,12 +649,25 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
     c->mt.alloc(2 * 256 * 256 * sizeof(float));
     c->qs.mt = c->mt.as<float>();
     if (!c->simt) {
-      c->Hlo.alloc((size_t)c->m * c->w * sizeof(float));
+      c->sliced = sliced_ok(false, c->m, c->i + 1, c->l, c->k);
+      if (c->sliced) {
+        c->hs_rows = round_up(c->m, 128);
+        c->Hs.alloc((size_t)3 * c->hs_rows * (c->i + 1) * 64 * 2);
+        c->sq.alloc(kSliceScratchDoubles * sizeof(double));
+        c->qs.G64 = c->sq.as<double>();
+        c->qs.C64 = c->qs.G64 + 64 * 64;
+        c->qs.Cfull = c->qs.C64 + 192 * 64;
+      } else {
+        c->Hlo.alloc((size_t)c->m * c->w * sizeof(float));
+      }
       if (c->n >= kTcMinRows) c->Tlo.alloc((size_t)c->n * c->w * sizeof(float));
-      const size_t sb = (size_t)6 * (round_up(std::max(c->m, c->n), 32)) * (2 * round_up(c->w, 64));
-      c->slices.alloc(sb);
-      c->qs.slices = c->slices.ptr;
-      c->qs.slice_bytes = sb;
+      const int64_t srows = c->sliced ? (c->n >= kTcMinRows ? c->n : 0) : std::max(c->m, c->n);
+      if (srows > 0) {
+        const size_t sb = (size_t)6 * round_up(srows, 32) * (2 * round_up(c->w, 64));
+        c->slices.alloc(sb);
+        c->qs.slices = c->slices.ptr;
+        c->qs.slice_bytes = sb;
+      }
     }
   }
   if (c->host_a) {
@@ -774,6 +873,25 @@ rpca_status rpca_op_qr(int32_t f64, int64_t m, int32_t nblk, int32_t l, void* H,
     qs.qf = reinterpret_cast<uint32_t*>(s);
     uint32_t* err = qs.qf + 4 * nblk;
     RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
+    if (sliced_ok(f64 != 0, m, nblk, l, 0)) {
+      // H held in three BF16 slices through the whole QR (tensor cores)
+      const int64_t prow = round_up(m, 128);
+      DevBuf hs, sq, mt16;
+      hs.alloc((size_t)3 * prow * nblk * 64 * 2);
+      sq.alloc(kSliceScratchDoubles * sizeof(double));
+      mt16.alloc((size_t)3 * 64 * 192 * 2);
+      qs.G64 = sq.as<double>();
+      qs.C64 = qs.G64 + 64 * 64;
+      qs.Cfull = qs.C64 + 192 * 64;
+      qs.mt = mt16.as<float>();
+      block_qr_sliced(m, nblk, l, static_cast<float*>(H), ld, hs.ptr, prow, nullptr, true, qs, err, st);
+      uint32_t flags = 0;
+      RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+      if (flags & DEV_ERR_BREAKDOWN) return RPCA_EBREAKDOWN;
+      if (flags & DEV_ERR_TIMEOUT) return RPCA_ETIMEOUT;
+      return RPCA_OK;
+    }
     DevBuf hlo, mt, sl;
     if (!f64 && m >= kTcMinRows) {
       hlo.alloc((size_t)m * ld * sizeof(float));

@@ -119,6 +119,24 @@ def test_block_qr(f64, m):
     assert est.max_principal_angle(Q, Qo) < (1e-10 if f64 else 1e-4)
 
 
+@pytest.mark.parametrize("m,l,nblk,decay", [(100_000, 60, 3, 0.97), (30_001, 48, 2, 0.9), (20_000, 64, 3, 0.95)])
+def test_block_qr_sliced_tensor_cores(m, l, nblk, decay):
+    """Step 2 with H held in three BF16 slices on tensor cores (blocks of
+    40..64 columns padded to 64): orthonormal to FP32 level and spanning the
+    pivoted-QR basis of the oracle."""
+    rng = np.random.default_rng(m + l)
+    w = nblk * l
+    H = rng.standard_normal((m, w)) @ np.diag(decay ** np.arange(w))
+    H32 = H.astype(np.float32)
+    Ht = _tt(H32)
+    R().qr_inplace(Ht, nblk, l)
+    torch.cuda.synchronize()
+    Q = Ht.cpu().double().numpy()
+    assert np.abs(Q.T @ Q - np.eye(w)).max() < 1e-5
+    Qo, _, _ = ro.pivoted_qr(H32.astype(np.float64))
+    assert est.max_principal_angle(Q, Qo) < 1e-4
+
+
 # ------------------------------------------------------------------ Step 4
 @pytest.mark.parametrize("f64,w", [(True, 24), (False, 66), (False, 180)])
 def test_small_svd(f64, w):
