@@ -183,6 +183,44 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
               (unsigned long long)__double_as_longlong(fmax(G[(int64_t)i * ldg + i], 0.0)));
   }
   __syncthreads();
+  if (pass >= 1 && in_smem) {
+    // A later pass of the sequence sees G = I + E with E tiny.  Then
+    // M = (I + E)^(-1/2) = I - E/2 + 3/8 E^2 + O(E^3) orthonormalises the
+    // block as well as R^-1 does (same span, (H M)^T (H M) = I + O(E^3)),
+    // and its inverse is I + E/2 - E^2/8 + O(E^3).  E^2 only needs a few
+    // digits: it is formed in FP32.
+    __shared__ unsigned long long emax_bits;
+    if (tid == 0) emax_bits = 0ull;
+    __syncthreads();
+    for (int e = tid; e < p * p; e += blockDim.x) {
+      const int i = e / p, j = e % p;
+      const double d = fabs(G[(int64_t)i * ldg + j] - (i == j ? 1.0 : 0.0));
+      atomicMax(&emax_bits, (unsigned long long)__double_as_longlong(isfinite(d) ? d : 1e300));
+    }
+    __syncthreads();
+    if (__longlong_as_double((long long)emax_bits) < 2e-3) {
+      float* Ef = reinterpret_cast<float*>(sm_chol);        // p x p
+      for (int e = tid; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e % p;
+        Ef[e] = (float)(G[(int64_t)i * ldg + j] - (i == j ? 1.0 : 0.0));
+      }
+      __syncthreads();
+      for (int e = tid; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e % p;
+        float e2 = 0.f;
+        for (int k = 0; k < p; ++k) e2 = fmaf(Ef[i * p + k], Ef[k * p + j], e2);
+        const double ee = G[(int64_t)i * ldg + j] - (i == j ? 1.0 : 0.0);
+        const double id = i == j ? 1.0 : 0.0;
+        Rinvout[e] = id - 0.5 * ee + 0.375 * (double)e2;
+        Rout[e] = id + 0.5 * ee - 0.125 * (double)e2;
+      }
+      if (tid == 0) {
+        if (pass == 1) qf[2] = (qf[0] & 3u) ? 1u : 0u;
+        if (pass == 2) qf[3] = ((qf[0] >> 1) & 3u) ? 1u : 0u;
+      }
+      return;
+    }
+  }
   bool shifted = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
     const double shift = (attempt == 0) ? 0.0 : shift_rel * dmax;

@@ -16,6 +16,7 @@
 #include <cudaTypedefs.h>
 #include <cstdio>
 #include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -84,29 +85,33 @@ __global__ void k_slice3(int64_t rows, int64_t plane_rows, int cols, int ldS, co
 // Accuracy: the tensor cores add each product into the FP32 accumulator
 // with rounding relative to the accumulator's magnitude, so a long run of
 // same-sign products (the diagonal of X^T X) drifts by a few ulp per step.
-// TMEM therefore only ever accumulates one chunk of G_DRAIN subtiles
-// (128 rows, a bias of ~1e-6 relative); two TMEM buffers alternate, and the
+// TMEM therefore only ever accumulates one chunk of 128 rows (a bias of
+// ~1e-6 relative); two TMEM buffers alternate, and the
 // epilogue warps add each finished chunk into per-thread FP32 sums on the
 // CUDA cores (round-to-nearest, so the few hundred chunk partials of a CTA
 // add without drift), which go to C in FP64 once at the end.
-constexpr int G_DRAIN = 4;                   // subtiles per TMEM chunk
 
 constexpr int G_EC = 32;                     // C columns per epilogue thread
 constexpr int G_EPI_WARPS_PER_T = 4 * (64 / G_EC);
 
-template <int NT, bool SAME>
+// KS rows per stage (box KS x 64 BF16); nxb X boxes loaded per slice.  A
+// stage holds 3 x nxb X boxes, 3 Y boxes unless SAME, and one spare box: the
+// M = 128 A operand of the last tile may span one box past the loaded ones
+// (rows of C beyond p, discarded).
+template <int NT, bool SAME, int KS>
 __global__ void __launch_bounds__(64 + 32 * G_EPI_WARPS_PER_T * NT, 1)
 k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t m,
-              int64_t plane_rows, int x0, int y0, int p, int q, int ngroup, int nstages, uint32_t stage_bytes,
-              double* __restrict__ C, int64_t ldc, uint32_t* __restrict__ dev_err,
+              int64_t plane_rows, int x0, int y0, int p, int q, int nxb, int ngroup, int nstages,
+              uint32_t stage_bytes, double* __restrict__ C, int64_t ldc, uint32_t* __restrict__ dev_err,
               const uint32_t* __restrict__ active) {
   if (active && *active == 0u) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  constexpr int NXB = NT * 2;                           // X boxes (64 cols each) per slice
-  constexpr uint32_t BOX = G_KSUB * 128;
+  constexpr uint32_t BOX = KS * 128;
   constexpr int NEPI = G_EPI_WARPS_PER_T * NT;          // epilogue warps
+  constexpr int DRAIN = 128 / KS;                       // stages per TMEM chunk (128 rows)
+  const uint32_t tx_bytes = (uint32_t)(3 * nxb + (SAME ? 0 : 3)) * BOX;
   constexpr uint32_t TCOLS = NT == 1 ? 128 : 256;       // 2 buffers x NT x 64 columns
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * stage_bytes);
   uint64_t* empty = full + nstages;
@@ -116,9 +121,9 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int group = blockIdx.x, cg = blockIdx.y;
-  const int64_t nsub = (m + G_KSUB - 1) / G_KSUB;
+  const int64_t nsub = (m + KS - 1) / KS;
   const int64_t my_subs = (nsub > group) ? (nsub - group + ngroup - 1) / ngroup : 0;
-  const int64_t nchunk = (my_subs + G_DRAIN - 1) / G_DRAIN;
+  const int64_t nchunk = (my_subs + DRAIN - 1) / DRAIN;
   if (tid == 0) {
     for (int s = 0; s < nstages; ++s) {
       tc::mbar_init(&full[s], 1);
@@ -145,13 +150,13 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         const int s = (int)(it % nstages);
         if (!tc::mbar_wait(&empty[s], (uint32_t)(((it / nstages) & 1) ^ 1), dev_err, abort_flag)) break;
         unsigned char* st = smem + (size_t)s * stage_bytes;
-        const int64_t r0 = (group + it * ngroup) * G_KSUB;
-        tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+        const int64_t r0 = (group + it * ngroup) * KS;
+        tc::mbar_arrive_expect_tx(&full[s], tx_bytes);
         for (int sl = 0; sl < 3; ++sl) {
           const int32_t y = (int32_t)(sl * plane_rows + r0);
-          for (int j = 0; j < NXB; ++j)
-            tc::tma_load_2d(st + (size_t)(sl * NXB + j) * BOX, &tmX, &full[s], x0 + 64 * j, y);
-          if (!SAME) tc::tma_load_2d(st + (size_t)(3 * NXB + sl) * BOX, &tmY, &full[s], y0 + 64 * cg, y);
+          for (int j = 0; j < nxb; ++j)
+            tc::tma_load_2d(st + (size_t)(sl * nxb + j) * BOX, &tmX, &full[s], x0 + 64 * j, y);
+          if (!SAME) tc::tma_load_2d(st + (size_t)(3 * nxb + sl) * BOX, &tmY, &full[s], y0 + 64 * cg, y);
         }
       }
     }
@@ -167,24 +172,24 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         const int b = (int)(c & 1);
         if (!tc::mbar_wait(&tfree[b], (uint32_t)(((c >> 1) & 1) ^ 1), dev_err, abort_flag)) break;
         tc::tc_fence_after();
-        const int64_t it_end = (it + G_DRAIN < my_subs) ? it + G_DRAIN : my_subs;
+        const int64_t it_end = (it + DRAIN < my_subs) ? it + DRAIN : my_subs;
         for (bool first = true; it < it_end; ++it, first = false) {
           const int s = (int)(it % nstages);
           if (!tc::mbar_wait(&full[s], (uint32_t)((it / nstages) & 1), dev_err, abort_flag)) { ok = false; break; }
           tc::tc_fence_after();
           const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
-          const uint32_t ybase = SAME ? sa + cg * BOX : sa + 3 * NXB * BOX;
-          const uint32_t ystride = SAME ? NXB * BOX : BOX;   // bytes between slices of Y
+          const uint32_t ybase = SAME ? sa + cg * BOX : sa + 3 * nxb * BOX;
+          const uint32_t ystride = SAME ? nxb * BOX : BOX;   // bytes between slices of Y
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
             const uint32_t d = tmem + (uint32_t)(b * NT + t) * 64u;
 #pragma unroll
-            for (int kk = 0; kk < G_KSUB / 16; ++kk) {
+            for (int kk = 0; kk < KS / 16; ++kk) {
               const uint32_t ko = kk * 2048;
 #pragma unroll 1
               for (int pr = 0; pr < 6; ++pr) {
                 const uint32_t a = (PA >> (4 * pr)) & 0xFu, bsl = (PB >> (4 * pr)) & 0xFu;
-                const uint64_t ad = tc::sdesc_sw128(sa + a * NXB * BOX + t * 2 * BOX + ko, BOX, 1024);
+                const uint64_t ad = tc::sdesc_sw128(sa + a * nxb * BOX + t * 2 * BOX + ko, BOX, 1024);
                 const uint64_t bd = tc::sdesc_sw128(ybase + bsl * ystride + ko, BOX, 1024);
                 tc::mma_f16(d, ad, bd, idesc, (!first || kk > 0 || pr > 0) ? 1u : 0u);
               }
@@ -472,7 +477,8 @@ bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* 
   if (!make_tmap_2d(&tX, SX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * prow, ldX, ldX, G_KSUB, 64)) return false;
   if (!make_tmap_2d(&tY, SY, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * prow, ldY, ldY, G_KSUB, 64)) return false;
   const uint32_t box = G_KSUB * 128;
-  const uint32_t stage_bytes = (uint32_t)(3 * NT * 2 + (same ? 0 : 3)) * box;
+  const int nxb = (int)cdiv(p, 64);
+  const uint32_t stage_bytes = (uint32_t)(3 * nxb + (same ? 0 : 3) + 1) * box;
   const int nstages = (int)std::min<int64_t>(6, (200 * 1024) / stage_bytes);
   if (nstages < 2) return false;
   if (reslice_x || same) slice3(m, prow, p, X, ldx, SX, st, active);
@@ -485,15 +491,15 @@ bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* 
   auto launch = [&](auto kern) {
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<dim3(ngroup, ncg), 64 + 32 * G_EPI_WARPS_PER_T * NT, smem, st>>>(
-        tX, tY, m, prow, 0, 0, p, q, ngroup, nstages, stage_bytes, C, ldc, dev_err, active);
+        tX, tY, m, prow, 0, 0, p, q, nxb, ngroup, nstages, stage_bytes, C, ldc, dev_err, active);
     RPCA_CUDA_TRY(cudaGetLastError());
   };
   if (NT == 2) {
-    if (same) launch(k_gram_bf16x3<2, true>);
-    else launch(k_gram_bf16x3<2, false>);
+    if (same) launch(k_gram_bf16x3<2, true, G_KSUB>);
+    else launch(k_gram_bf16x3<2, false, G_KSUB>);
   } else {
-    if (same) launch(k_gram_bf16x3<1, true>);
-    else launch(k_gram_bf16x3<1, false>);
+    if (same) launch(k_gram_bf16x3<1, true, G_KSUB>);
+    else launch(k_gram_bf16x3<1, false, G_KSUB>);
   }
   count_launch();
   return true;
@@ -501,33 +507,50 @@ bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* 
 
 bool gram_slices(int64_t m, int64_t plane_rows, const void* S, int lds, int x0, int p, int y0, int q, double* C,
                  int64_t ldc, cudaStream_t st, uint32_t* dev_err, const uint32_t* active) {
-  if (p > 256 || q > 256 || (x0 & 63) || (y0 & 63) || plane_rows % G_KSUB) return false;
+  if (p > 256 || q > 256 || (x0 & 63) || (y0 & 63) || plane_rows % 128) return false;
   const bool same = (x0 == y0 && p == q);
   const int NT = (p > 128) ? 2 : 1;
   const int ncg = (int)cdiv(q, 64);
-  CUtensorMap tS;
-  if (!make_tmap_2d(&tS, S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * plane_rows, lds, lds, G_KSUB, 64)) return false;
-  const uint32_t box = G_KSUB * 128;
-  const uint32_t stage_bytes = (uint32_t)(3 * NT * 2 + (same ? 0 : 3)) * box;
+  const int nxb = (int)cdiv(p, 64);
+  // deepest row box that leaves at least three stages (else two)
+  const int nbox = 3 * nxb + (same ? 0 : 3) + 1;
+  int ks = 32;
+  for (int cand : {128, 64, 32}) {
+    if ((size_t)3 * nbox * cand * 128 <= 200 * 1024) { ks = cand; break; }
+  }
+  if ((size_t)2 * nbox * ks * 128 > 200 * 1024) return false;
+  const uint32_t stage_bytes = (uint32_t)nbox * ks * 128;
   const int nstages = (int)std::min<int64_t>(6, (200 * 1024) / stage_bytes);
-  if (nstages < 2) return false;
+  CUtensorMap tS;
+  if (!make_tmap_2d(&tS, S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 3 * plane_rows, lds, lds, (uint32_t)ks, 64))
+    return false;
   const size_t smem = 1024 + (size_t)nstages * stage_bytes + (2 * nstages + 4) * 8 + 16;
   if (!g_sms_qr) g_sms_qr = num_sms();
-  const int ngroup =
-      (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, G_KSUB), std::max(1, g_sms_qr / ncg)));
+  const int ngroup = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, ks), std::max(1, g_sms_qr / ncg)));
   RPCA_CUDA_TRY(cudaMemset2DAsync(C, ldc * 8, 0, q * 8, p, st));
   auto launch = [&](auto kern) {
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<dim3(ngroup, ncg), 64 + 32 * G_EPI_WARPS_PER_T * NT, smem, st>>>(
-        tS, tS, m, plane_rows, x0, y0, p, q, ngroup, nstages, stage_bytes, C, ldc, dev_err, active);
+        tS, tS, m, plane_rows, x0, y0, p, q, nxb, ngroup, nstages, stage_bytes, C, ldc, dev_err, active);
     RPCA_CUDA_TRY(cudaGetLastError());
   };
+  auto pick_ks = [&](auto nt, auto sm) {
+    constexpr int NTc = decltype(nt)::value;
+    constexpr bool SMc = decltype(sm)::value;
+    if (ks == 128) launch(k_gram_bf16x3<NTc, SMc, 128>);
+    else if (ks == 64) launch(k_gram_bf16x3<NTc, SMc, 64>);
+    else launch(k_gram_bf16x3<NTc, SMc, 32>);
+  };
+  using T1 = std::integral_constant<int, 1>;
+  using T2 = std::integral_constant<int, 2>;
+  using S1 = std::integral_constant<bool, true>;
+  using S0 = std::integral_constant<bool, false>;
   if (NT == 2) {
-    if (same) launch(k_gram_bf16x3<2, true>);
-    else launch(k_gram_bf16x3<2, false>);
+    if (same) pick_ks(T2{}, S1{});
+    else pick_ks(T2{}, S0{});
   } else {
-    if (same) launch(k_gram_bf16x3<1, true>);
-    else launch(k_gram_bf16x3<1, false>);
+    if (same) pick_ks(T1{}, S1{});
+    else pick_ks(T1{}, S0{});
   }
   count_launch();
   return true;

@@ -57,6 +57,9 @@ void gemm_xm(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, cons
 // FP64 Gram G = R^T R (R upper), write R and Rinv (p x p, ld p).  A pivot
 // below piv_rel * max diag retries with a diagonal shift shift_rel * max
 // diag.  Passes 2 and 3 run only after a shifted pass (else identities).
+// A pass >= 1 whose G is within 2e-3 of I (p <= 64) writes instead the
+// symmetric M = I - E/2 + 3/8 E^2 (E = G - I) as Rinv and its inverse as R:
+// the same span, orthonormal to O(E^3).
 // qf: 4 device words private to the block; the word qf + pass gates the
 // Gram/gemm of passes 2-3 (qf[2], qf[3]).
 void chol_small(int p, const double* G, int64_t ldg, double* R, double* Rinv, int pass,
