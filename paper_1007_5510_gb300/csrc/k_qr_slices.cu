@@ -257,14 +257,20 @@ k_apply_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
           }
           tc::tc_fence_after();
           const uint32_t sa = tc::smem_u32(stages + (size_t)s * 3 * AS_XBOX);
+          // descriptors of the three X slices and the three M slices of this
+          // K box; the K steps are compile-time offsets (cheap issue)
+          const uint64_t xa = tc::sdesc_sw128(sa, 16, 1024);
+          const uint64_t xS[3] = {xa, tc::sdesc_add(xa, AS_XBOX), tc::sdesc_add(xa, 2 * AS_XBOX)};
+          const uint64_t mb = tc::sdesc_sw128(ma + kb * AS_MBOX, 16, 1024);
+          const uint32_t mstride = (uint32_t)p.nkb * AS_MBOX;
+          const uint64_t mS[3] = {mb, tc::sdesc_add(mb, mstride), tc::sdesc_add(mb, 2 * mstride)};
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll 1
+#pragma unroll
             for (int pr = 0; pr < 6; ++pr) {
-              const uint32_t a = (PA >> (4 * pr)) & 0xFu, bs = (PB >> (4 * pr)) & 0xFu;
-              const uint64_t ad = tc::sdesc_sw128(sa + a * AS_XBOX + kk * 32, 16, 1024);
-              const uint64_t bd = tc::sdesc_sw128(ma + (bs * p.nkb + kb) * AS_MBOX + kk * 32, 16, 1024);
-              tc::mma_f16(tmem + b * 64, ad, bd, idesc, (kb > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+              const int a = (int)((PA >> (4 * pr)) & 0xFu), bs = (int)((PB >> (4 * pr)) & 0xFu);
+              tc::mma_f16(tmem + b * 64, tc::sdesc_add(xS[a], kk * 32), tc::sdesc_add(mS[bs], kk * 32), idesc,
+                          (kb > 0 || kk > 0 || pr > 0) ? 1u : 0u);
             }
           }
           tc::mma_commit(&empty[s]);

@@ -180,18 +180,22 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
           const uint32_t ybase = SAME ? sa + cg * BOX : sa + 3 * nxb * BOX;
           const uint32_t ystride = SAME ? nxb * BOX : BOX;   // bytes between slices of Y
+          // one descriptor per slice and operand; every MMA of the stage is
+          // a compile-time offset from these (cheap issue)
+          const uint64_t a0 = tc::sdesc_sw128(sa, BOX, 1024);
+          const uint64_t aS[3] = {a0, tc::sdesc_add(a0, nxb * BOX), tc::sdesc_add(a0, 2 * nxb * BOX)};
+          const uint64_t b0 = tc::sdesc_sw128(ybase, BOX, 1024);
+          const uint64_t bS[3] = {b0, tc::sdesc_add(b0, ystride), tc::sdesc_add(b0, 2 * ystride)};
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
             const uint32_t d = tmem + (uint32_t)(b * NT + t) * 64u;
 #pragma unroll
             for (int kk = 0; kk < KS / 16; ++kk) {
-              const uint32_t ko = kk * 2048;
-#pragma unroll 1
+#pragma unroll
               for (int pr = 0; pr < 6; ++pr) {
-                const uint32_t a = (PA >> (4 * pr)) & 0xFu, bsl = (PB >> (4 * pr)) & 0xFu;
-                const uint64_t ad = tc::sdesc_sw128(sa + a * nxb * BOX + t * 2 * BOX + ko, BOX, 1024);
-                const uint64_t bd = tc::sdesc_sw128(ybase + bsl * ystride + ko, BOX, 1024);
-                tc::mma_f16(d, ad, bd, idesc, (!first || kk > 0 || pr > 0) ? 1u : 0u);
+                const int a = (int)((PA >> (4 * pr)) & 0xFu), bsl = (int)((PB >> (4 * pr)) & 0xFu);
+                tc::mma_f16(d, tc::sdesc_add(aS[a], t * 2 * BOX + kk * 2048), tc::sdesc_add(bS[bsl], kk * 2048),
+                            idesc, (!first || kk > 0 || pr > 0) ? 1u : 0u);
               }
             }
           }

@@ -185,6 +185,10 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo, ui
   d |= (uint64_t)2 << 61;
   return d;
 }
+// Descriptor of the same layout starting byte_off bytes later (the start
+// address field holds addr >> 4; shared addresses stay below 2^18, so the
+// 14-bit field never carries).
+__device__ __forceinline__ uint64_t sdesc_add(uint64_t d, uint32_t byte_off) { return d + (byte_off >> 4); }
 // Instruction descriptor: FP32 accumulate, A/B format code (kind::f16: 1 =
 // BF16; kind::tf32: 2 = TF32), major-ness (0 K-major, 1 MN-major), M, N.
 __host__ __device__ constexpr uint32_t idesc_make(uint32_t ab_fmt, uint32_t a_mn, uint32_t b_mn, uint32_t M,
