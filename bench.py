@@ -29,7 +29,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="precision", m=1_000_000, n=4096, k=50, l=60, i=2, seed=1007)
-CPU_SAMPLE_ROWS = 20_000
+CPU_SAMPLE_ROWS = 150_000     # cpu_baseline: one oracle PCA on this many rows (~13 s)
+REF_SAMPLE_ROWS = 40_000      # --impl reference: rows per timed step
+# DRAM bytes (read + write) per row of A of one launch of the BF16 tensor-core
+# fused pass at n = 4,096, L = 64 (ncu capture at m = 100,000; traffic grows
+# in proportion to the rows), see profiles/fused_pass_bf16_m100000_n4096_l60.md
+FUSED_BF16_N4096_TRAFFIC_PER_ROW = 848.1e6 / 100_000
 
 
 def parse():
@@ -272,7 +277,9 @@ def main():
             "phases_ms": phases16,
             "roofline": {"bound": "hbm", "kernel": "fused pass (BF16, l=%d)" % l,
                          "achieved": round(achieved, 2), "peak": hbm, "peak_kind": peak_kind,
-                         "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                         "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                         "traffic": (round(FUSED_BF16_N4096_TRAFFIC_PER_ROW * m)
+                                     if (n == 4096 and not args.simt) else None),
                          "algorithmic_bytes_per_launch": m * n * bytes_bf16,
                          "avg_launch_ms": round(fused_ms16, 4),
                          "t_pass_ms": round(tpass_ms16, 4)},
@@ -356,7 +363,7 @@ def run_reference(args, W):
     import numpy as np
     from synth import generators as gen
     m, n, k, l, i = W["m"], W["n"], W["k"], W["l"], W["i"]
-    rows = min(CPU_SAMPLE_ROWS, m)
+    rows = min(REF_SAMPLE_ROWS, m)
     A = gen.workload_np("precision", m=rows, n=n, seed=W["seed"], rank_cap=1024)
     A = gen.round_bf16_np(A).astype(np.float64)
     for _ in range(args.warmup):
