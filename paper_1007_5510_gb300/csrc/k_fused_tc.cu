@@ -81,6 +81,14 @@ __device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr) {
                : "r"(addr));
   return v;
 }
+// Bulk copy of `bytes` (multiple of 16) from this CTA's shared memory to a
+// peer's (dst and its mbarrier rbar are shared::cluster addresses), counted
+// on rbar; the source may be reused after cp.async.bulk.wait_group.read.
+__device__ __forceinline__ void bulk_to_peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t rbar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "r"(src), "r"(bytes), "r"(rbar)
+               : "memory");
+}
 __device__ __forceinline__ void st_cluster_b64(uint32_t addr, uint32_t a, uint32_t b) {
   asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
@@ -119,6 +127,8 @@ struct FusedParams {
 //   [stages: nstages x (NC/64 boxes of 128 rows x 128 B)]
 //   [Pst: 128 rows x L FP32, 16-byte chunks XOR-swizzled by row]
 //   [Hs[2]: 128 rows x 128 B BF16, SW128 MN-major operand]
+//   [Hst: this CTA's rows of H_b in BF16 (128/CS rows x 128 B), staged for
+//    the bulk copies into every CTA's Hs]
 //   [barriers]
 template <int L, int NT, bool FUSED>
 __global__ void __launch_bounds__(FP_THREADS, 1)
@@ -139,7 +149,9 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   unsigned char* stages = xs + p.xs_bytes;
   unsigned char* pst = stages + (size_t)p.nstages * p.stage_bytes;
   unsigned char* hs = pst + PST_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(hs + 2 * HS_BYTES);
+  const uint32_t hst_bytes = (uint32_t)(FP_BM / cluster_nctarank()) * 128;   // rows of this CTA
+  unsigned char* hst = hs + 2 * HS_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(hst + hst_bytes);
   uint64_t* full = bars;                      // [nstages]
   uint64_t* empty = full + p.nstages;         // [nstages]
   uint64_t* pfull = empty + p.nstages;        // [2]
@@ -171,7 +183,7 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     for (int x = 0; x < 2; ++x) {
       tc::mbar_init(&pfull[x], 1);
       tc::mbar_init(&pempty[x], 4);
-      tc::mbar_init(&hready[x], cs);
+      tc::mbar_init(&hready[x], 1);   // armed with the byte count of H_b
       tc::mbar_init(&hfree[x], cs);
     }
     tc::mbar_init(pready, cs);
@@ -180,6 +192,10 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     tc::mbar_init(done, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
+    if (FUSED) {
+      tc::mbar_arrive_expect_tx(&hready[0], HS_BYTES);
+      tc::mbar_arrive_expect_tx(&hready[1], HS_BYTES);
+    }
     tc::tma_prefetch(&tmA);
     tc::tma_prefetch(&tmX);
   }
@@ -253,6 +269,8 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           const int x = (int)(jt & 1);
           if (!tc::mbar_wait(&hready[x], (uint32_t)((jt >> 1) & 1), p.dev_err, abort_flag, true)) break;
           tc::tc_fence_after();
+          // next use of this buffer (panel jt + 2): all CS owners' rows
+          tc::mbar_arrive_expect_tx(&hready[x], HS_BYTES);
           const uint32_t sa = tc::smem_u32(stages + (size_t)s * p.stage_bytes);
           const uint32_t hb = hs_a + x * HS_BYTES;
 #pragma unroll
@@ -310,6 +328,8 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       ok = tc::mbar_wait(pready, (uint32_t)(it & 1), p.dev_err, abort_flag, true);
       if (FUSED)
         ok = ok && tc::mbar_wait(&hfree[x], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag, true);
+      // the staged rows of the previous panel have been read by their copies
+      if (FUSED && e < (int)cs) tc::bulk_wait_read0();
       ok = epi_bar_and(ok);
       if (!ok) break;
       // rows [row0, row0 + rpc) of H_b: sum the cluster's partials, apply the
@@ -318,14 +338,14 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int rr = row0 + ch / CPR, chunk = ch % CPR, col = chunk * 4;
         const uint32_t off = (uint32_t)(rr * L * 4 + ((chunk ^ (rr & (CPR - 1))) * 16));
         float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (uint32_t c0 = 0; c0 < cs; c0 += 8) {
-          float4 v[8];
+        {
+          float4 v[16];   // every peer's chunk in flight at once
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (c0 + q < cs) v[q] = ld_cluster_f4(mapa(pst_a + off, c0 + q));
+          for (int q = 0; q < 16; ++q)
+            if (q < (int)cs) v[q] = ld_cluster_f4(mapa(pst_a + off, (uint32_t)q));
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (c0 + q < cs) { sacc.x += v[q].x; sacc.y += v[q].y; sacc.z += v[q].z; sacc.w += v[q].w; }
+          for (int q = 0; q < 16; ++q)
+            if (q < (int)cs) { sacc.x += v[q].x; sacc.y += v[q].y; sacc.z += v[q].z; sacc.w += v[q].w; }
         }
         const int64_t grow = r0 + rr;
         float vv[4] = {sacc.x, sacc.y, sacc.z, sacc.w};
@@ -335,21 +355,41 @@ k_fused_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           if (p.corr && cc < p.l) vv[q] -= p.corr[cc];
           if (grow >= p.m || cc >= p.l) vv[q] = 0.f;
           if (cc == p.ones_col && grow < p.m) vv[q] = 1.f;
-          if (grow < p.m && cc < p.l) p.H[grow * p.ldh + cc] = vv[q];
+        }
+        if (grow < p.m) {
+          float* hrow = p.H + grow * p.ldh;
+          if (col + 3 < p.l && ((reinterpret_cast<uintptr_t>(hrow + col) & 15) == 0)) {
+            *reinterpret_cast<float4*>(hrow + col) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (col + q < p.l) hrow[col + q] = vv[q];
+          }
         }
         if (FUSED) {
-          const uint32_t hoff = (uint32_t)(rr * 128 + ((((col >> 3) ^ (rr & 7))) << 4) + (col & 7) * 2);
-          const uint32_t lo = pack_bf16(vv[0], vv[1]), hi = pack_bf16(vv[2], vv[3]);
-          for (uint32_t c = 0; c < cs; ++c) st_cluster_b64(mapa(hs_a + x * HS_BYTES + hoff, c), lo, hi);
+          // row rr of Hs, swizzled as in its destination
+          const uint32_t hoff = (uint32_t)((rr - row0) * 128 + ((((col >> 3) ^ (rr & 7))) << 4) + (col & 7) * 2);
+          *reinterpret_cast<uint2*>(hst + hoff) = make_uint2(pack_bf16(vv[0], vv[1]),
+                                                                           pack_bf16(vv[2], vv[3]));
         }
       }
-      if (FUSED) asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
       epi_bar();
-      if (e < (int)cs) {
-        tc::mbar_arrive_cluster(pfree, (uint32_t)e);
-        if (FUSED) tc::mbar_arrive_cluster(&hready[x], (uint32_t)e);
+      // the partials of this panel have been read: the senders may reuse Pst
+      if (e < (int)cs) tc::mbar_arrive_cluster(pfree, (uint32_t)e);
+      if (FUSED) {
+        // (GEMM2 reads columns [0, L) of Hs only)
+        tc::fence_proxy_async_smem();
+        epi_bar();
+        if (e < (int)cs) {
+          bulk_to_peer(mapa(hs_a + x * HS_BYTES + (uint32_t)row0 * 128, (uint32_t)e),
+                       tc::smem_u32(hst), (uint32_t)rpc * 128,
+                       mapa(tc::smem_u32(&hready[x]), (uint32_t)e));
+          tc::bulk_commit();
+        }
       }
     }
+    // staged rows must stay until the copies have read them
+    if (FUSED && e < (int)cs) tc::bulk_wait_read0();
     // ---------------------------------------------------- flush F slab
     if (FUSED) {
       bool okd = ok && my_pan > 0 && tc::mbar_wait(done, 0, p.dev_err, abort_flag);
@@ -408,7 +448,8 @@ bool launch_fused(const PassArgs& a, cudaStream_t st, uint32_t* dev_err, int cs)
   p.ones_col = a.ones_col;
   p.xs_bytes = (uint32_t)(NC / 64) * L * 128;
   p.stage_bytes = (uint32_t)(NC / 64) * FP_BM * 128;
-  const size_t fixed = 1024 + p.xs_bytes + (size_t)FP_BM * L * 4 + 2 * (size_t)FP_BM * 128 + 256;
+  const size_t fixed = 1024 + p.xs_bytes + (size_t)FP_BM * L * 4 + 2 * (size_t)FP_BM * 128 +
+                       (size_t)(FP_BM / cs) * 128 + 256;
   const size_t budget = 227 * 1024;
   p.nstages = (int)std::min<size_t>(4, (budget - fixed) / p.stage_bytes);
   if (p.nstages < 2) return false;
