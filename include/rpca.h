@@ -208,6 +208,38 @@ uint64_t rpca_kernel_launches(void);
 int32_t rpca_phase_times(rpca_ctx* c, double* ms, int32_t cap, int32_t* runs);
 
 /* ---------------------------------------------------------------------- */
+/* Batches of independent problems (uneven shapes).                        */
+/* ---------------------------------------------------------------------- */
+typedef struct rpca_batch rpca_batch;
+
+/* One context per problem (problems[p] as for rpca_init; device matrices
+ * only, no RPCA_TIMING), spread over nstreams streams of the library that
+ * fork from and join to problems[0].stream.  All workspace is allocated
+ * here. */
+rpca_status rpca_batch_init(rpca_batch** out, int32_t count,
+                            const rpca_problem* problems, int32_t nstreams);
+
+/* All problems: A[p] as for rpca_pass, outputs as for rpca_finish (arrays
+ * of count pointers / leading dimensions; U, S, V or their entries may be
+ * NULL).  The first run, and the first run after any pointer in the
+ * arguments changed, executes directly and then records the whole batch as
+ * one CUDA graph; later runs with the same pointers replay that graph (one
+ * launch).  Synchronises problems[0].stream and reports the first problem
+ * whose device-side checks failed (rpca_batch_last_error names it).  The
+ * batch runs on streams of its own, ordered after the work queued on
+ * problems[0].stream, which in turn waits for the batch. */
+rpca_status rpca_batch_run(rpca_batch* b, const rpca_matrix* A, void* const* U,
+                           const int64_t* ldu, double* const* S, void* const* V,
+                           const int64_t* ldv);
+
+/* Frees the batch (NULL is a no-op). */
+void rpca_batch_destroy(rpca_batch* b);
+
+/* Last error message of a batch, or of the last failed rpca_batch_init when
+ * b is NULL (never NULL). */
+const char* rpca_batch_last_error(const rpca_batch* b);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free fused pass.  The paper has no counterpart to this call: */
 /* it exists for callers that must not allocate device memory per call.   */
 /* ---------------------------------------------------------------------- */

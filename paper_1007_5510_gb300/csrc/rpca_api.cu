@@ -15,6 +15,12 @@ namespace rpca {
 
 std::atomic<uint64_t> g_launches{0};
 
+// Error text of the last failed rpca_batch_init (no batch object remains).
+static std::string& last_batch_error() {
+  static thread_local std::string s;
+  return s;
+}
+
 // ------------------------------------------------------------- Philox (host)
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplies with key bumps by the Weyl constants.
@@ -527,7 +533,9 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   return RPCA_OK;
 }
 
-rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int64_t ldv) {
+// Steps 4-6 and the copies into the caller's buffers, queued on the context
+// stream only (no host synchronisation: usable inside a stream capture).
+void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int64_t ldv) {
   if (c->next_pass != c->i + 2) throw Invalid("finish before all passes");
   const bool f64 = c->f64;
   cudaStream_t st = c->stream;
@@ -573,6 +581,11 @@ rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int
                                     cudaMemcpyDefault, st));
   }
   if (S) RPCA_CUDA_TRY(cudaMemcpyAsync(S, c->S, c->k * sizeof(double), cudaMemcpyDefault, st));
+}
+
+// Waits for the context stream and reports device-side errors of the run.
+rpca_status do_finish_check(rpca_ctx* c) {
+  cudaStream_t st = c->stream;
   uint32_t flags = 0;
   RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, c->err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   RPCA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -587,6 +600,11 @@ rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int
   if (flags & DEV_ERR_TIMEOUT) return fail(c, RPCA_ETIMEOUT, "a device-side wait timed out");
   if (flags & DEV_ERR_BREAKDOWN) return fail(c, RPCA_EBREAKDOWN, "Cholesky QR broke down");
   return RPCA_OK;
+}
+
+rpca_status do_finish(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, int64_t ldv) {
+  do_finish_enqueue(c, U, ldu, S, V, ldv);
+  return do_finish_check(c);
 }
 
 rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
@@ -699,6 +717,108 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   return RPCA_OK;
 }
 
+// --------------------------------------------------------------- batches
+// Many independent problems: one context each, spread over a pool of
+// streams forked from and joined to the caller's stream.  The first run is
+// executed directly (every lazy set-up happens outside a capture) and then
+// recorded once as a CUDA graph; later runs with the same buffers replay
+// that graph with one launch.
+__global__ void k_gather_flags(const uint32_t* const* __restrict__ src, int count, uint32_t* __restrict__ dst) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < count) dst[p] = *src[p];
+}
+
+}  // namespace
+
+struct rpca_batch {
+  std::vector<rpca_ctx*> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr, ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t caller = nullptr;         // problems[0].stream (may be the legacy stream)
+  cudaStream_t origin = nullptr;         // the batch's own stream: captured, ordered after caller
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> key;          // buffers the graph was recorded with
+  rpca::DevBuf err_ptrs, flags;          // device array of the contexts' error words, gathered words
+  std::vector<uint32_t> host_flags;
+  int bad = -1;                          // index of the last failing problem
+  std::string last_error;
+  ~rpca_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto* c : ctx) rpca_destroy(c);
+    for (auto e : ev_join) if (e) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    for (auto s : streams) if (s) cudaStreamDestroy(s);
+    if (origin) cudaStreamDestroy(origin);
+  }
+};
+
+namespace {
+
+void batch_enqueue(rpca_batch* b, const rpca_matrix* A, void* const* U, const int64_t* ldu, double* const* S,
+                   void* const* V, const int64_t* ldv) {
+  RPCA_CUDA_TRY(cudaEventRecord(b->ev_fork, b->origin));
+  for (auto st : b->streams) RPCA_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_fork, 0));
+  for (size_t p = 0; p < b->ctx.size(); ++p) {
+    rpca_ctx* c = b->ctx[p];
+    c->next_pass = 0;
+    while (do_pass(c, &A[p]) == RPCA_MORE) {
+    }
+    do_finish_enqueue(c, U ? U[p] : nullptr, ldu ? ldu[p] : 0, S ? S[p] : nullptr, V ? V[p] : nullptr,
+                      ldv ? ldv[p] : 0);
+  }
+  for (size_t s = 0; s < b->streams.size(); ++s) {
+    RPCA_CUDA_TRY(cudaEventRecord(b->ev_join[s], b->streams[s]));
+    RPCA_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_join[s], 0));
+  }
+  const int count = (int)b->ctx.size();
+  k_gather_flags<<<(unsigned)cdiv(count, 256), 256, 0, b->origin>>>(b->err_ptrs.as<const uint32_t*>(), count,
+                                                                    b->flags.as<uint32_t>());
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+rpca_status batch_check(rpca_batch* b) {
+  const int count = (int)b->ctx.size();
+  RPCA_CUDA_TRY(cudaMemcpyAsync(b->host_flags.data(), b->flags.ptr, count * sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, b->origin));
+  RPCA_CUDA_TRY(cudaEventRecord(b->ev_out, b->origin));
+  RPCA_CUDA_TRY(cudaStreamWaitEvent(b->caller, b->ev_out, 0));
+  RPCA_CUDA_TRY(cudaStreamSynchronize(b->origin));
+  for (int p = 0; p < count; ++p) {
+    const uint32_t f = b->host_flags[p];
+    if (f & (DEV_ERR_TIMEOUT | DEV_ERR_BREAKDOWN)) {
+      b->bad = p;
+      b->last_error = "problem " + std::to_string(p) +
+                      ((f & DEV_ERR_TIMEOUT) ? ": a device-side wait timed out" : ": Cholesky QR broke down");
+      return (f & DEV_ERR_TIMEOUT) ? RPCA_ETIMEOUT : RPCA_EBREAKDOWN;
+    }
+  }
+  return RPCA_OK;
+}
+
+template <typename Fn>
+rpca_status bguarded(rpca_batch* b, Fn&& fn) {
+  try {
+    return fn();
+  } catch (const CudaFailure& e) {
+    if (b) b->last_error = e.what;
+    if (e.code == cudaErrorMemoryAllocation) return RPCA_ENOMEM;
+    if (e.code == cudaErrorNoDevice || e.code == cudaErrorInsufficientDriver) return RPCA_ENODEV;
+    return RPCA_ECUDA;
+  } catch (const Invalid& e) {
+    if (b) b->last_error = e.what;
+    return RPCA_EINVAL;
+  } catch (const std::bad_alloc&) {
+    if (b) b->last_error = "host allocation failed";
+    return RPCA_ENOMEM;
+  }
+}
+
 }  // namespace
 
 // ================================================================== C-ABI
@@ -757,6 +877,121 @@ rpca_status rpca_run(const rpca_problem* p, const rpca_matrix* A, void* U, int64
   s = rpca_rerun(c, A, U, ldu, S, V, ldv);
   rpca_destroy(c);
   return s;
+}
+
+rpca_status rpca_batch_init(rpca_batch** out, int32_t count, const rpca_problem* problems, int32_t nstreams) {
+  if (!out) return RPCA_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !problems || nstreams < 1) return RPCA_EINVAL;
+  rpca_batch* b = new (std::nothrow) rpca_batch();
+  if (!b) return RPCA_ENOMEM;
+  rpca_status s = bguarded(b, [&] {
+    check_device();
+    for (int32_t p = 0; p < count; ++p) {
+      if (problems[p].flags & RPCA_HOST_A) throw Invalid("batched problems take device matrices");
+      if (problems[p].flags & RPCA_TIMING) throw Invalid("batched problems are not timed per phase");
+    }
+    b->caller = static_cast<cudaStream_t>(problems[0].stream);
+    RPCA_CUDA_TRY(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
+    RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+    RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+    const int ns = std::min<int32_t>(nstreams, count);
+    b->streams.assign(ns, nullptr);
+    b->ev_join.assign(ns, nullptr);
+    for (int i = 0; i < ns; ++i) {
+      RPCA_CUDA_TRY(cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking));
+      RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming));
+    }
+    RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    std::vector<const uint32_t*> ptrs(count);
+    for (int32_t p = 0; p < count; ++p) {
+      rpca_problem q = problems[p];
+      q.stream = b->streams[p % ns];
+      rpca_ctx* c = new rpca_ctx();
+      b->ctx.push_back(c);
+      rpca_status si = guarded(c, [&] { return do_init(c, &q); });
+      if (si != RPCA_OK) {
+        b->last_error = "problem " + std::to_string(p) + ": " + c->last_error;
+        return si;
+      }
+      ptrs[p] = c->err.as<uint32_t>();
+    }
+    b->err_ptrs.alloc(count * sizeof(uint32_t*));
+    b->flags.alloc(count * sizeof(uint32_t));
+    b->host_flags.assign(count, 0u);
+    RPCA_CUDA_TRY(cudaMemcpy(b->err_ptrs.ptr, ptrs.data(), count * sizeof(uint32_t*), cudaMemcpyHostToDevice));
+    return RPCA_OK;
+  });
+  if (s != RPCA_OK) {
+    last_batch_error() = b->last_error;
+    delete b;
+    return s;
+  }
+  *out = b;
+  return RPCA_OK;
+}
+
+rpca_status rpca_batch_run(rpca_batch* b, const rpca_matrix* A, void* const* U, const int64_t* ldu,
+                           double* const* S, void* const* V, const int64_t* ldv) {
+  if (!b || !A) return RPCA_EINVAL;
+  return bguarded(b, [&] {
+    const size_t count = b->ctx.size();
+    std::vector<const void*> key;
+    key.reserve(6 * count);
+    for (size_t p = 0; p < count; ++p) {
+      key.push_back(A[p].data);
+      key.push_back(reinterpret_cast<const void*>(A[p].ld));
+      key.push_back(A[p].col_scale);
+      key.push_back(U ? U[p] : nullptr);
+      key.push_back(S ? S[p] : nullptr);
+      key.push_back(V ? V[p] : nullptr);
+    }
+    // the batch runs after the caller's queued work
+    RPCA_CUDA_TRY(cudaEventRecord(b->ev_in, b->caller));
+    RPCA_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+    if (b->exec && key == b->key) {
+      RPCA_CUDA_TRY(cudaGraphLaunch(b->exec, b->origin));
+      count_launch();
+      return batch_check(b);
+    }
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+    }
+    // direct run (lazy set-up happens here), then record the graph
+    batch_enqueue(b, A, U, ldu, S, V, ldv);
+    rpca_status s = batch_check(b);
+    if (s != RPCA_OK) return s;
+    const uint64_t launches_before = g_launches.load();
+    RPCA_CUDA_TRY(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    try {
+      batch_enqueue(b, A, U, ldu, S, V, ldv);
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(b->origin, &g);
+      if (g) cudaGraphDestroy(g);
+      g_launches.store(launches_before);
+      throw;
+    }
+    g_launches.store(launches_before);     // recorded, not launched
+    RPCA_CUDA_TRY(cudaStreamEndCapture(b->origin, &b->graph));
+    RPCA_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->key = key;
+    return RPCA_OK;
+  });
+}
+
+void rpca_batch_destroy(rpca_batch* b) {
+  if (!b) return;
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  for (auto st : b->streams) cudaStreamSynchronize(st);
+  delete b;
+}
+
+const char* rpca_batch_last_error(const rpca_batch* b) {
+  return b ? b->last_error.c_str() : last_batch_error().c_str();
 }
 
 const char* rpca_strerror(rpca_status s) {

@@ -22,7 +22,8 @@ CENTER, HOST_A, SIMT, TIMING = 0x1, 0x2, 0x4, 0x8
 EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
            "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
            "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
-           "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc"]
+           "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc",
+           "rpca_batch_init", "rpca_batch_run", "rpca_batch_destroy", "rpca_batch_last_error"]
 
 
 class RpcaError(RuntimeError):
@@ -95,6 +96,15 @@ def load_library(path=None):
     lib.rpca_op_apply.restype = st
     lib.rpca_op_fused_pass_noalloc.argtypes = [i64, i64, i32, vp, i64, vp, i64, vp, i64, vp, i64, vp]
     lib.rpca_op_fused_pass_noalloc.restype = st
+    lib.rpca_batch_init.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Problem), i32]
+    lib.rpca_batch_init.restype = st
+    lib.rpca_batch_run.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                   ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64)]
+    lib.rpca_batch_run.restype = st
+    lib.rpca_batch_destroy.argtypes = [vp]
+    lib.rpca_batch_destroy.restype = None
+    lib.rpca_batch_last_error.argtypes = [vp]
+    lib.rpca_batch_last_error.restype = ctypes.c_char_p
     if path is None:
         _lib = lib
     return lib
@@ -242,6 +252,64 @@ def pca(A, k, l, i, seed=0, center=False, G=None, col_scale=None, simt=False):
         return ctx.run(A, col_scale=col_scale)
     finally:
         ctx.close()
+
+
+class Batch:
+    """Independent PCAs of uneven shapes run together (rpca_batch_*): one
+    context per problem over `nstreams` library streams; from the second run
+    with the same buffers on, one CUDA-graph launch per run."""
+
+    def __init__(self, shapes, k, l, i, dtype=BF16, seeds=None, nstreams=16, stream=None):
+        lib = load_library()
+        self.shapes = [(int(m), int(n)) for m, n in shapes]
+        self.k, self.dtype = k, dtype
+        cnt = len(self.shapes)
+        seeds = list(range(cnt)) if seeds is None else list(seeds)
+        sp = _stream_ptr(stream)
+        arr = (Problem * cnt)()
+        for p, (m, n) in enumerate(self.shapes):
+            arr[p] = Problem(m, n, k, l, i, ctypes.c_uint64(seeds[p]), None, dtype, 0, 0, sp)
+        self.ctx = ctypes.c_void_p()
+        status = lib.rpca_batch_init(ctypes.byref(self.ctx), cnt, arr, nstreams)
+        if status != OK:
+            raise RpcaError(status, lib.rpca_batch_last_error(None).decode())
+        self._keep = None
+
+    def run(self, As, outs=None):
+        """As: list of device tensors; returns [(U, S, V)] (allocated on the
+        first call unless given; pass the same list again to replay)."""
+        torch = _torch()
+        lib = load_library()
+        cnt = len(self.shapes)
+        cdt = torch.float64 if self.dtype == F64 else torch.float32
+        if outs is None:
+            outs = [(torch.empty(m, self.k, dtype=cdt, device="cuda"), torch.empty(self.k, dtype=torch.float64, device="cuda"),
+                     torch.empty(n, self.k, dtype=cdt, device="cuda")) for m, n in self.shapes]
+        mats = (Matrix * cnt)()
+        for p, A in enumerate(As):
+            mats[p] = Matrix(ctypes.c_void_p(A.data_ptr()), A.stride(0), None)
+        vp = ctypes.c_void_p
+        U = (vp * cnt)(*[vp(o[0].data_ptr()) for o in outs])
+        S = (vp * cnt)(*[vp(o[1].data_ptr()) for o in outs])
+        V = (vp * cnt)(*[vp(o[2].data_ptr()) for o in outs])
+        ldu = (ctypes.c_int64 * cnt)(*[o[0].stride(0) for o in outs])
+        ldv = (ctypes.c_int64 * cnt)(*[o[2].stride(0) for o in outs])
+        self._keep = (mats, U, S, V, ldu, ldv)
+        status = lib.rpca_batch_run(self.ctx, mats, U, ldu, S, V, ldv)
+        if status != OK:
+            raise RpcaError(status, lib.rpca_batch_last_error(self.ctx).decode())
+        return outs
+
+    def close(self):
+        if self.ctx:
+            load_library().rpca_batch_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --------------------------------------------------------------- single ops
