@@ -740,6 +740,7 @@ struct rpca_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> key;          // buffers the graph was recorded with
+  uint64_t graph_kernels = 0;            // kernels in the recorded graph
   rpca::DevBuf err_ptrs, flags;          // device array of the contexts' error words, gathered words
   std::vector<uint32_t> host_flags;
   int bad = -1;                          // index of the last failing problem
@@ -951,7 +952,7 @@ rpca_status rpca_batch_run(rpca_batch* b, const rpca_matrix* A, void* const* U, 
     RPCA_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
     if (b->exec && key == b->key) {
       RPCA_CUDA_TRY(cudaGraphLaunch(b->exec, b->origin));
-      count_launch();
+      count_launch(b->graph_kernels);
       return batch_check(b);
     }
     if (b->exec) {
@@ -975,6 +976,7 @@ rpca_status rpca_batch_run(rpca_batch* b, const rpca_matrix* A, void* const* U, 
       g_launches.store(launches_before);
       throw;
     }
+    b->graph_kernels = g_launches.load() - launches_before;
     g_launches.store(launches_before);     // recorded, not launched
     RPCA_CUDA_TRY(cudaStreamEndCapture(b->origin, &b->graph));
     RPCA_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
