@@ -74,6 +74,8 @@ typedef enum {
                                  out-of-core form of Section 4.2) */
 #define RPCA_SIMT       0x4u  /* force the CUDA-core pass kernels (testing) */
 #define RPCA_TIMING     0x8u  /* record per-phase CUDA-event times */
+#define RPCA_ADJOINT    0x10u /* keep what rpca_backward needs (m >= n, no
+                                 centring, device A) */
 
 typedef struct {
   int64_t m, n;           /* A is m x n; 1 <= k < min(m, n) */
@@ -206,6 +208,23 @@ uint64_t rpca_kernel_launches(void);
  * to ms (host), the run count to *runs (may be NULL); returns i+5, or 0
  * without RPCA_TIMING. */
 int32_t rpca_phase_times(rpca_ctx* c, double* ms, int32_t cap, int32_t* runs);
+
+/* ---------------------------------------------------------------------- */
+/* Adjoint.  The paper has no gradient; this differentiates the computed    */
+/* singular values with respect to A (G fixed).                             */
+/* ---------------------------------------------------------------------- */
+
+/* dA (m x n, ldda, device, FP64 for RPCA_F64 else FP32) = sum_j dS[j]
+ * d sigma_j / dA for the k singular values of the last completed run of a
+ * context created with RPCA_ADJOINT (A the same matrix, device memory).
+ * dS: k FP64 values in device memory.  Re-streams A 2 + 2i times (the
+ * blocks H^(j) are recomputed from the saved n x l blocks X^(j), not
+ * stored) and writes dA once as the product of two thin factors.  The
+ * losses sum_j sigma_j and ||A - U S V^T||_F^2 = ||A||_F^2 - sum_j sigma_j^2
+ * take dS = 1 and dS = -2 sigma (plus 2A).  RPCA_EBREAKDOWN if a small
+ * factor is singular. */
+rpca_status rpca_backward(rpca_ctx* c, const rpca_matrix* A, const double* dS,
+                          void* dA, int64_t ldda);
 
 /* ---------------------------------------------------------------------- */
 /* Batches of independent problems (uneven shapes).                        */

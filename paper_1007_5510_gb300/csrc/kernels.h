@@ -103,6 +103,21 @@ bool apply_slices(int64_t m, int64_t plane_rows, void* S, int lds, int x0, int n
                   int krows, int q, int64_t ldm, double alpha, int rl, bool beta, bool write_slices, float* Yf,
                   int64_t ldf, int qf, void* mt, cudaStream_t st, uint32_t* dev_err, const uint32_t* active);
 
+// ---------------------------------------------------------- adjoint
+// (k_adjoint.cu)  out = (M^-1)^T (p x p FP64, ld p), aug: p x 2p scratch.
+void small_inv_t(int p, const double* M, int64_t ldm, double* aug, double* out, uint32_t* dev_err, cudaStream_t st);
+// Mk (k x w) = diag(c) W[:, :k]^T, W w x w row-major FP64
+void make_mk(int k, int w, const double* c, const double* W, double* Mk, cudaStream_t st);
+// out = V diag(c) (rows x k, compute type)
+void scale_cols(bool f64, int64_t rows, int k, const void* V, int64_t ldv, const double* c, void* out, int64_t ldo,
+                cudaStream_t st);
+// dst += src (compute type)
+void add_matrix(bool f64, int64_t rows, int cols, const void* src, int64_t lds, void* dst, int64_t ldd,
+                cudaStream_t st);
+// G (m x n) = P Z^T, P m x r, Z n x r (compute type)
+void lowrank_out(bool f64, int64_t m, int64_t n, int r, const void* P, int64_t ldp, const void* Z, int64_t ldz,
+                 void* G, int64_t ldg, cudaStream_t st);
+
 void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub, double* W,
                 double* work, uint32_t* dev_err, cudaStream_t st);
 

@@ -275,6 +275,9 @@ struct rpca_ctx {
   std::string last_error;
 
   DevBuf X, F, H, T, Tc, shift, corr, d, vtmp, q1, G64, small, err, At, tiles[2], work, Hlo, Tlo, mt, slices;
+  // adjoint: saved X^(j) blocks and backward workspace
+  bool adjoint = false, fwd_done = false;
+  DevBuf Xsave, Bcat, XM, Hb, Tm, Xb64, Xb, Dn, Fb, Mw, Pf, Zf, bsmall;
   // H in three BF16 slices for the tensor-core QR (sliced_ok)
   bool sliced = false;
   int64_t hs_rows = 0;
@@ -347,7 +350,9 @@ void validate(const rpca_problem* p) {
   if (p->l > 255) throw Invalid("l > 255 is not supported");
   if ((int64_t)(p->i + 1) * p->l > 256) throw Invalid("(i+1) l > 256 is not supported");
   if (p->dtype < RPCA_F64 || p->dtype > RPCA_FP8E4M3) throw Invalid("unknown dtype");
-  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT | RPCA_TIMING)) throw Invalid("unknown flag");
+  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT | RPCA_TIMING | RPCA_ADJOINT)) throw Invalid("unknown flag");
+  if ((p->flags & RPCA_ADJOINT) && ((p->flags & (RPCA_CENTER | RPCA_HOST_A)) || p->n > p->m))
+    throw Invalid("RPCA_ADJOINT needs m >= n, no centring and device A");
   if ((p->flags & RPCA_HOST_A) && p->n > p->m) throw Invalid("RPCA_HOST_A needs n <= m");
 }
 
@@ -445,10 +450,12 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   const int j = c->next_pass;
   if (j == 0) {
     RPCA_CUDA_TRY(cudaMemsetAsync(c->err.ptr, 0, 64 * sizeof(uint32_t), st));
+    c->fwd_done = false;
     if (c->transposed)
       transpose(c->prob.dtype, c->m, c->n, Am->data, Am->ld, c->At.ptr, c->n, st);
     if (c->centered) compute_shift(c, Am);
     reset_x(c);
+    if (c->adjoint) copy_matrix(f64, f64, c->n, c->l, c->X.ptr, c->ldx, c->Xsave.ptr, c->l, st);
   }
   PassArgs a;
   a.dtype = c->prob.dtype;
@@ -490,6 +497,9 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
       block_qr(f64, c->n, 1, c->l, c->F.ptr, c->ldx, nullptr, nullptr, c->qs, c->dev_err(), st);
       std::swap(c->X.ptr, c->F.ptr);
       std::swap(c->X.bytes, c->F.bytes);
+      if (c->adjoint)
+        copy_matrix(f64, f64, c->n, c->l, c->X.ptr, c->ldx,
+                    static_cast<char*>(c->Xsave.ptr) + (size_t)(j + 1) * c->n * c->l * es, c->l, st);
     }
     c->next_pass = j + 1;
     return RPCA_MORE;
@@ -500,8 +510,8 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   const bool t16 = c->sliced && tpass_bf16_ok(c, Am);
   c->tic(c->i + 1);
   if (c->sliced)
-    block_qr_sliced(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows, c->E, !t16, c->qs,
-                    c->dev_err(), st);
+    block_qr_sliced(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows, c->E,
+                    !t16 || c->adjoint, c->qs, c->dev_err(), st);
   else
     block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->E, c->qs, c->dev_err(), st,
              c->Hlo.as<float>());
@@ -581,6 +591,7 @@ void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, in
                                     cudaMemcpyDefault, st));
   }
   if (S) RPCA_CUDA_TRY(cudaMemcpyAsync(S, c->S, c->k * sizeof(double), cudaMemcpyDefault, st));
+  c->fwd_done = true;
 }
 
 // Waits for the context stream and reports device-side errors of the run.
@@ -704,6 +715,26 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   std::vector<double> G((size_t)c->n * c->l);
   if (p->G) std::memcpy(G.data(), p->G, G.size() * sizeof(double));
   else gaussian_stream(p->seed, 0u, (int64_t)G.size(), G.data());
+  c->adjoint = (p->flags & RPCA_ADJOINT) != 0;
+  if (c->adjoint) {
+    const int64_t m = c->m, n = c->n;
+    const int k = c->k, l = c->l, i = c->i, w = c->w;
+    const int r = k + w + i * l;
+    c->Xsave.alloc((size_t)(i + 1) * n * l * es);
+    c->Bcat.alloc((size_t)m * 2 * w * es);
+    c->XM.alloc((size_t)n * 2 * w * es);
+    c->Hb.alloc((size_t)m * w * es);
+    c->Tm.alloc((size_t)m * l * es);
+    c->Xb64.alloc((size_t)n * l * sizeof(double));
+    c->Xb.alloc((size_t)n * l * es);
+    c->Dn.alloc((size_t)n * l * es);
+    c->Fb.alloc((size_t)std::max(1, i) * n * l * es);
+    c->Mw.alloc((size_t)n * w * es);
+    c->Pf.alloc((size_t)m * r * es);
+    c->Zf.alloc((size_t)n * r * es);
+    c->bsmall.alloc(((size_t)k * w + 3 * (size_t)w * w + 2 * (size_t)w * w + 3 * (size_t)l * l + 2 * (size_t)l * l) *
+                    sizeof(double));
+  }
   c->G64.alloc(G.size() * sizeof(double));
   RPCA_CUDA_TRY(cudaMemcpy(c->G64.ptr, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
   c->timing = (p->flags & RPCA_TIMING) != 0;
@@ -714,6 +745,127 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
     c->phase_ms.assign(nph, 0.0);
   }
   c->next_pass = 0;
+  return RPCA_OK;
+}
+
+// --------------------------------------------------------------- adjoint
+// Gradient of L(sigma_1..k) with respect to A, G fixed.  With T = A^T Q =
+// V~ S~ W^T and c_j = dL/dsigma_j, dL = <M, dT> for M = V~_k C W_k^T, so
+//   A-bar = Q M^T + (terms through Q),  Q-bar = A M.
+// L depends on each orthonormalised block only through its span, so for
+// any orthonormal X with span(X) = span(F) and R = X^T F the map F -> X
+// back-propagates as F-bar = (X-bar - X (X^T X-bar)) R^-T.  Through
+// H^(j) = A X^(j) and F^(j) = A^T H^(j):
+//   X-bar^(j) = A^T H-bar^(j),  A-bar += H-bar^(j) X^(j)T + H^(j-1) F-bar^(j-1)T,
+//   H-bar^(j-1) += A F-bar^(j-1),  R^(j-1) = X^(j)T F^(j-1) = H^(j)T H^(j-1).
+// A-bar is the thin product P Z^T with
+//   P = [U, H-bar^(0..i), H^(0..i-1)],  Z = [V C, X^(0..i), F-bar^(0..i-1)].
+rpca_status do_backward(rpca_ctx* c, const rpca_matrix* Am, const double* dS, void* dA, int64_t ldda) {
+  if (!c->adjoint) throw Invalid("context created without RPCA_ADJOINT");
+  if (!c->fwd_done) throw Invalid("backward before a completed run");
+  if (!Am || !Am->data || !dS || !dA) throw Invalid("null pointer");
+  const bool f64 = c->f64;
+  const size_t es = c->cbytes();
+  cudaStream_t st = c->stream;
+  const int64_t m = c->m, n = c->n;
+  const int k = c->k, l = c->l, i = c->i, w = c->w;
+  const int r = k + w + i * l;
+  if (ldda < n || Am->ld < n) throw Invalid("ld < n");
+  auto at = [&](const DevBuf& b, size_t elems) { return static_cast<char*>(b.ptr) + elems * es; };
+  PassArgs base;
+  base.dtype = c->prob.dtype;
+  base.A = Am->data;
+  base.lda = Am->ld;
+  base.m = m;
+  base.n = n;
+  base.scale = Am->col_scale;
+  auto pass_h = [&](const void* X, int64_t ldx, int p, void* Hout, int64_t ldh) {   // Hout = A X
+    PassArgs a = base;
+    a.mode = MODE_H;
+    a.X = X;
+    a.ldx = ldx;
+    a.p = p;
+    a.H = Hout;
+    a.ldh = ldh;
+    launch_pass_simt(a, st);
+  };
+  auto pass_t = [&](const void* Y, int64_t ldy, int p, double* Out, int64_t ldo) {   // Out = A^T Y (FP64)
+    PassArgs a = base;
+    a.mode = MODE_T;
+    a.p = p;
+    a.H = const_cast<void*>(Y);
+    a.ldh = ldy;
+    a.F = Out;
+    a.ldf = ldo;
+    a.f_f64 = true;
+    launch_pass_simt(a, st);
+  };
+  double* s = c->bsmall.as<double>();
+  double* Mk = s; s += (size_t)k * w;
+  double* RH = s; s += (size_t)w * w;
+  double* Bw = s; s += (size_t)w * w;
+  double* RHit = s; s += (size_t)w * w;
+  double* aug = s; s += 2 * (size_t)w * w;
+  double* Om = s; s += (size_t)l * l;
+  double* Rl = s; s += (size_t)l * l;
+  double* Rlit = s; s += (size_t)l * l;
+  double* augl = s;
+  uint32_t* err = c->dev_err();
+  RPCA_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), st));
+  // M = V C W_k^T (n x w)
+  make_mk(k, w, dS, c->W, Mk, st);
+  gemm_xm(f64, n, k, w, c->outV.ptr, k, Mk, w, 1.0, 0.0, c->Mw.ptr, w, st);
+  // [H | Q-bar] = A [X^(0..i) | M]  (H recomputed from the saved blocks)
+  for (int j = 0; j <= i; ++j)
+    copy_matrix(f64, f64, n, l, at(c->Xsave, (size_t)j * n * l), l, at(c->XM, (size_t)j * l), 2 * w, st);
+  copy_matrix(f64, f64, n, w, c->Mw.ptr, w, at(c->XM, (size_t)w), 2 * w, st);
+  if (2 * w <= 256) {
+    pass_h(c->XM.ptr, 2 * w, 2 * w, c->Bcat.ptr, 2 * w);
+  } else {
+    pass_h(c->XM.ptr, 2 * w, w, c->Bcat.ptr, 2 * w);
+    pass_h(at(c->XM, (size_t)w), 2 * w, w, at(c->Bcat, (size_t)w), 2 * w);
+  }
+  void* Hc = c->Bcat.ptr;
+  void* Qb = at(c->Bcat, (size_t)w);
+  // H-bar = (Q-bar - Q (Q^T Q-bar)) R_H^-T with R_H = Q^T H
+  gram(f64, m, w, w, c->H.ptr, w, Hc, 2 * w, RH, w, false, st);
+  gram(f64, m, w, w, c->H.ptr, w, Qb, 2 * w, Bw, w, false, st);
+  gemm_xm(f64, m, w, w, c->H.ptr, w, Bw, w, -1.0, 1.0, Qb, 2 * w, st);
+  small_inv_t(w, RH, w, aug, RHit, err, st);
+  gemm_xm(f64, m, w, w, Qb, 2 * w, RHit, w, 1.0, 0.0, c->Hb.ptr, w, st);
+  for (int j = i; j >= 1; --j) {
+    // X-bar^(j) = A^T H-bar^(j)
+    pass_t(at(c->Hb, (size_t)j * l), w, l, c->Xb64.as<double>(), l);
+    copy_matrix(true, f64, n, l, c->Xb64.ptr, l, c->Xb.ptr, l, st);
+    const void* Xj = at(c->Xsave, (size_t)j * n * l);
+    // F-bar^(j-1) = (X-bar - X (X^T X-bar)) R^-T,  R = H^(j)T H^(j-1)
+    gram(f64, n, l, l, Xj, l, c->Xb.ptr, l, Om, l, false, st);
+    copy_matrix(f64, f64, n, l, c->Xb.ptr, l, c->Dn.ptr, l, st);
+    gemm_xm(f64, n, l, l, Xj, l, Om, l, -1.0, 1.0, c->Dn.ptr, l, st);
+    gram(f64, m, l, l, at(c->Bcat, (size_t)j * l), 2 * w, at(c->Bcat, (size_t)(j - 1) * l), 2 * w, Rl, l, false, st);
+    small_inv_t(l, Rl, l, augl, Rlit, err, st);
+    void* Fbj = at(c->Fb, (size_t)(j - 1) * n * l);
+    gemm_xm(f64, n, l, l, c->Dn.ptr, l, Rlit, l, 1.0, 0.0, Fbj, l, st);
+    // H-bar^(j-1) += A F-bar^(j-1)
+    pass_h(Fbj, l, l, c->Tm.ptr, l);
+    add_matrix(f64, m, l, c->Tm.ptr, l, at(c->Hb, (size_t)(j - 1) * l), w, st);
+  }
+  // P = [U, H-bar, H^(0..i-1)],  Z = [V C, X^(0..i), F-bar^(0..i-1)]
+  copy_matrix(f64, f64, m, k, c->outU.ptr, k, c->Pf.ptr, r, st);
+  scale_cols(f64, n, k, c->outV.ptr, k, dS, c->Zf.ptr, r, st);
+  copy_matrix(f64, f64, m, w, c->Hb.ptr, w, at(c->Pf, (size_t)k), r, st);
+  for (int j = 0; j <= i; ++j)
+    copy_matrix(f64, f64, n, l, at(c->Xsave, (size_t)j * n * l), l, at(c->Zf, (size_t)(k + j * l)), r, st);
+  for (int j = 1; j <= i; ++j) {
+    copy_matrix(f64, f64, m, l, at(c->Bcat, (size_t)(j - 1) * l), 2 * w, at(c->Pf, (size_t)(k + w + (j - 1) * l)), r,
+                st);
+    copy_matrix(f64, f64, n, l, at(c->Fb, (size_t)(j - 1) * n * l), l, at(c->Zf, (size_t)(k + w + (j - 1) * l)), r, st);
+  }
+  lowrank_out(f64, m, n, r, c->Pf.ptr, r, c->Zf.ptr, r, dA, ldda, st);
+  uint32_t flags = 0;
+  RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (flags & DEV_ERR_BREAKDOWN) return fail(c, RPCA_EBREAKDOWN, "a small factor of the adjoint is singular");
   return RPCA_OK;
 }
 
@@ -878,6 +1030,11 @@ rpca_status rpca_run(const rpca_problem* p, const rpca_matrix* A, void* U, int64
   s = rpca_rerun(c, A, U, ldu, S, V, ldv);
   rpca_destroy(c);
   return s;
+}
+
+rpca_status rpca_backward(rpca_ctx* c, const rpca_matrix* A, const double* dS, void* dA, int64_t ldda) {
+  if (!c) return RPCA_EINVAL;
+  return guarded(c, [&] { return do_backward(c, A, dS, dA, ldda); });
 }
 
 rpca_status rpca_batch_init(rpca_batch** out, int32_t count, const rpca_problem* problems, int32_t nstreams) {

@@ -17,13 +17,14 @@ OK, MORE = 0, 1
 STATUS = {0: "RPCA_OK", 1: "RPCA_MORE", -1: "RPCA_EINVAL", -2: "RPCA_ENOMEM", -3: "RPCA_ECUDA",
           -4: "RPCA_ENODEV", -5: "RPCA_EBREAKDOWN", -6: "RPCA_ETIMEOUT", -7: "RPCA_ESTATE"}
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
-CENTER, HOST_A, SIMT, TIMING = 0x1, 0x2, 0x4, 0x8
+CENTER, HOST_A, SIMT, TIMING, ADJOINT = 0x1, 0x2, 0x4, 0x8, 0x10
 
 EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
            "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
            "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
            "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc",
-           "rpca_batch_init", "rpca_batch_run", "rpca_batch_destroy", "rpca_batch_last_error"]
+           "rpca_batch_init", "rpca_batch_run", "rpca_batch_destroy", "rpca_batch_last_error",
+           "rpca_backward"]
 
 
 class RpcaError(RuntimeError):
@@ -96,6 +97,8 @@ def load_library(path=None):
     lib.rpca_op_apply.restype = st
     lib.rpca_op_fused_pass_noalloc.argtypes = [i64, i64, i32, vp, i64, vp, i64, vp, i64, vp, i64, vp]
     lib.rpca_op_fused_pass_noalloc.restype = st
+    lib.rpca_backward.argtypes = [vp, ctypes.POINTER(Matrix), vp, vp, i64]
+    lib.rpca_backward.restype = st
     lib.rpca_batch_init.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Problem), i32]
     lib.rpca_batch_init.restype = st
     lib.rpca_batch_run.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(i64),
@@ -163,10 +166,11 @@ class PCA:
     """A context: rpca_init on construction, passes, finish, rerun."""
 
     def __init__(self, m, n, k, l, i, dtype=F32, seed=0, center=False, G=None, host_a=False,
-                 tile_rows=0, simt=False, stream=None, timing=False):
+                 tile_rows=0, simt=False, stream=None, timing=False, adjoint=False):
         lib = load_library()
         self.m, self.n, self.k, self.l, self.i, self.dtype = m, n, k, l, i, dtype
         flags = ((CENTER if center else 0) | (HOST_A if host_a else 0) | (SIMT if simt else 0)
+                 | (ADJOINT if adjoint else 0)
                  | (TIMING if timing else 0))
         self._G = None
         Gp = None
@@ -232,6 +236,19 @@ class PCA:
         n = load_library().rpca_phase_times(self.ctx, buf, 64, ctypes.byref(runs))
         return [buf[t] for t in range(n)], runs.value
 
+    def backward(self, A, dS, dA=None):
+        """dA = sum_j dS[j] dsigma_j/dA for the last run (context created with
+        adjoint=True; A the same device matrix).  dS: k values."""
+        torch = _torch()
+        cdt = torch.float64 if self.dtype == F64 else torch.float32
+        dS = torch.as_tensor(dS, dtype=torch.float64, device="cuda").contiguous()
+        if dA is None:
+            dA = torch.empty(self.m, self.n, dtype=cdt, device="cuda")
+        mat = self._matrix(A)
+        _check(load_library().rpca_backward(self.ctx, ctypes.byref(mat), _ptr(dS), _ptr(dA), dA.stride(0)),
+               self.ctx)
+        return dA
+
     def close(self):
         if self.ctx:
             load_library().rpca_destroy(self.ctx)
@@ -252,6 +269,45 @@ def pca(A, k, l, i, seed=0, center=False, G=None, col_scale=None, simt=False):
         return ctx.run(A, col_scale=col_scale)
     finally:
         ctx.close()
+
+
+def _pca_function():
+    torch = _torch()
+
+    class PCAFunction(torch.autograd.Function):
+        """(U, S, V) = rank-k PCA of A with gradients of S with respect to A
+        (G fixed by the seed); U and V take no gradient."""
+
+        @staticmethod
+        def forward(ctx, A, k, l, i, seed):
+            obj = PCA(A.shape[0], A.shape[1], k, l, i, dtype_code(A), seed=seed, adjoint=True)
+            U, S, V = obj.run(A.detach())
+            ctx.obj = obj
+            ctx.save_for_backward(A)
+            ctx.mark_non_differentiable(U, V)
+            return U, S, V
+
+        @staticmethod
+        def backward(ctx, gU, gS, gV):
+            (A,) = ctx.saved_tensors
+            dA = None
+            if gS is not None:
+                dA = ctx.obj.backward(A.detach(), gS.to(torch.float64)).to(A.dtype)
+            ctx.obj.close()
+            return dA, None, None, None, None
+
+    return PCAFunction
+
+
+_PCAF = None
+
+
+def pca_autograd(A, k, l, i, seed=0):
+    """Differentiable rank-k PCA: (U, S, V) with S differentiable in A."""
+    global _PCAF
+    if _PCAF is None:
+        _PCAF = _pca_function()
+    return _PCAF.apply(A, k, l, i, seed)
 
 
 class Batch:
