@@ -29,6 +29,17 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="precision", m=1_000_000, n=4096, k=50, l=60, i=2, seed=1007)
+
+
+def max_over_ranks(ms, world, dist, device=None):
+    """Slowest rank's time (the whole job's): all-reduce MAX over the process
+    group (a CUDA tensor under NCCL, a CPU tensor under gloo)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 CPU_SAMPLE_ROWS = 150_000     # cpu_baseline: one oracle PCA on this many rows (~13 s)
 REF_SAMPLE_ROWS = 40_000      # --impl reference: rows per timed step
 # DRAM bytes (read + write) per row of A of one launch of the BF16 tensor-core
@@ -43,7 +54,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--m", type=int, default=WORKLOAD["m"])
+    ap.add_argument("--rows", "--m", dest="m", type=int, default=WORKLOAD["m"],
+                    help="rows of A (precision workload; the oracle arm's sample is capped by it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--simt", action="store_true", help="force the CUDA-core pass kernels")
@@ -195,10 +207,7 @@ def main():
         if world > 1:
             dist.barrier()
         ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world, dist, dev)
         return ms
 
     for _ in range(args.warmup):
@@ -354,10 +363,7 @@ def end_to_end(ctx, A_dev, m, n, k, i, b, steps, dev, world, dist):
     ev1.record(st)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dist, dev)
     t = ms / steps / 1e3
     return {"value": round(world * (i + 2) * m * n * b / t / 1e9, 2), "unit": "GB/s",
             "s_per_pca": round(t, 6), "h2d_bytes_per_step": m * n * b,
@@ -401,10 +407,7 @@ def run_batched(args, world, rank, local, dist):
     ms = ev0.elapsed_time(ev1)
     launches = rpca.kernel_launches() - launches0
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dist, dev)
     t = ms / args.steps / 1e3
     a_bytes = sum(m * n * 2 for m, n in shapes)
     hbm, peak_kind = peaks()
