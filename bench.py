@@ -183,25 +183,28 @@ def main():
     t0 = time.perf_counter()
     A32 = gen.workload_torch("precision", dev, m=m, n=n, seed=W["seed"] + rank, rank_cap=1024)
     A16 = A32.to(torch.bfloat16)
+    A8, s8 = gen.quantize_fp8_torch(A32)          # FP8-e4m3 bytes + per-column FP32 scales
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
 
     stream = torch.cuda.current_stream()
     ctx16 = rpca.PCA(m, n, k, l, i, rpca.BF16, seed=W["seed"], timing=True, simt=args.simt)
     ctx32 = rpca.PCA(m, n, k, l, i, rpca.F32, seed=W["seed"], timing=True, simt=args.simt)
+    ctx8 = rpca.PCA(m, n, k, l, i, rpca.FP8E4M3, seed=W["seed"], timing=True, simt=args.simt)
     U16 = torch.empty(m, k, device=dev)
     V16 = torch.empty(n, k, device=dev)
     S16 = torch.empty(k, dtype=torch.float64, device=dev)
     U32, V32, S32 = torch.empty_like(U16), torch.empty_like(V16), torch.empty_like(S16)
+    U8, V8, S8 = torch.empty_like(U16), torch.empty_like(V16), torch.empty_like(S16)
 
-    def timed(ctx, A, U, S, V, steps):
+    def timed(ctx, A, U, S, V, steps, col_scale=None):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(steps):
-            ctx.run(A, U=U, S=S, V=V)
+            ctx.run(A, col_scale=col_scale, U=U, S=S, V=V)
         ev1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -213,9 +216,11 @@ def main():
     for _ in range(args.warmup):
         ctx16.run(A16, U=U16, S=S16, V=V16)
         ctx32.run(A32, U=U32, S=S32, V=V32)
+        ctx8.run(A8, col_scale=s8, U=U8, S=S8, V=V8)
     torch.cuda.synchronize()
     ctx16.phase_times()
     ctx32.phase_times()
+    ctx8.phase_times()
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -223,9 +228,12 @@ def main():
     ms16 = timed(ctx16, A16, U16, S16, V16, args.steps)
     launches = rpca.kernel_launches() - launches0
     ms32 = timed(ctx32, A32, U32, S32, V32, args.steps)
+    ms8 = timed(ctx8, A8, U8, S8, V8, args.steps, col_scale=s8)
     clocks = sampler.stop()
     ph16, runs16 = ctx16.phase_times()
     ph32, runs32 = ctx32.phase_times()
+    ph8, runs8 = ctx8.phase_times()
+    t8 = ms8 / args.steps / 1e3
 
     t16 = ms16 / args.steps / 1e3
     t32 = ms32 / args.steps / 1e3
@@ -252,7 +260,7 @@ def main():
     acc = {"sigma_rel_bf16_vs_f32": float(abs(s16 - s32).max() / s32.max()),
            "sigma_1": float(s32[0]), "sigma_k": float(s32[-1])}
     try:
-        acc.update(spectral_errors(A32, [(U32, S32, V32), (U16, S16, V16)], ["f32", "bf16"]))
+        acc.update(spectral_errors(A32, [(U32, S32, V32), (U16, S16, V16), (U8, S8, V8)], ["f32", "bf16", "fp8"]))
     except Exception as e:  # measurement only
         acc["spectral_error_failed"] = str(e)[:200]
 
@@ -289,6 +297,9 @@ def main():
                      "s_per_pca": round(t32, 6), "fused_pass_ms": round(fused_ms32, 4),
                      "phases_ms": phases32},
             "bf16_speedup_vs_fp32": round(t32 / t16, 3),
+            "fp8": {"value": round(world * (i + 2) * m * n * 1 / t8 / 1e9, 2), "unit": "GB/s",
+                    "s_per_pca": round(t8, 6), "kernels": "cuda-cores (FP8 bytes, per-column scales)",
+                    "phases_ms": {nm: round(v / max(1, runs8), 4) for nm, v in zip(names, ph8)}},
             "phases_ms": phases16,
             "roofline": {"bound": "hbm", "kernel": "fused pass (BF16, l=%d)" % l,
                          "achieved": round(achieved, 2), "peak": hbm, "peak_kind": peak_kind,
@@ -307,6 +318,7 @@ def main():
         print(json.dumps(line))
     ctx16.close()
     ctx32.close()
+    ctx8.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -329,8 +341,8 @@ def spectral_errors(A, outs, labels, iters=30, nvec=4):
             est = float(torch.sqrt(nz.max() / torch.linalg.norm(x, dim=0)[nz.argmax()]))
             x = torch.linalg.qr(z.cpu())[0].to(z.device)   # n x nvec: small
         res["spectral_error_" + lab] = est
-    if len(labels) == 2:
-        res["spectral_error_ratio_bf16_over_f32"] = res["spectral_error_bf16"] / res["spectral_error_f32"]
+    for lab in labels[1:]:
+        res["spectral_error_ratio_%s_over_f32" % lab] = res["spectral_error_" + lab] / res["spectral_error_f32"]
     return res
 
 

@@ -420,3 +420,19 @@ def test_pca_ordered_after_callers_default_stream_work():
     U, S, V = R().pca(Ad, k, l, i, seed=3)
     torch.cuda.synchronize()
     assert np.max(np.abs(S.cpu().numpy() - ref[1].cpu().numpy()) / ref[1].cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("m,n", [(20_000, 512), (9_001, 333)])
+def test_pca_fp8_column_scaled_matches_oracle(m, n):
+    """FP8-e4m3 storage with per-column FP32 scales: the PCA of the stored
+    matrix diag-scaled (A~ = A8 diag(s)), against the oracle on the same
+    dequantised values; FP32 arithmetic, so the FP32 tolerances apply."""
+    rng = np.random.default_rng(m + n)
+    A = gen.lowrank_np(m, n, np.exp(-np.arange(1, n + 1) / 20.0), seed=8) + 1e-3 * rng.standard_normal((m, n))
+    At = torch.from_numpy(A.astype(np.float32)).cuda()
+    q, s = gen.quantize_fp8_torch(At)
+    k, l, i = 10, 12, 2
+    U, S, V = R().pca(q, k, l, i, seed=5, col_scale=s)
+    Adq = (q.view(torch.float8_e4m3fn).float() * s[None, :]).double().cpu().numpy()
+    Uo, So, Vo = ro.rpca(Adq, k, l, i, seed=5, normalize=True)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
