@@ -197,7 +197,9 @@ rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w,
 rpca_status rpca_gaussian(uint64_t seed, uint32_t domain, int64_t count,
                           double* out);
 
-/* Number of the library's own kernels launched since load (all devices). */
+/* Number of the library's own kernels launched since load (all devices).
+ * A replay of a batch's captured CUDA graph adds the number of kernels the
+ * graph holds. */
 uint64_t rpca_kernel_launches(void);
 
 /* Per-phase device times of a context created with RPCA_TIMING, summed
