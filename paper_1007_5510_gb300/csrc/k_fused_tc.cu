@@ -531,6 +531,9 @@ bool dispatch_l(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
 
 bool fused_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   if (a.dtype != RPCA_BF16) return false;
+  // the L2 re-read form first (RPCA_FUSED_HELD=1 selects this held-tile form)
+  static const bool held = getenv("RPCA_FUSED_HELD") != nullptr;
+  if (!held && fused_pass_rr(a, st, dev_err)) return true;
   if (a.mode != MODE_FUSED && a.mode != MODE_H) return false;
   if (a.shift || a.scale || !a.work) return false;
   if (a.ones_col >= 0 && a.ones_col != a.p) return false;

@@ -805,7 +805,8 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
   k_svd_finish<<<1, 256, smem, st>>>(w, B64, W0, S, Ub, W);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
-  if (getenv("RPCA_DEBUG")) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (getenv("RPCA_DEBUG") && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
     uint32_t sw[2] = {0, 0};
     cudaMemcpyAsync(sw, dev_err + 8, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
