@@ -179,7 +179,7 @@ struct RRParams {
 //   [GEMM1 ring: nh x (128 rows x 128 B)]
 //   [GEMM2 ring: nf x (2 boxes of 64 rows x 128 B)]      (FUSED)
 //   [Rcv[2]: per epilogue group, CS senders x 128/CS rows x L/2 FP32]
-//   [Hs: 128 rows x 128 B BF16, SW128 MN-major operand]  (FUSED)
+//   [Hs[2]: 128 rows x 128 B BF16, SW128 MN-major operand] (FUSED; panel it uses Hs[it & 1])
 //   [barriers]
 template <int L, bool FUSED>
 __global__ void __launch_bounds__(RR_THREADS, 1)
@@ -198,7 +198,7 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   unsigned char* fring = hring + (size_t)p.nh * RR_HBOX;
   unsigned char* rcvbase = fring + (size_t)p.nf * RR_FST;
   unsigned char* hs = rcvbase + 2 * RCV_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(hs + (FUSED ? RR_HS : 0));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(hs + (FUSED ? 2 * RR_HS : 0));
   uint64_t* hfull = bars;                     // [nh]
   uint64_t* hempty = hfull + p.nh;            // [nh]
   uint64_t* ffull = hempty + p.nh;            // [nf]
@@ -207,9 +207,9 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   uint64_t* pempty = pfull + 2;               // [2]
   uint64_t* rfull = pempty + 2;               // [2] every sender's rows have reached Rcv[g]
   uint64_t* rfree = rfull + 2;                // [2] every owner has summed this CTA's rows
-  uint64_t* hready = rfree + 2;               // every owner's rows of H_b have reached Hs
-  uint64_t* hfree = hready + 1;               // every CTA's GEMM2 has read its Hs
-  uint64_t* xfull = hfree + 1;
+  uint64_t* hready = rfree + 2;               // [2] every owner's rows of H_b have reached Hs[x]
+  uint64_t* hfree = hready + 2;               // [2] every CTA's GEMM2 has read its Hs[x]
+  uint64_t* xfull = hfree + 2;
   uint64_t* done1 = xfull + 1;                // GEMM1 issuer's last MMA
   uint64_t* done2 = done1 + 1;                // GEMM2 issuer's last MMA
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done2 + 1);
@@ -241,8 +241,10 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       tc::mbar_init(&rfull[x], 1);            // the owner's arming arrival + bytes
       tc::mbar_init(&rfree[x], cs);
     }
-    tc::mbar_init(hready, 1);                 // GEMM2's arming arrival + bytes
-    tc::mbar_init(hfree, cs);
+    for (int x = 0; x < 2; ++x) {
+      tc::mbar_init(&hready[x], 1);           // GEMM2's arming arrival + bytes
+      tc::mbar_init(&hfree[x], cs);
+    }
     tc::mbar_init(xfull, 1);
     tc::mbar_init(done1, 1);
     tc::mbar_init(done2, 1);
@@ -250,7 +252,10 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     tc::fence_mbar_init();
     tc::mbar_arrive_expect_tx(&rfull[0], RCV_BYTES);
     tc::mbar_arrive_expect_tx(&rfull[1], RCV_BYTES);
-    if (FUSED) tc::mbar_arrive_expect_tx(hready, HS_TX);
+    if (FUSED) {
+      tc::mbar_arrive_expect_tx(&hready[0], HS_TX);
+      tc::mbar_arrive_expect_tx(&hready[1], HS_TX);
+    }
     tc::tma_prefetch(&tmA);
     if (FUSED) tc::tma_prefetch(&tmA2);
     tc::tma_prefetch(&tmX);
@@ -359,13 +364,14 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       int64_t q = 0;
       bool ok = true;
       for (int64_t it = 0; ok && it < my_pan; ++it) {
-        if (!tc::mbar_wait(hready, (uint32_t)(it & 1), p.dev_err, abort_flag, true)) break;
-        // Hs was written by the owners' asynchronous stores; order them
+        const int x = (int)(it & 1);
+        if (!tc::mbar_wait(&hready[x], (uint32_t)((it >> 1) & 1), p.dev_err, abort_flag, true)) break;
+        // Hs[x] was written by the owners' asynchronous stores; order them
         // before the tensor core's reads
         tc::fence_proxy_async_smem();
         tc::tc_fence_after();
-        // arm the next panel's phase (all owners' bytes of H_b)
-        tc::mbar_arrive_expect_tx(hready, HS_TX);
+        // arm the buffer's next use (panel it + 2: all owners' bytes of H)
+        tc::mbar_arrive_expect_tx(&hready[x], HS_TX);
         for (int u = 0; u < 2 * RR_NT; ++u, ++q) {
           const int t = u >> 1, h = u & 1;
           const int s = (int)(q % p.nf);
@@ -375,7 +381,7 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
           }
           tc::tc_fence_after();
           const uint64_t da = tc::sdesc_sw128(tc::smem_u32(fring + (size_t)s * RR_FST), RR_FHALF, 1024);
-          const uint64_t db = tc::sdesc_sw128(hs_a + (uint32_t)h * 8192u, RR_HS, 1024);
+          const uint64_t db = tc::sdesc_sw128(hs_a + (uint32_t)x * RR_HS + (uint32_t)h * 8192u, RR_HS, 1024);
 #pragma unroll
           for (int kr = 0; kr < 4; ++kr)
             tc::mma_f16(tm_f + t * L, tc::sdesc_add(da, kr * 2048), tc::sdesc_add(db, kr * 2048), idesc2,
@@ -383,7 +389,7 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
           tc::mma_commit(&fempty[s]);
         }
         if (!ok) break;
-        tc::mma_commit_multicast(hfree, cmask);
+        tc::mma_commit_multicast(&hfree[x], cmask);
       }
       tc::mma_commit(done2);
     }
@@ -405,7 +411,7 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     const uint32_t owner = (uint32_t)(trow / rpc);
     const uint32_t dst_row = mapa(rcv_a + (uint32_t)((int)crank * rpc + trow % rpc) * ROWB, owner);
     const uint32_t dst_bar = mapa(tc::smem_u32(my_rfull), owner);
-    const uint32_t hready_a = tc::smem_u32(hready);
+    const uint32_t hready_a = tc::smem_u32(hready);     // + 8 x for Hs[x]
     bool ok = true;
     for (int64_t it = 0; it < my_pan; ++it) {
       const int pb = (int)(it & 1);
@@ -428,8 +434,8 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       if (lane == 0) tc::mbar_arrive(&pempty[pb]);
       // every sender's rows of this panel have arrived
       ok = tc::mbar_wait(my_rfull, (uint32_t)(it & 1), p.dev_err, abort_flag, true);
-      // every CTA's GEMM2 of the previous panel has read its Hs
-      if (FUSED) ok = ok && tc::mbar_wait(hfree, (uint32_t)((it - 1) & 1), p.dev_err, abort_flag, true);
+      // every CTA's GEMM2 of panel it - 2 has read its Hs[it & 1]
+      if (FUSED) ok = ok && tc::mbar_wait(&hfree[pb], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag, true);
       ok = grp_bar_and(g, ok);
       if (!ok) break;
       if (e == 0) tc::mbar_arrive_expect_tx(my_rfull, RCV_BYTES);   // arm the next panel
@@ -456,10 +462,12 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
           if (cc == p.ones_col && grow < p.m) vv[qq] = 1.f;
         }
         if (FUSED) {
-          // row rr of Hs (SW128, MN-major), in every CTA of the cluster
-          const uint32_t hoff = (uint32_t)(rr * 128 + ((((col >> 3) ^ (rr & 7))) << 4) + (col & 7) * 2);
+          // row rr of Hs[pb] (SW128, MN-major), in every CTA of the cluster
+          const uint32_t hoff = (uint32_t)pb * RR_HS +
+                                (uint32_t)(rr * 128 + ((((col >> 3) ^ (rr & 7))) << 4) + (col & 7) * 2);
           const uint32_t lo = pack_bf16(vv[0], vv[1]), hi = pack_bf16(vv[2], vv[3]);
-          for (uint32_t c = 0; c < cs; ++c) st_async_v2(mapa(hs_a + hoff, c), lo, hi, mapa(hready_a, c));
+          const uint32_t rb = hready_a + 8u * (uint32_t)pb;
+          for (uint32_t c = 0; c < cs; ++c) st_async_v2(mapa(hs_a + hoff, c), lo, hi, mapa(rb, c));
         }
         if (grow < p.m) {
           float* hrow = p.H + grow * p.ldh;
@@ -566,12 +574,12 @@ bool launch_rr(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   p.n = a.n;
   p.l = a.p;
   p.ones_col = a.ones_col;
-  // X slab, two receive buffers (RR_BM x L/2 FP32 each), Hs, barriers
-  const size_t fixed = 1024 + (size_t)RR_NBOX * L * 128 + (size_t)RR_BM * L * 4 + (FUSED ? RR_HS : 0) + 512;
+  // X slab, two receive buffers (RR_BM x L/2 FP32 each), Hs[2], barriers
+  const size_t fixed = 1024 + (size_t)RR_NBOX * L * 128 + (size_t)RR_BM * L * 4 + (FUSED ? 2 * RR_HS : 0) + 512;
   if (fixed + 4 * (size_t)RR_HBOX > RR_SMEM_LIMIT) return false;
   const int total = (int)((RR_SMEM_LIMIT - fixed) / RR_HBOX);
   if (FUSED) {
-    p.nf = std::max(2, std::min(4, total * 3 / 7));
+    p.nf = std::max(2, std::min(4, (total + 1) / 2));
     p.nh = std::min(8, total - p.nf);
   } else {
     p.nf = 0;
