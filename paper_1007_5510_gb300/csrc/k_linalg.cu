@@ -146,15 +146,268 @@ k_gemm_xm(int64_t m, int p, int q, const TC* __restrict__ X, int64_t ldx,
 // --------------------------------------------------------------- Cholesky
 // One CTA.  G = R^T R (R upper), then Rinv by back substitution, both in
 // shared memory (p <= 64) or global memory (larger p).
-// Pass `pass` (0..3) of a Cholesky-QR sequence on one block (qf: 4 words
-// private to the block: qf[0] = which passes needed a shift, qf[2], qf[3] =
-// whether passes 2 and 3 run).  A pivot below piv_rel * max(diag G) retries
-// with G + shift_rel * max(diag G) I (shifted Cholesky QR); passes 2-3 only
-// run after a shifted pass and otherwise leave identities (exact no-ops).
+// Pass `pass` (0..kCholPasses-1) of a Cholesky-QR sequence on one block (qf:
+// kQfWords words private to the block: qf[0] = which passes needed a shift,
+// qf[1] = some pass needed one (gates the re-orthogonalisation against the
+// earlier blocks), qf[p] (p >= 2) = whether pass p runs).
+// A pivot below piv_rel * max(diag G) retries with G + shift_rel * max(diag G) I
+// (shifted Cholesky QR); pass p >= 2 runs only if pass p-1 or p-2 needed a
+// shift, and otherwise leaves identities (exact no-ops).  Each shifted pass
+// multiplies the directions a numerically rank-deficient block is missing by
+// about 1/sqrt(shift_rel), so a block whose missing directions start at the
+// rounding level needs a few of them before an unshifted pass.
+// 1 / sqrt(d) for d > 0 in FP64: an FP32 seed refined by Newton-Raphson
+// steps y <- y (3 - d y^2) / 2 (quadratic convergence: ~2^-22 -> 2^-44 ->
+// below FP64 rounding).  A short chain of multiplies instead of a division
+// and a square root; one step (2^-44) when the factor only feeds FP32 work.
+__device__ __forceinline__ double rsqrt_newton(double d, bool two_steps) {
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  if (two_steps) y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
+// p <= 64, in shared memory.  FP64 Cholesky by 16-column blocks: warp 0
+// factors the diagonal block (warp-synchronous), then the whole CTA solves
+// the block row (one column per thread) and updates the trailing triangle.
+// Rinv = R^-1 = U^-1 D^-1 with R = D U (U unit upper triangular): U^-1 by
+// right-looking elimination, one barrier per step (U^-1's row k is final at
+// step k), then scaled by columns; in FP32 when inv_f32 (the factor then
+// only feeds FP32 / BF16-slice products, whose own rounding is of the same
+// order), else FP64.
 __global__ void __launch_bounds__(256)
 k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Rout,
        double* __restrict__ Rinvout, int pass, double piv_rel, double shift_rel, uint32_t* qf,
-       uint32_t* dev_err) {
+       uint32_t* dev_err, int inv_f32, const uint32_t* __restrict__ gate) {
+  if (gate && *gate == 0u) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int fail;
+  __shared__ double dmax;
+  __shared__ double dinv[64];
+  extern __shared__ double sm_chol[];
+  const int ps = p | 1;                                  // odd row stride (banks)
+  double* R = sm_chol;                                   // p x ps
+  double* X64 = sm_chol + p * ps;                        // p x ps (FP64 inverse)
+  float* X32 = reinterpret_cast<float*>(X64);            // p x ps (FP32 inverse)
+  const bool active = (pass < 2) || (qf[pass] != 0u);
+  if (!active) {
+    for (int e = tid; e < p * p; e += blockDim.x) {
+      double v = (e / p == e % p) ? 1.0 : 0.0;
+      Rout[e] = v;
+      Rinvout[e] = v;
+    }
+    if (tid == 0 && pass + 1 < kCholPasses) qf[pass + 1] = 0u;
+    return;
+  }
+  if (tid == 0) {
+    dmax = 0.0;
+    if (pass == 0) {
+      qf[0] = 0u;
+      qf[1] = 0u;
+    }
+  }
+  // G -> shared memory (all of it: the near-identity branch reads it all)
+  for (int e = tid; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    R[i * ps + j] = G[(int64_t)i * ldg + j];
+  }
+  __syncthreads();
+  for (int i = tid; i < p; i += blockDim.x) {
+    // diagonal entries are non-negative: their bit patterns order like integers
+    atomicMax(reinterpret_cast<unsigned long long*>(&dmax),
+              (unsigned long long)__double_as_longlong(fmax(R[i * ps + i], 0.0)));
+  }
+  __syncthreads();
+  if (pass >= 1) {
+    // A later pass of the sequence sees G = I + E with E tiny.  Then
+    // M = (I + E)^(-1/2) = I - E/2 + 3/8 E^2 + O(E^3) orthonormalises the
+    // block as well as R^-1 does (same span, (H M)^T (H M) = I + O(E^3)),
+    // and its inverse is I + E/2 - E^2/8 + O(E^3).  E^2 only needs a few
+    // digits: it is formed in FP32.
+    __shared__ unsigned long long emax_bits;
+    if (tid == 0) emax_bits = 0ull;
+    __syncthreads();
+    {
+      // max |G - I| (non-negative doubles order like their bit patterns):
+      // per thread, then per warp, then one shared atomic per warp
+      unsigned long long mb = 0ull;
+      for (int e = tid; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e % p;
+        const double d = fabs(R[i * ps + j] - (i == j ? 1.0 : 0.0));
+        const unsigned long long b = (unsigned long long)__double_as_longlong(isfinite(d) ? d : 1e300);
+        mb = b > mb ? b : mb;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = t > mb ? t : mb;
+      }
+      if (lane == 0) atomicMax(&emax_bits, mb);
+    }
+    __syncthreads();
+    if (__longlong_as_double((long long)emax_bits) < 2e-3) {
+      float* Ef = X32;                                   // p x ps
+      for (int e = tid; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e % p;
+        Ef[i * ps + j] = (float)(R[i * ps + j] - (i == j ? 1.0 : 0.0));
+      }
+      __syncthreads();
+      // E^2 in strips of 4 columns (independent accumulators)
+      const int nst = (p + 3) / 4;
+      for (int t = tid; t < p * nst; t += blockDim.x) {
+        const int i = t / nst, j0 = 4 * (t % nst);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < p; ++k) {
+          const float a = Ef[i * ps + k];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (j0 + u < p) acc[u] = fmaf(a, Ef[k * ps + j0 + u], acc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          if (j >= p) break;
+          const double exact = R[i * ps + j] - (i == j ? 1.0 : 0.0);
+          const double id = i == j ? 1.0 : 0.0;
+          Rinvout[i * p + j] = id - 0.5 * exact + 0.375 * (double)acc[u];
+          Rout[i * p + j] = id + 0.5 * exact - 0.125 * (double)acc[u];
+        }
+      }
+      if (tid == 0) {
+        if (pass + 1 < kCholPasses) qf[pass + 1] = ((qf[0] >> (pass - 1)) & 3u) ? 1u : 0u;
+      }
+      return;
+    }
+  }
+  bool shifted = false;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const double shift = (attempt == 0) ? 0.0 : shift_rel * dmax;
+    // the shifted retry: a missing direction's pivot is the shift plus or
+    // minus rounding, so only a pivot below half the shift is a failure
+    const double piv_min = (attempt == 0) ? piv_rel * dmax : 0.5 * shift;
+    if (attempt == 1) {
+      // restart from G + shift I (upper triangle)
+      for (int e = tid; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e % p;
+        if (j >= i) R[i * ps + j] = G[(int64_t)i * ldg + j] + (i == j ? shift : 0.0);
+      }
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int kb = 0; kb < p; kb += 16) {
+      const int bs = min(16, p - kb);
+      if (warp == 0) {
+        // ---- diagonal block [kb, kb + bs): right-looking, warp-synchronous
+        for (int k = kb; k < kb + bs; ++k) {
+          const double d = R[k * ps + k];
+          const bool bad = !(d > piv_min) || !isfinite(d);
+          if (bad) {
+            if (lane == 0) fail = 1;
+            break;
+          }
+          double y = 0.0;
+          if (lane == 0) y = rsqrt_newton(d, !inv_f32);
+          y = __shfl_sync(0xffffffffu, y, 0);
+          const int j = kb + lane;
+          if (lane == 0) dinv[k] = y;
+          if (j > k && j < kb + bs) R[k * ps + j] *= y;
+          if (j == k) R[k * ps + k] = d * y;
+          __syncwarp();
+          // rank-1 update of the block's trailing triangle, element-parallel
+          const int r = kb + bs - k - 1;                 // trailing size
+          for (int e = lane; e < r * r; e += 32) {
+            const int ii = k + 1 + e / r, jj = k + 1 + e % r;
+            if (jj >= ii) R[ii * ps + jj] -= R[k * ps + ii] * R[k * ps + jj];
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      if (fail) break;
+      // ---- block row: R[kb+t][c] for c >= kb + bs, forward substitution
+      for (int c = kb + bs + tid; c < p; c += blockDim.x) {
+        for (int k = kb; k < kb + bs; ++k) {
+          double v = R[k * ps + c];
+          for (int t = kb; t < k; ++t) v -= R[t * ps + k] * R[t * ps + c];
+          R[k * ps + c] = v * dinv[k];
+        }
+      }
+      __syncthreads();
+      // ---- trailing update: R[i][j] -= sum_t R[t][i] R[t][j], i <= j
+      const int r0 = kb + bs, rn = p - r0;
+      for (int e = tid; e < rn * rn; e += blockDim.x) {
+        const int i = r0 + e / rn, j = r0 + e % rn;
+        if (j < i) continue;
+        double v = R[i * ps + j];
+        for (int t = kb; t < kb + bs; ++t) v -= R[t * ps + i] * R[t * ps + j];
+        R[i * ps + j] = v;
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!fail) break;
+    if (attempt == 1 || !(dmax > 0.0) || !isfinite(dmax)) {
+      if (tid == 0) atomicOr(dev_err, DEV_ERR_BREAKDOWN);
+      for (int e = tid; e < p * p; e += blockDim.x) {
+        double v = (e / p == e % p) ? 1.0 : 0.0;
+        Rout[e] = v;
+        Rinvout[e] = v;
+      }
+      return;
+    }
+    shifted = true;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (shifted) {
+      qf[0] |= 1u << pass;
+      qf[1] = 1u;
+      atomicOr(dev_err, DEV_ERR_SHIFTED);
+      if (pass == kCholPasses - 1) atomicOr(dev_err, DEV_ERR_BREAKDOWN);
+    }
+    if (pass >= 1 && pass + 1 < kCholPasses) qf[pass + 1] = ((qf[0] >> (pass - 1)) & 3u) ? 1u : 0u;
+  }
+  // ---- Rinv.  U[i][c] = R[i][c] * dinv[i] (i < c).  X = U^-1 (unit upper):
+  // at step k (from the bottom) row k of X is final; rows i < k receive
+  // -U[i][k] * row k.  Then Rinv[i][c] = X[i][c] * dinv[c].
+  float* U32 = X32 + p * ps;                              // FP32 copy of U (the X64 region's second half)
+  for (int e = tid; e < p * p; e += blockDim.x) {
+    const int i = e / p, c = e % p;
+    Rout[e] = c >= i ? R[i * ps + c] : 0.0;
+    if (inv_f32) {
+      X32[i * ps + c] = (i == c) ? 1.0f : 0.f;
+      U32[i * ps + c] = c > i ? (float)(R[i * ps + c] * dinv[i]) : 0.f;
+    } else {
+      X64[i * ps + c] = (i == c) ? 1.0 : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int k = p - 1; k >= 1; --k) {
+    // rows i < k, columns c in [k, p)
+    const int nc = p - k;
+    for (int e = tid; e < k * nc; e += blockDim.x) {
+      const int i = e / nc, c = k + e % nc;
+      if (inv_f32) {
+        X32[i * ps + c] = fmaf(-U32[i * ps + k], X32[k * ps + c], X32[i * ps + c]);
+      } else {
+        const double u = R[i * ps + k] * dinv[i];
+        X64[i * ps + c] -= u * X64[k * ps + c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < p * p; e += blockDim.x) {
+    const int i = e / p, c = e % p;
+    const double x = inv_f32 ? (double)X32[i * ps + c] : X64[i * ps + c];
+    Rinvout[e] = c >= i ? x * dinv[c] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_chol_global(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Rout,
+       double* __restrict__ Rinvout, int pass, double piv_rel, double shift_rel, uint32_t* qf,
+       uint32_t* dev_err, const uint32_t* __restrict__ gate) {
+  if (gate && *gate == 0u) return;
   const int tid = threadIdx.x;
   __shared__ int fail;
   __shared__ double dmax;
@@ -169,12 +422,15 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
       Rout[e] = v;
       Rinvout[e] = v;
     }
-    if (tid == 0 && pass == 2) qf[3] = 0u;
+    if (tid == 0 && pass + 1 < kCholPasses) qf[pass + 1] = 0u;
     return;
   }
   if (tid == 0) {
     dmax = 0.0;
-    if (pass == 0) qf[0] = 0u;
+    if (pass == 0) {
+      qf[0] = 0u;
+      qf[1] = 0u;
+    }
   }
   __syncthreads();
   for (int i = tid; i < p; i += blockDim.x) {
@@ -192,10 +448,22 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
     __shared__ unsigned long long emax_bits;
     if (tid == 0) emax_bits = 0ull;
     __syncthreads();
-    for (int e = tid; e < p * p; e += blockDim.x) {
-      const int i = e / p, j = e % p;
-      const double d = fabs(G[(int64_t)i * ldg + j] - (i == j ? 1.0 : 0.0));
-      atomicMax(&emax_bits, (unsigned long long)__double_as_longlong(isfinite(d) ? d : 1e300));
+    {
+      // max |G - I| (non-negative doubles order like their bit patterns):
+      // per thread, then per warp, then one shared atomic per warp
+      unsigned long long mb = 0ull;
+      for (int e = tid; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e % p;
+        const double d = fabs(G[(int64_t)i * ldg + j] - (i == j ? 1.0 : 0.0));
+        const unsigned long long b = (unsigned long long)__double_as_longlong(isfinite(d) ? d : 1e300);
+        mb = b > mb ? b : mb;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = t > mb ? t : mb;
+      }
+      if ((tid & 31) == 0) atomicMax(&emax_bits, mb);
     }
     __syncthreads();
     if (__longlong_as_double((long long)emax_bits) < 2e-3) {
@@ -215,8 +483,7 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
         Rout[e] = id + 0.5 * ee - 0.125 * (double)e2;
       }
       if (tid == 0) {
-        if (pass == 1) qf[2] = (qf[0] & 3u) ? 1u : 0u;
-        if (pass == 2) qf[3] = ((qf[0] >> 1) & 3u) ? 1u : 0u;
+        if (pass + 1 < kCholPasses) qf[pass + 1] = ((qf[0] >> (pass - 1)) & 3u) ? 1u : 0u;
       }
       return;
     }
@@ -230,16 +497,25 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
     }
     if (tid == 0) fail = 0;
     __syncthreads();
+    // the pivot's square root and reciprocal: computed once per step (FP64
+    // division and square root are long instruction sequences) and shared
+    __shared__ double piv_r[2];
+    const double piv_min = (attempt == 0) ? piv_rel * dmax : 0.5 * shift;
     for (int k = 0; k < p; ++k) {
       double d = R[k * p + k];
-      bool bad = !(d > piv_rel * dmax) || !isfinite(d);
+      bool bad = !(d > piv_min) || !isfinite(d);
       if (bad) {
         if (tid == 0) fail = 1;
         break;
       }
-      const double rkk = sqrt(d);
-      const double irkk = 1.0 / rkk;
+      if (tid == 0) {
+        const double rkk0 = sqrt(d);
+        piv_r[0] = rkk0;
+        piv_r[1] = 1.0 / rkk0;
+      }
       __syncthreads();
+      const double rkk = piv_r[0];
+      const double irkk = piv_r[1];
       for (int j = k + tid; j < p; j += blockDim.x) R[k * p + j] = (j == k) ? rkk : R[k * p + j] * irkk;
       __syncthreads();
       // trailing update of the upper triangle, 16 x 16 thread tile (no
@@ -270,11 +546,11 @@ k_chol(int p, const double* __restrict__ G, int64_t ldg, double* __restrict__ Ro
   if (tid == 0) {
     if (shifted) {
       qf[0] |= 1u << pass;
+      qf[1] = 1u;
       atomicOr(dev_err, DEV_ERR_SHIFTED);
-      if (pass == 3) atomicOr(dev_err, DEV_ERR_BREAKDOWN);
+      if (pass == kCholPasses - 1) atomicOr(dev_err, DEV_ERR_BREAKDOWN);
     }
-    if (pass == 1) qf[2] = (qf[0] & 3u) ? 1u : 0u;
-    if (pass == 2) qf[3] = ((qf[0] >> 1) & 3u) ? 1u : 0u;
+    if (pass >= 1 && pass + 1 < kCholPasses) qf[pass + 1] = ((qf[0] >> (pass - 1)) & 3u) ? 1u : 0u;
   }
   // Rinv = R^-1: rows from the bottom up, all columns in parallel
   for (int e = tid; e < p * p; e += blockDim.x) Rinv[e] = 0.0;
@@ -521,11 +797,13 @@ __global__ void k_jacobi_w(int w, const TJ* __restrict__ Jc, double* __restrict_
 __global__ void k_svd_finish(int w, const double* __restrict__ B64, const double* __restrict__ Win,
                              double* __restrict__ S, double* __restrict__ Ub, double* __restrict__ W) {
   extern __shared__ double sig[];
-  int* pos = reinterpret_cast<int*>(sig + w);
+  double* isig = sig + w;                      // 1 / sigma (one FP64 division per column)
+  int* pos = reinterpret_cast<int*>(isig + w);
   for (int c = threadIdx.x; c < w; c += blockDim.x) {
     double s = 0.0;
     for (int r = 0; r < w; ++r) { double v = B64[(int64_t)r * w + c]; s += v * v; }
     sig[c] = sqrt(s);
+    isig[c] = sig[c] > 0 ? 1.0 / sig[c] : 0.0;
   }
   __syncthreads();
   for (int c = threadIdx.x; c < w; c += blockDim.x) {
@@ -539,7 +817,7 @@ __global__ void k_svd_finish(int w, const double* __restrict__ B64, const double
     int r = e / w, c = e % w;
     int d = pos[c];
     double sc = sig[c];
-    Ub[(int64_t)r * w + d] = sc > 0 ? B64[e] / sc : (r == c ? 1.0 : 0.0);
+    Ub[(int64_t)r * w + d] = sc > 0 ? B64[e] * isig[c] : (r == c ? 1.0 : 0.0);
     W[(int64_t)r * w + d] = Win[e];
   }
   for (int c = threadIdx.x; c < w; c += blockDim.x) S[pos[c]] = sig[c];
@@ -547,19 +825,42 @@ __global__ void k_svd_finish(int w, const double* __restrict__ B64, const double
 
 
 
-// Y = beta Y + alpha X M, FP64 storage, FP32 arithmetic; one thread per
-// output element.
-__global__ void k_small_gemm_f32(int m, int p, int q, const double* __restrict__ X, int64_t ldx,
-                                 const double* __restrict__ M, int64_t ldm, double alpha, double beta,
-                                 double* __restrict__ Y, int64_t ldy) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m * q) return;
-  int i = e / q, j = e % q;
-  float acc = 0.f;
-  for (int k = 0; k < p; ++k) acc = fmaf((float)X[(int64_t)i * ldx + k], (float)M[(int64_t)k * ldm + j], acc);
-  double y = alpha * (double)acc;
-  if (beta != 0.0) y += beta * Y[(int64_t)i * ldy + j];
-  Y[(int64_t)i * ldy + j] = y;
+// Y = beta Y + alpha X M, FP64 storage, FP32 arithmetic.  32 x 32 output
+// tiles, 256 threads (4 outputs each); X and M are converted to FP32 once per
+// tile in shared memory (FP64 -> FP32 conversions are not free here).
+__global__ void __launch_bounds__(256) k_small_gemm_f32(int m, int p, int q, const double* __restrict__ X,
+                                                        int64_t ldx, const double* __restrict__ M, int64_t ldm,
+                                                        double alpha, double beta, double* __restrict__ Y,
+                                                        int64_t ldy) {
+  __shared__ float xs[32][33];
+  __shared__ float ms[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // ty 0..7
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < p; k0 += 32) {
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int r = e >> 5, c = e & 31;
+      xs[r][c] = (i0 + r < m && k0 + c < p) ? (float)X[(int64_t)(i0 + r) * ldx + k0 + c] : 0.f;
+      ms[r][c] = (k0 + r < p && j0 + c < q) ? (float)M[(int64_t)(k0 + r) * ldm + j0 + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float b = ms[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fmaf(xs[ty + 8 * u][kk], b, acc[u]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + ty + 8 * u, j = j0 + tx;
+    if (i < m && j < q) {
+      double y = alpha * (double)acc[u];
+      if (beta != 0.0) y += beta * Y[(int64_t)i * ldy + j];
+      Y[(int64_t)i * ldy + j] = y;
+    }
+  }
 }
 
 // ----------------------------------------------------------------- small ops
@@ -729,17 +1030,24 @@ void gemm_xm(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, cons
 }
 
 void chol_small(int p, const double* G, int64_t ldg, double* R, double* Rinv, int pass,
-                double piv_rel, double shift_rel, uint32_t* qf, uint32_t* dev_err, cudaStream_t st) {
-  const size_t sm = p <= 64 ? (size_t)2 * p * p * sizeof(double) : 0;
-  static bool attr = false;
-  if (!attr) {
-    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
-    attr = true;
+                double piv_rel, double shift_rel, uint32_t* qf, uint32_t* dev_err, cudaStream_t st, bool inv_f32,
+                const uint32_t* gate) {
+  if (p <= 64) {
+    const int ps = p | 1;
+    const size_t sm = (size_t)2 * p * ps * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+      RPCA_CUDA_TRY(cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 65 * 8));
+      attr = true;
+    }
+    k_chol<<<1, 256, sm, st>>>(p, G, ldg, R, Rinv, pass, piv_rel, shift_rel, qf, dev_err, inv_f32 ? 1 : 0, gate);
+  } else {
+    k_chol_global<<<1, 256, 0, st>>>(p, G, ldg, R, Rinv, pass, piv_rel, shift_rel, qf, dev_err, gate);
   }
-  k_chol<<<1, 256, sm, st>>>(p, G, ldg, R, Rinv, pass, piv_rel, shift_rel, qf, dev_err);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
 }
+
 
 void left_mul(int p, const double* Rk, double* Racc, cudaStream_t st) {
   k_left_mul<<<1, 256, (size_t)p * p * sizeof(double), st>>>(p, Rk, Racc);
@@ -801,7 +1109,7 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
   // right singular vectors (second-order accurate).
   if (f64) gemm_xm(true, w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st, nullptr);
   else small_gemm_f32(w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st);
-  size_t smem = (size_t)w * (sizeof(double) + sizeof(int));
+  size_t smem = (size_t)w * (2 * sizeof(double) + sizeof(int));
   k_svd_finish<<<1, 256, smem, st>>>(w, B64, W0, S, Ub, W);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
@@ -817,7 +1125,8 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
 void small_gemm_f32(int m, int p, int q, const double* X, int64_t ldx, const double* M, int64_t ldm,
                     double alpha, double beta, double* Y, int64_t ldy, cudaStream_t st) {
   if (m <= 0 || q <= 0) return;
-  k_small_gemm_f32<<<grid1((int64_t)m * q), 256, 0, st>>>(m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy);
+  dim3 grid((unsigned)cdiv(q, 32), (unsigned)cdiv(m, 32));
+  k_small_gemm_f32<<<grid, 256, 0, st>>>(m, p, q, X, ldx, M, ldm, alpha, beta, Y, ldy);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
 }

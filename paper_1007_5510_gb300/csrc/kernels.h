@@ -64,8 +64,16 @@ void gemm_xm(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, cons
 // the same span, orthonormal to O(E^3).
 // qf: 4 device words private to the block; the word qf + pass gates the
 // Gram/gemm of passes 2-3 (qf[2], qf[3]).
+// Cholesky-QR passes per block (passes >= 2 run only after a shifted pass)
+// and device words of flags per block (qf).
+constexpr int kCholPasses = 6;
+constexpr int kQfWords = 8;
+// inv_f32: Rinv may be formed in FP32 (it then only feeds FP32 products).
+// gate (device word, may be null): the kernel does nothing when it is 0.
 void chol_small(int p, const double* G, int64_t ldg, double* R, double* Rinv, int pass,
-                double piv_rel, double shift_rel, uint32_t* qf, uint32_t* dev_err, cudaStream_t st);
+                double piv_rel, double shift_rel, uint32_t* qf, uint32_t* dev_err, cudaStream_t st,
+                bool inv_f32 = false, const uint32_t* gate = nullptr);
+
 // Racc = Rk * Racc (p x p FP64)
 void left_mul(int p, const double* Rk, double* Racc, cudaStream_t st);
 // M -= I (p x p FP64, ld p)

@@ -108,7 +108,7 @@ struct QrScratch {
   double* Rk = nullptr;    // l x l
   double* Rinv = nullptr;  // l x l
   double* Racc = nullptr;  // l x l
-  uint32_t* qf = nullptr;  // 4 words per block
+  uint32_t* qf = nullptr;  // kQfWords words per block
   float* mt = nullptr;     // 2 * 256 * 256 floats (tensor-core products)
   void* slices = nullptr;  // BF16 slice scratch for tensor-core Grams
   size_t slice_bytes = 0;
@@ -150,6 +150,23 @@ static void qr_apply(bool f64, int64_t m, int p, int q, const void* X, const flo
   if (Ylo) split_lo(m, q, (const float*)Y, ldy, Ylo, ldy, st);
 }
 
+// A block whose Cholesky needed a shift is numerically rank deficient: the
+// passes have multiplied the projection's rounding residue against the
+// earlier blocks by the block's condition number.  When qf[1] says so (set
+// by the Cholesky kernel; every launch here is a no-op otherwise), project once more against the
+// earlier blocks and re-orthonormalise with one more pass.  (The triangular
+// factor is not tracked here: callers that want it skip this step.)
+static void reorth_after_shift(bool f64, int64_t m, int jl, int l, void* H, float* Hlo, int64_t ld, void* Hj,
+                               float* Hjlo, uint32_t* qf, double piv_rel, double shift_rel, const QrScratch& s,
+                               uint32_t* dev_err, cudaStream_t st) {
+  const uint32_t* g = qf + 1;
+  qr_gram(f64, m, jl, l, H, ld, Hj, ld, s.C, l, s, st, dev_err, g, true);
+  qr_apply(f64, m, jl, l, H, Hlo, ld, s.C, l, -1.0, 1.0, Hj, Hjlo, ld, s, st, dev_err, g);
+  qr_gram(f64, m, l, l, Hj, ld, Hj, ld, s.Gm, l, s, st, dev_err, g);
+  chol_small(l, s.Gm, l, s.Rk, s.Rinv, 1, piv_rel, shift_rel, qf, dev_err, st, !f64, g);
+  qr_apply(f64, m, l, l, Hj, Hjlo, ld, s.Rinv, l, 1.0, 0.0, Hj, Hjlo, ld, s, st, dev_err, g);
+}
+
 // E_out (w x w FP64, optional): Q^T Q - I of the stored Q, measured with an
 // FP64-accumulated Gram, so that consumers can apply the first-order
 // orthonormalisation Q (I - E/2) in FP64 without rewriting Q.
@@ -175,15 +192,17 @@ static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, 
         if (R_out) mat_add(jl, l, s.C, l, R_out + jl, w, st);
       }
     }
-    uint32_t* qf = s.qf + 4 * j;
+    uint32_t* qf = s.qf + kQfWords * j;
     if (R_out) set_identity(l, s.Racc, st);
-    for (int pass = 0; pass < 4; ++pass) {
+    for (int pass = 0; pass < kCholPasses; ++pass) {
       const uint32_t* active = pass >= 2 ? qf + pass : nullptr;
       qr_gram(f64, m, l, l, Hj, ld, Hj, ld, s.Gm, l, s, st, dev_err, active);
-      chol_small(l, s.Gm, l, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st);
+      chol_small(l, s.Gm, l, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st, !f64);
       qr_apply(f64, m, l, l, Hj, Hjlo, ld, s.Rinv, l, 1.0, 0.0, Hj, Hjlo, ld, s, st, dev_err, active);
       if (R_out) left_mul(l, s.Rk, s.Racc, st);
     }
+    if (j > 0 && !R_out) reorth_after_shift(f64, m, jl, l, H, Hlo, ld, Hj, Hjlo, qf, piv_rel, shift_rel, s, dev_err,
+                                            st);
     if (R_out) mat_add(l, l, s.Racc, l, R_out + (size_t)jl * w + jl, w, st);
   }
   if (E_out) {
@@ -214,13 +233,25 @@ static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, vo
                           s.mt, st, dev_err, nullptr));
       }
     }
-    uint32_t* qf = s.qf + 4 * j;
-    for (int pass = 0; pass < 4; ++pass) {
+    uint32_t* qf = s.qf + kQfWords * j;
+    for (int pass = 0; pass < kCholPasses; ++pass) {
       const uint32_t* active = pass >= 2 ? qf + pass : nullptr;
       need(gram_slices(m, prow, S, lds, 64 * j, 64, 64 * j, 64, s.G64, 64, st, dev_err, active));
-      chol_small(l, s.G64, 64, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st);
+      chol_small(l, s.G64, 64, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st, true);
       need(apply_slices(m, prow, S, lds, 64 * j, 1, 64 * j, s.Rinv, l, l, l, 1.0, l, false, true, nullptr, 0, 0,
                         s.mt, st, dev_err, active));
+    }
+    if (j > 0) {
+      // numerically rank-deficient block: one more projection and pass
+      // (launches are no-ops unless a pass above needed a shift)
+      const uint32_t* g = qf + 1;
+      need(gram_slices(m, prow, S, lds, 0, 64 * j, 64 * j, 64, s.C64, 64, st, dev_err, g));
+      need(apply_slices(m, prow, S, lds, 0, j, 64 * j, s.C64, 64 * j, 64, 64, -1.0, 0, true, true, nullptr, 0, 0,
+                        s.mt, st, dev_err, g));
+      need(gram_slices(m, prow, S, lds, 64 * j, 64, 64 * j, 64, s.G64, 64, st, dev_err, g));
+      chol_small(l, s.G64, 64, s.Rk, s.Rinv, 1, piv_rel, shift_rel, qf, dev_err, st, true, g);
+      need(apply_slices(m, prow, S, lds, 64 * j, 1, 64 * j, s.Rinv, l, l, l, 1.0, l, false, true, nullptr, 0, 0,
+                        s.mt, st, dev_err, g));
     }
   }
   if (E_out) {
@@ -652,7 +683,8 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->outV.alloc((size_t)c->n * c->k * es);
   const size_t w = c->w, l = c->l;
   const size_t small_doubles = w * l + 4 * l * l + w * w * 4 + w + 4 * w * w + 3 * w * w + 2 * w * c->k;
-  c->small.alloc(small_doubles * sizeof(double) + 4 * 16 * sizeof(uint32_t));
+  const size_t qf_words = (size_t)kQfWords * (c->i + 1);   // the most blocks any QR here has
+  c->small.alloc(small_doubles * sizeof(double) + qf_words * sizeof(uint32_t));
   double* s = c->small.as<double>();
   c->qs.C = s; s += w * l;
   c->qs.Gm = s; s += l * l;
@@ -671,7 +703,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->MU = s; s += w * c->k;
   c->MV = s; s += w * c->k;
   c->qs.qf = reinterpret_cast<uint32_t*>(s);
-  RPCA_CUDA_TRY(cudaMemsetAsync(c->qs.qf, 0, 4 * 16 * sizeof(uint32_t), c->stream));
+  RPCA_CUDA_TRY(cudaMemsetAsync(c->qs.qf, 0, qf_words * sizeof(uint32_t), c->stream));
   if (c->transposed) c->At.alloc((size_t)c->m * c->n * dtype_bytes(p->dtype));
   if (!c->simt) c->work.alloc((size_t)c->m * round_up(c->w, 64) * 2 + 4096);
   if (!c->f64) {
@@ -1256,7 +1288,8 @@ rpca_status rpca_op_qr(int32_t f64, int64_t m, int32_t nblk, int32_t l, void* H,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     DevBuf scratch;
     const size_t w = (size_t)nblk * l;
-    scratch.alloc((w * l + 4 * (size_t)l * l) * sizeof(double) + 4 * nblk * sizeof(uint32_t) + 64 * sizeof(uint32_t));
+    scratch.alloc((w * l + 4 * (size_t)l * l) * sizeof(double) + (size_t)kQfWords * nblk * sizeof(uint32_t) +
+                  64 * sizeof(uint32_t));
     QrScratch qs;
     double* s = scratch.as<double>();
     qs.C = s; s += w * l;
@@ -1265,8 +1298,8 @@ rpca_status rpca_op_qr(int32_t f64, int64_t m, int32_t nblk, int32_t l, void* H,
     qs.Rinv = s; s += (size_t)l * l;
     qs.Racc = s; s += (size_t)l * l;
     qs.qf = reinterpret_cast<uint32_t*>(s);
-    uint32_t* err = qs.qf + 4 * nblk;
-    RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
+    uint32_t* err = qs.qf + kQfWords * nblk;
+    RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, ((size_t)kQfWords * nblk + 64) * sizeof(uint32_t), st));
     if (sliced_ok(f64 != 0, m, nblk, l, 0)) {
       // H held in three BF16 slices through the whole QR (tensor cores)
       const int64_t prow = round_up(m, 128);
@@ -1371,7 +1404,8 @@ rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w, const void* T, 
     Tq.alloc((size_t)n * w * es);
     RPCA_CUDA_TRY(cudaMemcpy2DAsync(Tq.ptr, w * es, T, ldt * es, w * es, n, cudaMemcpyDeviceToDevice, st));
     const size_t ww = (size_t)w * w;
-    scratch.alloc((w * l + 4 * (size_t)l * l + ww * 10) * sizeof(double) + (4 * nblk + 64) * sizeof(uint32_t));
+    scratch.alloc((w * l + 4 * (size_t)l * l + ww * 10) * sizeof(double) +
+                  ((size_t)kQfWords * nblk + 64) * sizeof(uint32_t));
     QrScratch qs;
     double* s = scratch.as<double>();
     qs.C = s; s += (size_t)w * l;
@@ -1386,8 +1420,8 @@ rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w, const void* T, 
     double* MV = s; s += ww;
     double* work = s; s += 4 * ww;
     qs.qf = reinterpret_cast<uint32_t*>(s);
-    uint32_t* err = qs.qf + 4 * nblk;
-    RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, (4 * nblk + 64) * sizeof(uint32_t), st));
+    uint32_t* err = qs.qf + kQfWords * nblk;
+    RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, ((size_t)kQfWords * nblk + 64) * sizeof(uint32_t), st));
     DevBuf Tc, tlo, mt, sl;
     Tc.alloc((size_t)n * w * es);
     if (!f64 && n >= kTcMinRows) {

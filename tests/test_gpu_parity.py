@@ -119,6 +119,27 @@ def test_block_qr(f64, m):
     assert est.max_principal_angle(Q, Qo) < (1e-10 if f64 else 1e-4)
 
 
+@pytest.mark.parametrize("f64,l,nblk", [(False, 20, 2), (True, 20, 2), (False, 60, 1), (True, 7, 3)])
+def test_block_qr_shifted_cholesky(f64, l, nblk):
+    """A block with two nearly equal columns makes the first Cholesky pivot
+    fail; the shifted Cholesky QR (Section 3's Step 2 with a diagonal shift,
+    then up to two more passes) must still return an orthonormal Q whose span
+    contains H's columns."""
+    rng = np.random.default_rng(l + nblk)
+    m, w = 6000, nblk * l
+    H = rng.standard_normal((m, w))
+    j = w - 3
+    H[:, j] = H[:, j - 1] + (1e-13 if f64 else 1e-7) * rng.standard_normal(m)
+    Ht = _tt(H, torch.float64 if f64 else torch.float32)
+    R().qr_inplace(Ht, nblk, l)
+    torch.cuda.synchronize()
+    Q = Ht.cpu().double().numpy()
+    Hc = H if f64 else H.astype(np.float32).astype(np.float64)
+    assert np.abs(Q.T @ Q - np.eye(w)).max() < (1e-12 if f64 else 1e-5)
+    res = np.linalg.norm(Hc - Q @ (Q.T @ Hc)) / np.linalg.norm(Hc)
+    assert res < (1e-12 if f64 else 1e-5)
+
+
 @pytest.mark.parametrize("m,l,nblk,decay", [(100_000, 60, 3, 0.97), (30_001, 48, 2, 0.9), (20_000, 64, 3, 0.95)])
 def test_block_qr_sliced_tensor_cores(m, l, nblk, decay):
     """Step 2 with H held in three BF16 slices on tensor cores (blocks of
@@ -186,6 +207,32 @@ def test_pca_fp32_matches_oracle(m, n, k, l, i):
     U, S, V = R().pca(_tt(A32), k, l, i, seed=99)
     Uo, So, Vo = ro.rpca(A32.astype(np.float64), k, l, i, seed=99, normalize=True)
     _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+
+
+@pytest.mark.parametrize("dtype,m,n,k,l,i,r", [("f32", 3000, 400, 5, 10, 2, 8), ("f64", 2000, 300, 4, 9, 2, 7),
+                                               ("bf16", 20_000, 512, 8, 48, 1, 16)])
+def test_pca_exactly_low_rank(dtype, m, n, k, l, i, r):
+    """rank(A) = r < (i+1) l: the later Krylov blocks are rounding noise, so H
+    is numerically rank deficient and their Cholesky passes need the shift.
+    The top k singular values still match the oracle (pivoted QR) on the same
+    matrix, and U, V stay orthonormal."""
+    sig = np.linspace(1.0, 0.3, r)
+    A = gen.lowrank_np(m, n, sig, seed=r)
+    if dtype == "f64":
+        At = _tt(A, torch.float64)
+    else:
+        At = torch.from_numpy(A.astype(np.float32)).cuda()
+        if dtype == "bf16":
+            At = At.to(torch.bfloat16)
+    U, S, V = R().pca(At, k, l, i, seed=5)
+    Aref = At.double().cpu().numpy()
+    Uo, So, Vo = ro.rpca(Aref, k, l, i, seed=5, normalize=True)
+    tol = {"f64": 1e-10, "f32": 1e-4, "bf16": 1e-3}[dtype]
+    assert np.max(np.abs(S.cpu().numpy() - So) / So) < tol
+    Ud, Vd = U.cpu().double().numpy(), V.cpu().double().numpy()
+    otol = 1e-12 if dtype == "f64" else 1e-4
+    assert np.abs(Ud.T @ Ud - np.eye(k)).max() < otol
+    assert np.abs(Vd.T @ Vd - np.eye(k)).max() < otol
 
 
 def oracle_spread(A64, k, l, i, seed, center):
