@@ -45,7 +45,7 @@ REF_SAMPLE_ROWS = 40_000      # --impl reference: rows per timed step
 # DRAM bytes (read + write) per row of A of one launch of the BF16 tensor-core
 # fused pass at n = 4,096, L = 64 (ncu capture at m = 100,000; traffic grows
 # in proportion to the rows), see profiles/fused_pass_bf16_m100000_n4096_l60.md
-FUSED_BF16_N4096_TRAFFIC_PER_ROW = 850.457e6 / 100_000
+FUSED_BF16_N4096_TRAFFIC_PER_ROW = 854.153e6 / 100_000
 
 
 def parse():
