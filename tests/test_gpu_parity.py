@@ -332,7 +332,9 @@ def test_t_pass_tensor_cores_bf16(m, n, w):
 
 # ------------------------------------------- tensor-core fused pass (BF16)
 @pytest.mark.parametrize("m,n,l", [(1000, 512, 12), (5000, 4096, 60), (777, 1000, 22),
-                                   (3001, 2000, 30), (300, 64, 20)])
+                                   (3001, 2000, 30), (300, 64, 20),
+                                   (8000, 4104, 40),       # 16-CTA clusters, 7 empty column slabs
+                                   (40_001, 2600, 63)])    # 6 slabs rounded up to 8, ~20 panels per cluster
 @pytest.mark.parametrize("with_f", [True, False])
 def test_fused_pass_tensor_cores_bf16(m, n, l, with_f):
     """Cluster-split tcgen05 pass: H = A bf16(X) and F = A^T bf16(H) (the
