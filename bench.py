@@ -270,7 +270,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(ctx16, A16, m, n, k, i, bytes_bf16, min(args.steps, 3), dev, world, dist)
+        e2e = end_to_end(A16, m, n, k, l, i, bytes_bf16, min(args.steps, 3), dev, world, dist, W["seed"])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -350,35 +350,37 @@ def spectral_errors(A, outs, labels, iters=30, nvec=4):
     return res
 
 
-def end_to_end(ctx, A_dev, m, n, k, i, b, steps, dev, world, dist):
-    """Same metric through the public API with host buffers: pinned host A
-    copied in, PCA, U S V copied out, every step."""
+def end_to_end(A_dev, m, n, k, l, i, b, steps, dev, world, dist, seed):
+    """Same metric through the public API with host buffers: one call per
+    step on A in pinned host memory (RPCA_HOST_A | RPCA_HOST_RESIDENT: the
+    library copies A in once, the first pass working on each tile as it
+    lands), then U S V copied out."""
     import torch
+    from paper_1007_5510_gb300 import rpca
     Ah = A_dev.cpu().pin_memory()
-    Ad = torch.empty_like(A_dev)
     Uh = torch.empty(m, k).pin_memory()
     Vh = torch.empty(n, k).pin_memory()
     Sh = torch.empty(k, dtype=torch.float64).pin_memory()
     U = torch.empty(m, k, device=dev)
     V = torch.empty(n, k, device=dev)
     S = torch.empty(k, dtype=torch.float64, device=dev)
+    ctx = rpca.PCA(m, n, k, l, i, rpca.BF16, seed=seed, host_a=True, host_resident=True)
     st = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    Ad.copy_(Ah, non_blocking=True)
-    ctx.run(Ad, U=U, S=S, V=V)
+    ctx.run(Ah, U=U, S=S, V=V)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ev0.record(st)
     for _ in range(steps):
-        Ad.copy_(Ah, non_blocking=True)
-        ctx.run(Ad, U=U, S=S, V=V)
+        ctx.run(Ah, U=U, S=S, V=V)
         Uh.copy_(U, non_blocking=True)
         Vh.copy_(V, non_blocking=True)
         Sh.copy_(S, non_blocking=True)
     ev1.record(st)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    ctx.close()
     ms = max_over_ranks(ms, world, dist, dev)
     t = ms / steps / 1e3
     return {"value": round(world * (i + 2) * m * n * b / t / 1e9, 2), "unit": "GB/s",

@@ -76,6 +76,15 @@ typedef enum {
 #define RPCA_TIMING     0x8u  /* record per-phase CUDA-event times */
 #define RPCA_ADJOINT    0x10u /* keep what rpca_backward needs (m >= n, no
                                  centring, device A) */
+#define RPCA_HOST_RESIDENT 0x20u /* with RPCA_HOST_A: the first pass of each
+                                 run copies A's tiles once into a device copy
+                                 the context owns (m x n, allocated at init;
+                                 each tile's pass-0 kernel runs as soon as its
+                                 copy lands), and the later passes read that
+                                 copy.  For A in host memory that fits in
+                                 device memory: one host-to-device transfer
+                                 per run instead of one per pass.  Not part of
+                                 the paper (no device memory there). */
 
 typedef struct {
   int64_t m, n;           /* A is m x n; 1 <= k < min(m, n) */

@@ -297,6 +297,10 @@ using namespace rpca;
 struct rpca_ctx {
   rpca_problem prob{};
   bool f64 = false, transposed = false, host_a = false, simt = false;
+  // RPCA_HOST_RESIDENT: device copy of host A, valid once this run's first
+  // pass has copied every tile
+  bool resident = false, resident_valid = false;
+  DevBuf Ares;
   int64_t m = 0, n = 0;   // working orientation (m >= n)
   int k = 0, l = 0, i = 0, w = 0;
   int64_t ldx = 0;        // ld of X and F (compute type)
@@ -381,7 +385,9 @@ void validate(const rpca_problem* p) {
   if (p->l > 255) throw Invalid("l > 255 is not supported");
   if ((int64_t)(p->i + 1) * p->l > 256) throw Invalid("(i+1) l > 256 is not supported");
   if (p->dtype < RPCA_F64 || p->dtype > RPCA_FP8E4M3) throw Invalid("unknown dtype");
-  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT | RPCA_TIMING | RPCA_ADJOINT)) throw Invalid("unknown flag");
+  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT | RPCA_TIMING | RPCA_ADJOINT | RPCA_HOST_RESIDENT))
+    throw Invalid("unknown flag");
+  if ((p->flags & RPCA_HOST_RESIDENT) && !(p->flags & RPCA_HOST_A)) throw Invalid("RPCA_HOST_RESIDENT needs RPCA_HOST_A");
   if ((p->flags & RPCA_ADJOINT) && ((p->flags & (RPCA_CENTER | RPCA_HOST_A)) || p->n > p->m))
     throw Invalid("RPCA_ADJOINT needs m >= n, no centring and device A");
   if ((p->flags & RPCA_HOST_A) && p->n > p->m) throw Invalid("RPCA_HOST_A needs n <= m");
@@ -392,7 +398,7 @@ void validate(const rpca_problem* p) {
 // centring shift or column scale)?
 bool tpass_bf16_ok(const rpca_ctx* c, const rpca_matrix* Am) {
   if (c->prob.dtype != RPCA_BF16 || c->centered || c->simt || Am->col_scale) return false;
-  if (c->host_a) return (c->n * 2) % 16 == 0;
+  if (c->host_a) return (c->n * 2) % 16 == 0 && (!c->resident || c->w <= 192);
   const void* A = c->transposed ? c->At.ptr : Am->data;
   const int64_t lda = c->transposed ? c->n : Am->ld;
   return (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda * 2) % 16 == 0 && c->w <= 192;
@@ -402,9 +408,10 @@ void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
   const size_t ab = dtype_bytes(c->prob.dtype);
   a.work = c->work.ptr;
   a.work_bytes = c->work.bytes;
-  if (!c->host_a) {
-    a.A = c->transposed ? c->At.ptr : Am->data;
-    a.lda = c->transposed ? c->n : Am->ld;
+  if (!c->host_a || (c->resident && c->resident_valid)) {
+    const bool res = c->host_a;                     // the context's device copy of A
+    a.A = res ? c->Ares.ptr : (c->transposed ? c->At.ptr : Am->data);
+    a.lda = res ? c->n : (c->transposed ? c->n : Am->ld);
     a.m = c->m;
     if (!(c->simt) && launch_pass_tc(a, c->stream, c->dev_err())) return;
     if (a.q16) throw Invalid("T pass: tensor-core kernel refused its BF16 operand");
@@ -420,18 +427,22 @@ void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
   const size_t fes = a.f_f64 ? 8 : es;
   if (a.F && a.mode != MODE_H)
     RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * fes, 0, fcols * fes, a.n, c->stream));
+  // resident copy: tile t lands in its final place (no buffer reuse, so no
+  // wait for the kernel of tile t - 2)
+  const bool to_res = c->resident;
   for (int64_t t = 0; t < ntiles; ++t) {
     const int b = (int)(t & 1);
     const int64_t r0 = t * tr, rows = std::min(tr, c->m - r0);
-    RPCA_CUDA_TRY(cudaStreamWaitEvent(c->copy_stream, c->ev_used[b], 0));
+    char* dst = to_res ? static_cast<char*>(c->Ares.ptr) + (size_t)r0 * c->n * ab : static_cast<char*>(c->tiles[b].ptr);
+    if (!to_res) RPCA_CUDA_TRY(cudaStreamWaitEvent(c->copy_stream, c->ev_used[b], 0));
     const char* src = static_cast<const char*>(Am->data) + (size_t)r0 * Am->ld * ab;
-    RPCA_CUDA_TRY(cudaMemcpy2DAsync(c->tiles[b].ptr, (size_t)c->n * ab, src, (size_t)Am->ld * ab,
+    RPCA_CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)c->n * ab, src, (size_t)Am->ld * ab,
                                     (size_t)c->n * ab, (size_t)rows, cudaMemcpyHostToDevice,
                                     c->copy_stream));
     RPCA_CUDA_TRY(cudaEventRecord(c->ev_copied[b], c->copy_stream));
     RPCA_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_copied[b], 0));
     PassArgs ta = a;
-    ta.A = c->tiles[b].ptr;
+    ta.A = dst;
     ta.lda = c->n;
     ta.m = rows;
     ta.H = static_cast<char*>(a.H) + (size_t)r0 * a.ldh * es;
@@ -444,6 +455,7 @@ void run_pass(rpca_ctx* c, const rpca_matrix* Am, PassArgs a) {
     }
     RPCA_CUDA_TRY(cudaEventRecord(c->ev_used[b], c->stream));
   }
+  if (to_res) c->resident_valid = true;
 }
 
 void compute_shift(rpca_ctx* c, const rpca_matrix* Am) {
@@ -482,6 +494,7 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   if (j == 0) {
     RPCA_CUDA_TRY(cudaMemsetAsync(c->err.ptr, 0, 64 * sizeof(uint32_t), st));
     c->fwd_done = false;
+    c->resident_valid = false;         // this run's A is copied by its first pass
     if (c->transposed)
       transpose(c->prob.dtype, c->m, c->n, Am->data, Am->ld, c->At.ptr, c->n, st);
     if (c->centered) compute_shift(c, Am);
@@ -733,6 +746,8 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   }
   if (c->host_a) {
     const size_t ab = dtype_bytes(p->dtype);
+    c->resident = (p->flags & RPCA_HOST_RESIDENT) != 0;
+    if (c->resident) c->Ares.alloc((size_t)c->m * c->n * ab);
     int64_t tr = p->tile_rows > 0 ? p->tile_rows : std::max<int64_t>(128, (int64_t)((1ull << 30) / (c->n * ab)));
     tr = std::min<int64_t>(tr, c->m);
     c->tile_rows = tr;

@@ -17,7 +17,7 @@ OK, MORE = 0, 1
 STATUS = {0: "RPCA_OK", 1: "RPCA_MORE", -1: "RPCA_EINVAL", -2: "RPCA_ENOMEM", -3: "RPCA_ECUDA",
           -4: "RPCA_ENODEV", -5: "RPCA_EBREAKDOWN", -6: "RPCA_ETIMEOUT", -7: "RPCA_ESTATE"}
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
-CENTER, HOST_A, SIMT, TIMING, ADJOINT = 0x1, 0x2, 0x4, 0x8, 0x10
+CENTER, HOST_A, SIMT, TIMING, ADJOINT, HOST_RESIDENT = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 
 EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
            "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
@@ -166,11 +166,14 @@ class PCA:
     """A context: rpca_init on construction, passes, finish, rerun."""
 
     def __init__(self, m, n, k, l, i, dtype=F32, seed=0, center=False, G=None, host_a=False,
-                 tile_rows=0, simt=False, stream=None, timing=False, adjoint=False):
+                 tile_rows=0, simt=False, stream=None, timing=False, adjoint=False, host_resident=False):
+        """host_a: A is in host memory and every pass streams it in tiles;
+        host_resident (with host_a): the first pass of each run copies it
+        once into a device copy that the later passes read."""
         lib = load_library()
         self.m, self.n, self.k, self.l, self.i, self.dtype = m, n, k, l, i, dtype
         flags = ((CENTER if center else 0) | (HOST_A if host_a else 0) | (SIMT if simt else 0)
-                 | (ADJOINT if adjoint else 0)
+                 | (ADJOINT if adjoint else 0) | (HOST_RESIDENT if host_resident else 0)
                  | (TIMING if timing else 0))
         self._G = None
         Gp = None

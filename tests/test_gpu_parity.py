@@ -302,6 +302,32 @@ def test_host_streamed_tiles_match_device():
     _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
 
 
+@pytest.mark.parametrize("dtype,m,n", [("f32", 5000, 256), ("bf16", 20_003, 1024)])
+def test_host_resident_matches_device(dtype, m, n):
+    """A in pinned host memory copied once per run (ragged tiles, the first
+    pass on each tile as it lands), the later passes on the device copy; a
+    second run with another matrix must see the new values."""
+    rng = np.random.default_rng(12)
+    A = (gen.lowrank_np(m, n, 0.8 ** np.arange(n), seed=2) + 1e-4 * rng.standard_normal((m, n))).astype(np.float32)
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    code = R().BF16 if dtype == "bf16" else R().F32
+    Ad = torch.from_numpy(A).cuda().to(tdt)
+    Ah = Ad.cpu().pin_memory()
+    Bh = (Ad * 4).cpu().pin_memory()                   # exact in BF16 too
+    k, l, i = 10, 12, 2
+    ctx = R().PCA(m, n, k, l, i, code, seed=3, host_a=True, host_resident=True, tile_rows=1700)
+    try:
+        _, S, _ = ctx.run(Ah)
+        S = S.clone()
+        _, S3, _ = ctx.run(Bh)
+        S3 = S3.clone()
+    finally:
+        ctx.close()
+    _, S2, _ = R().pca(Ad, k, l, i, seed=3)
+    assert torch.allclose(S, S2, rtol=1e-5 if dtype == "f32" else 1e-4)
+    assert torch.allclose(S3, 4 * S2, rtol=1e-5 if dtype == "f32" else 1e-4)
+
+
 def test_rerun_reuses_context():
     rng = np.random.default_rng(9)
     A = rng.standard_normal((1200, 200)).astype(np.float32)
