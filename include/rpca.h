@@ -276,8 +276,8 @@ const char* rpca_batch_last_error(const rpca_batch* b);
 
 /* Limits of the fixed scratch: X^T in BF16 for up to RPCA_NOALLOC_MAX_P
  * columns and RPCA_NOALLOC_MAX_N rows, then 64 error words (512 KiB + 256 B
- * per device in total); 4096 is also the widest A the tensor-core fused
- * pass takes. */
+ * per device in total).  (The allocating entry's tensor-core pass takes n
+ * up to 8192.) */
 #define RPCA_NOALLOC_MAX_N 4096
 #define RPCA_NOALLOC_MAX_P 64
 #define RPCA_NOALLOC_SCRATCH_BYTES (64 * 4096 * 2 + 256)

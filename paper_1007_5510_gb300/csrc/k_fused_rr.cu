@@ -641,7 +641,7 @@ bool dispatch_rr(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
 
 }  // namespace
 
-bool fused_pass_rr(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
+bool fused_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   if (a.dtype != RPCA_BF16) return false;
   if (a.mode != MODE_FUSED && a.mode != MODE_H) return false;
   if (a.shift || a.scale || !a.work) return false;

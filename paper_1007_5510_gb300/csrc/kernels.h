@@ -38,10 +38,8 @@ struct PassArgs {
 void launch_pass_simt(const PassArgs& a, cudaStream_t st);
 // Tensor-core pass; returns false when the shape/dtype is not supported.
 bool launch_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
-// Fused Step-1 pass on tensor cores (k_fused_tc.cu); false if unsupported.
+// Fused Step-1 pass on tensor cores (k_fused_rr.cu); false if unsupported.
 bool fused_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
-// Its L2 re-read form (k_fused_rr.cu), tried first; false if unsupported.
-bool fused_pass_rr(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
 
 // ---------------------------------------------------------------- linalg
 // C (p x q, FP64, ldc) (+)= X^T Y over rows [0, m); X m x p (ldx), Y m x q.
