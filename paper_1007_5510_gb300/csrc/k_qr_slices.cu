@@ -116,7 +116,8 @@ __global__ void k_compact_sq(int nblk, int l, const double* __restrict__ C, int6
   if (e >= w * w) return;
   const int i = e / w, j = e % w;
   const int pi = (i / l) * 64 + i % l, pj = (j / l) * 64 + j % l;
-  E[e] = C[(int64_t)pi * ldc + pj];
+  // symmetric: the lower block triangle from the upper one
+  E[e] = (i / l <= j / l) ? C[(int64_t)pi * ldc + pj] : C[(int64_t)pj * ldc + pi];
 }
 
 // ------------------------------------------------------------ sliced apply

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(64 + 32 * G_EPI_WARPS_PER_T * NT, 1)
 k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t m,
               int64_t plane_rows, int x0, int y0, int p, int q, int nxb, int ngroup, int nstages,
               uint32_t stage_bytes, double* __restrict__ C, int64_t ldc, uint32_t* __restrict__ dev_err,
-              const uint32_t* __restrict__ active) {
+              const uint32_t* __restrict__ active, int upper) {
   if (active && *active == 0u) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
@@ -111,7 +111,10 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   constexpr uint32_t BOX = KS * 128;
   constexpr int NEPI = G_EPI_WARPS_PER_T * NT;          // epilogue warps
   constexpr int DRAIN = 128 / KS;                       // stages per TMEM chunk (128 rows)
-  const uint32_t tx_bytes = (uint32_t)(3 * nxb + (SAME ? 0 : 3)) * BOX;
+  // upper (SAME only): column group cg needs rows [0, 64 (cg + 1)) of C,
+  // i.e. the first cg + 1 boxes of X; the rest of C is left to symmetry
+  const int nxl = (SAME && upper) ? min(nxb, (int)blockIdx.y + 1) : nxb;
+  const uint32_t tx_bytes = (uint32_t)(3 * nxl + (SAME ? 0 : 3)) * BOX;
   constexpr uint32_t TCOLS = NT == 1 ? 128 : 256;       // 2 buffers x NT x 64 columns
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * stage_bytes);
   uint64_t* empty = full + nstages;
@@ -154,7 +157,7 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         tc::mbar_arrive_expect_tx(&full[s], tx_bytes);
         for (int sl = 0; sl < 3; ++sl) {
           const int32_t y = (int32_t)(sl * plane_rows + r0);
-          for (int j = 0; j < nxb; ++j)
+          for (int j = 0; j < nxl; ++j)
             tc::tma_load_2d(st + (size_t)(sl * nxb + j) * BOX, &tmX, &full[s], x0 + 64 * j, y);
           if (!SAME) tc::tma_load_2d(st + (size_t)(3 * nxb + sl) * BOX, &tmY, &full[s], y0 + 64 * cg, y);
         }
@@ -188,6 +191,7 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           const uint64_t bS[3] = {b0, tc::sdesc_add(b0, ystride), tc::sdesc_add(b0, 2 * ystride)};
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
+            if (2 * t >= nxl) continue;                    // below the loaded boxes (upper)
             const uint32_t d = tmem + (uint32_t)(b * NT + t) * 64u;
 #pragma unroll
             for (int kk = 0; kk < KS / 16; ++kk) {
@@ -234,7 +238,7 @@ k_gram_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tfree[b]);
     }
-    if (ok && row < p) {
+    if (ok && row < p && row < 64 * nxl) {
       const int c0 = cg * 64 + cs;
 #pragma unroll
       for (int j = 0; j < G_EC; ++j)
@@ -495,7 +499,7 @@ bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* 
   auto launch = [&](auto kern) {
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<dim3(ngroup, ncg), 64 + 32 * G_EPI_WARPS_PER_T * NT, smem, st>>>(
-        tX, tY, m, prow, 0, 0, p, q, nxb, ngroup, nstages, stage_bytes, C, ldc, dev_err, active);
+        tX, tY, m, prow, 0, 0, p, q, nxb, ngroup, nstages, stage_bytes, C, ldc, dev_err, active, 0);
     RPCA_CUDA_TRY(cudaGetLastError());
   };
   if (NT == 2) {
@@ -510,9 +514,10 @@ bool gram_tc(int64_t m, int p, int q, const float* X, int64_t ldx, const float* 
 }
 
 bool gram_slices(int64_t m, int64_t plane_rows, const void* S, int lds, int x0, int p, int y0, int q, double* C,
-                 int64_t ldc, cudaStream_t st, uint32_t* dev_err, const uint32_t* active) {
+                 int64_t ldc, cudaStream_t st, uint32_t* dev_err, const uint32_t* active, bool upper) {
   if (p > 256 || q > 256 || (x0 & 63) || (y0 & 63) || plane_rows % 128) return false;
   const bool same = (x0 == y0 && p == q);
+  if (upper && !same) return false;
   const int NT = (p > 128) ? 2 : 1;
   const int ncg = (int)cdiv(q, 64);
   const int nxb = (int)cdiv(p, 64);
@@ -535,7 +540,8 @@ bool gram_slices(int64_t m, int64_t plane_rows, const void* S, int lds, int x0, 
   auto launch = [&](auto kern) {
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<dim3(ngroup, ncg), 64 + 32 * G_EPI_WARPS_PER_T * NT, smem, st>>>(
-        tS, tS, m, plane_rows, x0, y0, p, q, nxb, ngroup, nstages, stage_bytes, C, ldc, dev_err, active);
+        tS, tS, m, plane_rows, x0, y0, p, q, nxb, ngroup, nstages, stage_bytes, C, ldc, dev_err, active,
+        upper ? 1 : 0);
     RPCA_CUDA_TRY(cudaGetLastError());
   };
   auto pick_ks = [&](auto nt, auto sm) {

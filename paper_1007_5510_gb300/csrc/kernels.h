@@ -97,12 +97,15 @@ void slice_blocks(int64_t m, int64_t plane_rows, int nblk, int l, const float* H
 void unslice_blocks(int64_t m, int64_t plane_rows, int nblk, int l, const void* S, float* H, int64_t ld,
                     cudaStream_t st);
 void col_sums_slices(int64_t m, int64_t plane_rows, int nblk, int l, const void* S, double* out, cudaStream_t st);
-// E (w x w, compact) from C with block-padded indices (ld ldc)
+// E (w x w, compact) from the symmetric C with block-padded indices (ld
+// ldc), read from C's upper block triangle (block row <= block column)
 void compact_sq(int nblk, int l, const double* C, int64_t ldc, double* E, cudaStream_t st);
 // C (p x q FP64, ldc) = X^T Y, X = columns [x0, x0+p), Y = [y0, y0+q) of the
-// slices (x0, y0 multiples of 64)
+// slices (x0, y0 multiples of 64).  upper (X = Y only): only the 64-wide
+// block rows at or above each block column are formed (and read: column
+// group g reads the first g + 1 boxes), the rest of C stays zero.
 bool gram_slices(int64_t m, int64_t plane_rows, const void* S, int lds, int x0, int p, int y0, int q, double* C,
-                 int64_t ldc, cudaStream_t st, uint32_t* dev_err, const uint32_t* active);
+                 int64_t ldc, cudaStream_t st, uint32_t* dev_err, const uint32_t* active, bool upper = false);
 // Y = beta Y + X (alpha M): X = nkb 64-column boxes at x0, Y = the 64 columns
 // at y0 (slices, rewritten when write_slices), M krows x q FP64 (ldm) with
 // row remap rl (block-padded K when rl > 0); optional FP32 copy Yf

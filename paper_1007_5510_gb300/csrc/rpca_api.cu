@@ -255,7 +255,9 @@ static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, vo
     }
   }
   if (E_out) {
-    need(gram_slices(m, prow, S, lds, 0, lds, 0, lds, s.Cfull, lds, st, dev_err, nullptr));
+    // Q^T Q is symmetric: form the upper block triangle only (one read of
+    // block j per block column >= j instead of every block per column)
+    need(gram_slices(m, prow, S, lds, 0, lds, 0, lds, s.Cfull, lds, st, dev_err, nullptr, true));
     compact_sq(nblk, l, s.Cfull, lds, E_out, st);
     sub_identity(nblk * l, E_out, st);
   }
