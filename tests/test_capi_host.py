@@ -43,7 +43,8 @@ def _problem(**kw):
 
 
 @pytest.mark.parametrize("kw", [dict(k=0), dict(k=50), dict(l=4), dict(i=-1), dict(l=30, i=1),
-                                dict(m=0), dict(dtype=9), dict(flags=0x100), dict(l=200, i=1, m=900, n=800)])
+                                dict(m=0), dict(dtype=9), dict(flags=0x100), dict(l=200, i=1, m=900, n=800),
+                                dict(flags=0x20)])     # RPCA_HOST_RESIDENT needs RPCA_HOST_A
 def test_invalid_arguments(lib, kw):
     ctx = ctypes.c_void_p()
     p = _problem(**kw)
