@@ -52,13 +52,17 @@ typedef enum {
   RPCA_ENOMEM = -2,       /* device or pinned-host allocation failed */
   RPCA_ECUDA = -3,        /* a CUDA runtime/driver call failed */
   RPCA_ENODEV = -4,       /* no usable CUDA device */
-  RPCA_EBREAKDOWN = -5,   /* QR could not orthonormalise (rank loss) */
+  RPCA_EBREAKDOWN = -5,   /* QR could not orthonormalise: a block still
+                             needed a shifted Cholesky in its last pass, or
+                             the shifted factorisation failed (numerical
+                             rank loss is otherwise handled) */
   RPCA_ETIMEOUT = -6,     /* a bounded device-side wait gave up */
   RPCA_ESTATE = -7        /* call out of order (e.g. finish before passes) */
 } rpca_status;
 
 /* Storage type of A.  Compute precision: FP64 for RPCA_F64, otherwise FP32
- * accumulation (tensor-core inputs TF32 / BF16 / FP8 widened to BF16). */
+ * accumulation (tensor-core operands BF16, or TF32 x3 for FP32 products;
+ * FP8 bytes are widened on the CUDA cores). */
 typedef enum {
   RPCA_F64 = 0,
   RPCA_F32 = 1,
