@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -44,7 +46,7 @@ CPU_SAMPLE_ROWS = 150_000     # cpu_baseline: one oracle PCA on this many rows (
 REF_SAMPLE_ROWS = 40_000      # --impl reference: rows per timed step
 # DRAM bytes (read + write) per row of A of one launch of the BF16 tensor-core
 # fused pass at n = 4,096, L = 64 (ncu capture at m = 100,000; traffic grows
-# in proportion to the rows), see profiles/fused_pass_bf16_m100000_n4096_l60.md
+# in proportion to the rows)
 FUSED_BF16_N4096_TRAFFIC_PER_ROW = 854.153e6 / 100_000
 
 
@@ -58,6 +60,8 @@ def parse():
                     help="rows of A (precision workload; the oracle arm's sample is capped by it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oracle-accuracy", action="store_true",
+                    help="skip the full-size FP64 oracle run that reports each path's error")
     ap.add_argument("--simt", action="store_true", help="force the CUDA-core pass kernels")
     ap.add_argument("--workload", default="precision", choices=["precision", "batched", "out_of_core"],
                     help="precision: the headline (one 1e6 x 4096 PCA); batched: 512 uneven BF16 PCAs; "
@@ -281,6 +285,11 @@ def main():
                "cores": cores(), "kind": "oracle",
                "sample": "first %d of %d rows of the BF16 matrix, upcast to FP64, one PCA "
                          "(%.1f s)" % (rows, m, secs)}
+        if not args.no_oracle_accuracy:
+            # the same oracle once on the whole FP32 matrix: every path's error
+            # against the FP64 result on the unquantised input
+            acc.update(oracle_errors(A32, k, l, i, W["seed"],
+                                     {"f32": (U32, S32, V32), "bf16": (U16, S16, V16), "fp8": (U8, S8, V8)}))
 
     if rank == 0:
         line = {
@@ -325,6 +334,26 @@ def main():
     ctx8.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def oracle_errors(A32, k, l, i, seed, outs):
+    """Relative singular-value error and largest principal angles of U and
+    V of each output against the FP64 oracle run on the FP32 matrix (rows
+    streamed from a host copy by 8192-row blocks)."""
+    from oracle import rpca_oracle, estimator
+    m, n = A32.shape
+    Ah = A32.cpu()
+    t0 = time.perf_counter()
+    Uo, So, Vo = rpca_oracle.rpca(lambda r0, r1: Ah[r0:r1].numpy(), k, l, i, seed=seed, normalize=True,
+                                  m=m, n=n)
+    res = {"oracle_full_s": round(time.perf_counter() - t0, 1)}
+    for lab, (U, S, V) in outs.items():
+        s = S.cpu().numpy()
+        res["vs_fp64_oracle_" + lab] = {
+            "sigma_rel": float(np.max(np.abs(s - So) / So)),
+            "angle_U": float(estimator.max_principal_angle(U.cpu().double().numpy(), Uo)),
+            "angle_V": float(estimator.max_principal_angle(V.cpu().double().numpy(), Vo))}
+    return res
 
 
 def spectral_errors(A, outs, labels, iters=30, nvec=4):

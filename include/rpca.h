@@ -163,7 +163,8 @@ const char* rpca_last_error(const rpca_ctx* c);
  *   F         = A_c^T H      (n x p, ldf; overwritten; skipped if F NULL)
  * with A_c = A diag(col_scale) - 1 shift^T (shift NULL = 0, FP32/FP64 as
  * compute).  X: n x p, ldx.  p <= 256.  kernel: 0 auto, 1 CUDA cores,
- * 2 tensor cores (RPCA_EINVAL where unsupported). */
+ * 2 tensor cores (RPCA_EINVAL where unsupported).  Synchronises `stream`;
+ * RPCA_ETIMEOUT if a bounded wait inside a tensor-core kernel expired. */
 rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n,
                                int32_t p, const void* A, int64_t lda,
                                const float* col_scale, const void* shift,
@@ -171,7 +172,8 @@ rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n,
                                int64_t ldh, void* F, int64_t ldf,
                                int32_t kernel, void* stream);
 
-/* Step 3 (eq. product_t3): T = A_c^T Q, T n x w (ldt), Q m x w (ldq). */
+/* Step 3 (eq. product_t3): T = A_c^T Q, T n x w (ldt), Q m x w (ldq).
+ * Synchronises `stream`; RPCA_ETIMEOUT as for rpca_op_fused_pass. */
 rpca_status rpca_op_t_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t w,
                            const void* A, int64_t lda, const float* col_scale,
                            const void* shift, const void* Q, int64_t ldq,
@@ -300,14 +302,33 @@ const char* rpca_batch_last_error(const rpca_batch* b);
  * wait inside the kernel expired.  Synchronises `stream`.
  * The scratch address is looked up (cudaGetSymbolAddress) on the first
  * call on each device, with that device current: make that first call
- * before any stream capture.  The error words are cleared on `stream` at
- * the start of every call.  Calls that overlap in time on one device (other
- * streams or host threads) share the scratch and race: serialise them. */
+ * before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset on a device this entry must not be called
+ * on it again.  The error words are cleared on `stream` at the start of
+ * every call.  Calls that overlap in time on one device (other streams or
+ * host threads) share the scratch and race: serialise them. */
 rpca_status rpca_op_fused_pass_noalloc(int64_t m, int64_t n, int32_t p,
                                        const void* A, int64_t lda,
                                        const float* X, int64_t ldx, float* H,
                                        int64_t ldh, float* F, int64_t ldf,
                                        void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Test hook of the bounded device-side waits.  The paper has no           */
+/* counterpart: it exists so that a test can make a wait expire and check  */
+/* that the call reports RPCA_ETIMEOUT and the device stays usable.        */
+/* ---------------------------------------------------------------------- */
+
+/* Arms the next tensor-core launch of one kernel (0: the fused pass of
+ * Step 1, 1: the T pass of Step 3), whichever call makes it: that launch's
+ * first CTA leaves its TMA stage `withhold_stage` unissued (nothing is in
+ * flight for it, so the wait on it can only expire) and every mbarrier wait
+ * of the launch gives up after limit_ns (100 us .. 2 s; the default is 2 s).
+ * The launch then returns early and the call that made it reports
+ * RPCA_ETIMEOUT.  withhold_stage = -1 only shortens the limit.  The arming
+ * is consumed by that one launch.  RPCA_EINVAL for an unknown kernel or a
+ * limit out of range. */
+rpca_status rpca_test_arm_wait_expiry(int32_t kernel, uint64_t limit_ns, int64_t withhold_stage);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ Modules
                the Gaussian test matrix G from a seed (Section 3, Step 1)
   rpca_oracle  the six steps of Section 3 in FP64, streaming A by row blocks
                as in Section 4.2, plus column-mean centering (Section 1)
-  estimator    the Appendix power-method estimate p_{j,k}(D) of ||D||_2 and
-               the error bound of eq. (sort_of_svd)
-  adjoint      FP64 gradients of sum(Sigma) and ||A - U Sigma V^T||_F^2
+  estimator    the Appendix power-method estimate p_{j,k}(D) of ||D||_2, the
+               error bound of eq. (sort_of_svd) and the largest principal
+               angle between two subspaces (the parity metric for U and V)
 """

@@ -172,6 +172,8 @@ struct RRParams {
   float* F;            // n x (l [+1]) FP32, accumulated (zeroed by the host)
   int64_t ldf;
   uint32_t* dev_err;
+  uint64_t wait_ns;    // limit of every bounded wait (2 s; shorter only under the wait-expiry test)
+  int64_t withhold;    // wait-expiry test: GEMM1 stage of CTA 0 left unissued (-1: none)
 };
 
 // Shared-memory layout (bytes from a 1024-aligned base):
@@ -216,6 +218,8 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t lim = p.wait_ns;
+  const int64_t withheld = blockIdx.x == 0 ? p.withhold : -1;
   const uint32_t cs = cluster_nctarank();
   const uint32_t crank = cluster_rank();
   const uint32_t cid = cluster_id_x(), ncl = nclusters_x();
@@ -285,16 +289,18 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         const int32_t r0 = (int32_t)((cid + it * ncl) * RR_BM);
         for (int j = 0; j < RR_NBOX; ++j, ++q) {
           const int s = (int)(q % p.nh);
-          if (!tc::mbar_wait(&hempty[s], (uint32_t)(((q / p.nh) & 1) ^ 1), p.dev_err, abort_flag)) {
+          if (!tc::mbar_wait(&hempty[s], (uint32_t)(((q / p.nh) & 1) ^ 1), p.dev_err, abort_flag, false, lim)) {
             ok = false;
             break;
           }
+          if (q == withheld) continue;        // wait-expiry test: this stage never arrives
           tc::mbar_arrive_expect_tx(&hfull[s], RR_HBOX);
           tc::tma_load_2d_hint(hring + (size_t)s * RR_HBOX, &tmA, &hfull[s], slab0 + 64 * j, r0, pol);
         }
       }
       // let in-flight copies land before the CTA can exit
       for (int64_t qq = (q > p.nh ? q - p.nh : 0); qq < q; ++qq) {
+        if (qq == withheld) continue;
         volatile int never = 0;
         tc::mbar_wait(&hfull[qq % p.nh], (uint32_t)((qq / p.nh) & 1), nullptr, &never);
       }
@@ -304,15 +310,15 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       // ------------------------------------------------------ GEMM1 issue
       constexpr uint32_t idesc1 = tc::idesc_make(1u, 0u, 0u, 128u, (uint32_t)L);
       const uint32_t xs_a = tc::smem_u32(xs);
-      bool ok = tc::mbar_wait(xfull, 0, p.dev_err, abort_flag);
+      bool ok = tc::mbar_wait(xfull, 0, p.dev_err, abort_flag, false, lim);
       int64_t q = 0;
       for (int64_t it = 0; ok && it < my_pan; ++it) {
         const int pb = (int)(it & 1);
-        if (!tc::mbar_wait(&pempty[pb], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag)) break;
+        if (!tc::mbar_wait(&pempty[pb], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag, false, lim)) break;
         tc::tc_fence_after();
         for (int j = 0; j < RR_NBOX; ++j, ++q) {
           const int s = (int)(q % p.nh);
-          if (!tc::mbar_wait(&hfull[s], (uint32_t)((q / p.nh) & 1), p.dev_err, abort_flag)) {
+          if (!tc::mbar_wait(&hfull[s], (uint32_t)((q / p.nh) & 1), p.dev_err, abort_flag, false, lim)) {
             ok = false;
             break;
           }
@@ -341,7 +347,7 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         for (int u = 0; u < 2 * RR_NT; ++u, ++q) {
           const int t = u >> 1, h = u & 1;
           const int s = (int)(q % p.nf);
-          if (!tc::mbar_wait(&fempty[s], (uint32_t)(((q / p.nf) & 1) ^ 1), p.dev_err, abort_flag)) {
+          if (!tc::mbar_wait(&fempty[s], (uint32_t)(((q / p.nf) & 1) ^ 1), p.dev_err, abort_flag, false, lim)) {
             ok = false;
             break;
           }
@@ -365,7 +371,7 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       bool ok = true;
       for (int64_t it = 0; ok && it < my_pan; ++it) {
         const int x = (int)(it & 1);
-        if (!tc::mbar_wait(&hready[x], (uint32_t)((it >> 1) & 1), p.dev_err, abort_flag, true)) break;
+        if (!tc::mbar_wait(&hready[x], (uint32_t)((it >> 1) & 1), p.dev_err, abort_flag, true, lim)) break;
         // Hs[x] was written by the owners' asynchronous stores; order them
         // before the tensor core's reads
         tc::fence_proxy_async_smem();
@@ -375,7 +381,7 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         for (int u = 0; u < 2 * RR_NT; ++u, ++q) {
           const int t = u >> 1, h = u & 1;
           const int s = (int)(q % p.nf);
-          if (!tc::mbar_wait(&ffull[s], (uint32_t)((q / p.nf) & 1), p.dev_err, abort_flag)) {
+          if (!tc::mbar_wait(&ffull[s], (uint32_t)((q / p.nf) & 1), p.dev_err, abort_flag, false, lim)) {
             ok = false;
             break;
           }
@@ -416,9 +422,9 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     for (int64_t it = 0; it < my_pan; ++it) {
       const int pb = (int)(it & 1);
       const int64_t r0 = (cid + it * ncl) * RR_BM;
-      ok = tc::mbar_wait(&pfull[pb], (uint32_t)((it >> 1) & 1), p.dev_err, abort_flag);
+      ok = tc::mbar_wait(&pfull[pb], (uint32_t)((it >> 1) & 1), p.dev_err, abort_flag, false, lim);
       // every owner has summed this CTA's rows of the previous panel
-      ok = ok && tc::mbar_wait(my_rfree, (uint32_t)((it - 1) & 1), p.dev_err, abort_flag, true);
+      ok = ok && tc::mbar_wait(my_rfree, (uint32_t)((it - 1) & 1), p.dev_err, abort_flag, true, lim);
       ok = grp_bar_and(g, ok);
       if (!ok) break;
       tc::tc_fence_after();
@@ -433,9 +439,9 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&pempty[pb]);
       // every sender's rows of this panel have arrived
-      ok = tc::mbar_wait(my_rfull, (uint32_t)(it & 1), p.dev_err, abort_flag, true);
+      ok = tc::mbar_wait(my_rfull, (uint32_t)(it & 1), p.dev_err, abort_flag, true, lim);
       // every CTA's GEMM2 of panel it - 2 has read its Hs[it & 1]
-      if (FUSED) ok = ok && tc::mbar_wait(&hfree[pb], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag, true);
+      if (FUSED) ok = ok && tc::mbar_wait(&hfree[pb], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag, true, lim);
       ok = grp_bar_and(g, ok);
       if (!ok) break;
       if (e == 0) tc::mbar_arrive_expect_tx(my_rfull, RCV_BYTES);   // arm the next panel
@@ -486,7 +492,7 @@ k_fused_rr(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
     // ---------------------------------------------------- flush F slab
     if (FUSED) {
-      bool okd = ok && my_pan > 0 && tc::mbar_wait(done2, 0, p.dev_err, abort_flag);
+      bool okd = ok && my_pan > 0 && tc::mbar_wait(done2, 0, p.dev_err, abort_flag, false, lim);
       okd = grp_bar_and(g, okd);
       tc::tc_fence_after();
       if (okd) {
@@ -592,6 +598,11 @@ bool launch_rr(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   p.F = static_cast<float*>(a.F);
   p.ldf = a.ldf;
   p.dev_err = dev_err;
+  {
+    const WaitTest wt = take_wait_test(0);
+    p.wait_ns = wt.limit_ns;
+    p.withhold = wt.withhold;
+  }
   const size_t smem = fixed + (size_t)p.nh * RR_HBOX + (size_t)p.nf * RR_FST;
   auto kern = k_fused_rr<L, FUSED>;
   cudaLaunchConfig_t cfg = {};

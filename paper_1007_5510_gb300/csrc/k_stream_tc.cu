@@ -75,7 +75,8 @@ template <int NT, typename TF>
 __global__ void __launch_bounds__(TP_THREADS, 1)
 k_tpass_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmQ, int64_t m,
              int64_t n, int w, int npad, int nqbox, int nslab, int ngroup, int nstages, uint32_t stage_bytes,
-             TF* __restrict__ T, int64_t ldt, int qblk, uint32_t* __restrict__ dev_err) {
+             TF* __restrict__ T, int64_t ldt, int qblk, uint32_t* __restrict__ dev_err, uint64_t wait_ns,
+             int64_t withhold) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t a_bytes = NT * 2 * TP_KSUB * 128;
@@ -116,10 +117,14 @@ k_tpass_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
-    for (int64_t it = 0; it < my_subs; ++it) {
+    // wait-expiry test: sub-panel `withheld` of CTA 0 is never issued
+    const int64_t withheld = blockIdx.x == 0 ? withhold : -1;
+    int64_t it = 0;
+    for (; it < my_subs; ++it) {
       const int s = (int)(it % nstages);
       const uint32_t ph = (uint32_t)((it / nstages) & 1);
-      if (!tc::mbar_wait(&empty[s], ph ^ 1u, dev_err, abort_flag)) break;
+      if (!tc::mbar_wait(&empty[s], ph ^ 1u, dev_err, abort_flag, false, wait_ns)) break;
+      if (it == withheld) continue;
       unsigned char* st = smem + (size_t)s * stage_bytes;
       const int32_t r0 = (int32_t)((group + it * ngroup) * TP_KSUB);
       tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
@@ -129,6 +134,13 @@ k_tpass_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       for (int j = 0; j < nqbox; ++j)
         tc::tma_load_2d(st + a_bytes + (size_t)j * TP_KSUB * 128, &tmQ, &full[s], 64 * j, r0);
     }
+    // after an abort, let the copies still in flight land before the CTA
+    // can exit
+    for (int64_t jt = (it > nstages ? it - nstages : 0); jt < it; ++jt) {
+      if (jt == withheld) continue;
+      volatile int never = 0;
+      tc::mbar_wait(&full[jt % nstages], (uint32_t)((jt / nstages) & 1), nullptr, &never);
+    }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------- MMA issue
     const uint32_t idesc = tc::idesc_make(1u, 1u, 1u, 128u, (uint32_t)npad);
@@ -136,7 +148,7 @@ k_tpass_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     for (int64_t it = 0; it < my_subs; ++it) {
       const int s = (int)(it % nstages);
       const uint32_t ph = (uint32_t)((it / nstages) & 1);
-      if (!tc::mbar_wait(&full[s], ph, dev_err, abort_flag)) break;
+      if (!tc::mbar_wait(&full[s], ph, dev_err, abort_flag, false, wait_ns)) break;
       tc::tc_fence_after();
       const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
       const uint32_t sq = sa + a_bytes;
@@ -155,7 +167,7 @@ k_tpass_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   }
   __syncwarp();
   // --------------------------------------------------------------- epilogue
-  bool ok = (my_subs == 0) ? false : tc::mbar_wait(done, 0, dev_err, abort_flag);
+  bool ok = (my_subs == 0) ? false : tc::mbar_wait(done, 0, dev_err, abort_flag, false, wait_ns);
   ok = __all_sync(0xffffffffu, ok);
   tc::tc_fence_after();
   if (ok) {
@@ -180,6 +192,13 @@ k_tpass_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         }
       }
     }
+  }
+  // every MMA issued by this CTA has completed before TMEM is released
+  // (after an abort the wait above returns early; the issuer always commits
+  // `done`)
+  if (warp == 1 && lane == 0) {
+    volatile int never = 0;
+    tc::mbar_wait(done, 0, nullptr, &never);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -227,16 +246,19 @@ static bool tpass_bf16(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   if (!a.accumulate_f)
     RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * fes, 0, a.p * fes, a.n, st));
   dim3 grid(nslab * ngroup);
+  const WaitTest wt = take_wait_test(1);
   if (a.f_f64) {
     auto kern = NT == 2 ? k_tpass_bf16<2, double> : k_tpass_bf16<1, double>;
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, TP_THREADS, smem, st>>>(tmA, tmQ, a.m, a.n, a.p, npad, nqbox, nslab, ngroup, nstages,
-                                          stage_bytes, static_cast<double*>(a.F), a.ldf, qblk, dev_err);
+                                          stage_bytes, static_cast<double*>(a.F), a.ldf, qblk, dev_err, wt.limit_ns,
+                                          wt.withhold);
   } else {
     auto kern = NT == 2 ? k_tpass_bf16<2, float> : k_tpass_bf16<1, float>;
     RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, TP_THREADS, smem, st>>>(tmA, tmQ, a.m, a.n, a.p, npad, nqbox, nslab, ngroup, nstages,
-                                          stage_bytes, static_cast<float*>(a.F), a.ldf, qblk, dev_err);
+                                          stage_bytes, static_cast<float*>(a.F), a.ldf, qblk, dev_err, wt.limit_ns,
+                                          wt.withhold);
   }
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();

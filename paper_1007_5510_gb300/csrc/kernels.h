@@ -35,6 +35,16 @@ struct PassArgs {
   int q_blk = 0;
 };
 
+// Test hook of the bounded-wait path (rpca_test_arm_wait_expiry): the next
+// tensor-core launch of kernel `kind` (0: fused pass, 1: T pass) leaves
+// TMA stage `withhold` of its first CTA unissued and bounds every wait by
+// limit_ns.  Returns {2 s, -1} when nothing is armed; disarms what it returns.
+struct WaitTest {
+  uint64_t limit_ns;
+  int64_t withhold;
+};
+WaitTest take_wait_test(int kind);
+
 void launch_pass_simt(const PassArgs& a, cudaStream_t st);
 // Tensor-core pass; returns false when the shape/dtype is not supported.
 bool launch_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);

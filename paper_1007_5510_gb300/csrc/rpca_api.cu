@@ -3,6 +3,7 @@
 // passes as in Section 4.2).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -14,6 +15,17 @@
 namespace rpca {
 
 std::atomic<uint64_t> g_launches{0};
+
+// -------------------------------------------------- wait-expiry test hook
+static std::mutex g_wait_test_mu;
+static WaitTest g_wait_test[2] = {{2000000000ull, -1}, {2000000000ull, -1}};
+
+WaitTest take_wait_test(int kind) {
+  std::lock_guard<std::mutex> lock(g_wait_test_mu);
+  const WaitTest w = g_wait_test[kind];
+  g_wait_test[kind] = {2000000000ull, -1};
+  return w;
+}
 
 // Error text of the last failed rpca_batch_init (no batch object remains).
 static std::string& last_batch_error() {
@@ -1021,10 +1033,28 @@ rpca_status bguarded(rpca_batch* b, Fn&& fn) {
   }
 }
 
+// Single-op entries: wait for the stream and turn the kernel's error word
+// into a status.
+rpca_status read_op_error(const DevBuf& err, cudaStream_t st) {
+  uint32_t flags = 0;
+  RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (flags & DEV_ERR_TIMEOUT) return RPCA_ETIMEOUT;
+  return RPCA_OK;
+}
+
 }  // namespace
 
 // ================================================================== C-ABI
 extern "C" {
+
+rpca_status rpca_test_arm_wait_expiry(int32_t kernel, uint64_t limit_ns, int64_t withhold_stage) {
+  if (kernel < 0 || kernel > 1 || limit_ns < 100000ull || limit_ns > 2000000000ull || withhold_stage < -1)
+    return RPCA_EINVAL;
+  std::lock_guard<std::mutex> lock(g_wait_test_mu);
+  g_wait_test[kernel] = {limit_ns, withhold_stage};
+  return RPCA_OK;
+}
 
 rpca_status rpca_init(rpca_ctx** out, const rpca_problem* p) {
   if (!out) return RPCA_EINVAL;
@@ -1253,18 +1283,20 @@ rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t p
     a.A = A; a.lda = lda; a.m = m; a.n = n; a.scale = col_scale; a.shift = shift;
     a.X = X; a.ldx = ldx; a.p = p; a.H = H; a.ldh = ldh; a.F = F; a.ldf = ldf;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    DevBuf work;
+    DevBuf work, err;
+    err.alloc(64 * sizeof(uint32_t));
+    RPCA_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, 64 * sizeof(uint32_t), st));
     if (kernel != 1 && dtype != RPCA_F64) {
       work.alloc((size_t)64 * round_up(n, 8) * 2 + 4096);
       a.work = work.ptr;
       a.work_bytes = work.bytes;
     }
     if (kernel == 2) {
-      if (!launch_pass_tc(a, st, nullptr)) throw Invalid("tensor-core pass unsupported for this shape");
-    } else if (kernel == 1 || !launch_pass_tc(a, st, nullptr)) {
+      if (!launch_pass_tc(a, st, err.as<uint32_t>())) throw Invalid("tensor-core pass unsupported for this shape");
+    } else if (kernel == 1 || !launch_pass_tc(a, st, err.as<uint32_t>())) {
       launch_pass_simt(a, st);
     }
-    return RPCA_OK;
+    return read_op_error(err, st);
   });
 }
 
@@ -1281,18 +1313,20 @@ rpca_status rpca_op_t_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t w, co
     a.A = A; a.lda = lda; a.m = m; a.n = n; a.scale = col_scale; a.shift = shift;
     a.p = w; a.H = const_cast<void*>(Q); a.ldh = ldq; a.F = T; a.ldf = ldt;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    DevBuf work;
+    DevBuf work, err;
+    err.alloc(64 * sizeof(uint32_t));
+    RPCA_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, 64 * sizeof(uint32_t), st));
     if (kernel != 1 && dtype != RPCA_F64) {
       work.alloc((size_t)m * round_up(w, 64) * 2 + 4096);
       a.work = work.ptr;
       a.work_bytes = work.bytes;
     }
     if (kernel == 2) {
-      if (!launch_pass_tc(a, st, nullptr)) throw Invalid("tensor-core pass unsupported for this shape");
-    } else if (kernel == 1 || !launch_pass_tc(a, st, nullptr)) {
+      if (!launch_pass_tc(a, st, err.as<uint32_t>())) throw Invalid("tensor-core pass unsupported for this shape");
+    } else if (kernel == 1 || !launch_pass_tc(a, st, err.as<uint32_t>())) {
       launch_pass_simt(a, st);
     }
-    return RPCA_OK;
+    return read_op_error(err, st);
   });
 }
 

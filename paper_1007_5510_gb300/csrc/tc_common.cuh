@@ -60,17 +60,19 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
   return ok != 0;
 }
 
-// Bounded wait: gives up after ~2 s of global time, records DEV_ERR_TIMEOUT
-// in *err (when non-null) and sets *abort so every role can leave its loop.
+// Bounded wait: gives up after limit_ns of global time (2 s by default),
+// records DEV_ERR_TIMEOUT in *err (when non-null) and sets *abort so every
+// role can leave its loop.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err,
-                                          volatile int* abort_flag, bool cluster_scope = false) {
+                                          volatile int* abort_flag, bool cluster_scope = false,
+                                          uint64_t limit_ns = kWaitLimitNs) {
   if (cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     if (cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (global_ns() - t0 > kWaitLimitNs) {
+    if (global_ns() - t0 > limit_ns) {
       if (err) atomicOr(err, DEV_ERR_TIMEOUT);
       *abort_flag = 1;
       return false;

@@ -24,7 +24,7 @@ EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", 
            "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
            "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc",
            "rpca_batch_init", "rpca_batch_run", "rpca_batch_destroy", "rpca_batch_last_error",
-           "rpca_backward"]
+           "rpca_backward", "rpca_test_arm_wait_expiry"]
 
 
 class RpcaError(RuntimeError):
@@ -108,6 +108,8 @@ def load_library(path=None):
     lib.rpca_batch_destroy.restype = None
     lib.rpca_batch_last_error.argtypes = [vp]
     lib.rpca_batch_last_error.restype = ctypes.c_char_p
+    lib.rpca_test_arm_wait_expiry.argtypes = [i32, u64, i64]
+    lib.rpca_test_arm_wait_expiry.restype = st
     if path is None:
         _lib = lib
     return lib
@@ -137,6 +139,43 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _check_shape(t, name, dtypes, rows=None, cols=None):
+    """Validate a matrix argument before its pointer crosses the C-ABI: the
+    library sees only a pointer and a leading dimension, so a wrong type is
+    silently reinterpreted and a short buffer is read or written out of
+    bounds.  Checks element type, rank 2, at least `rows` rows and `cols`
+    columns, unit column stride and a row stride covering the columns.
+    Raises ValueError."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s must be a torch tensor" % name)
+    if t.dtype not in dtypes:
+        raise ValueError("%s: dtype %s, expected one of %s" % (name, t.dtype, [str(d) for d in dtypes]))
+    if t.dim() != 2:
+        raise ValueError("%s must be a 2-D matrix, got %d dimensions" % (name, t.dim()))
+    if rows is not None and t.shape[0] < rows:
+        raise ValueError("%s has %d rows, needs at least %d" % (name, t.shape[0], rows))
+    if cols is not None and t.shape[1] < cols:
+        raise ValueError("%s has %d columns, needs at least %d" % (name, t.shape[1], cols))
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError("%s must have unit column stride (row-major), got stride %s" % (name, t.stride()))
+    if t.stride(0) < max(1, t.shape[1]) and t.shape[0] > 1:
+        raise ValueError("%s: row stride %d is below its column count" % (name, t.stride(0)))
+
+
+def _check_device(t, name, device=None):
+    """t is a CUDA tensor (on `device` when given); raises ValueError."""
+    if t.device.type != "cuda":
+        raise ValueError("%s must be a CUDA tensor, got %s" % (name, t.device))
+    if device is not None and t.device != device:
+        raise ValueError("%s is on %s, expected %s" % (name, t.device, device))
+
+
+def _check_mat(t, name, dtypes, rows=None, cols=None, device=None):
+    _check_shape(t, name, dtypes, rows, cols)
+    _check_device(t, name, device)
+
+
 def dtype_code(t):
     torch = _torch()
     if t.dtype == torch.float64:
@@ -162,6 +201,13 @@ def kernel_launches():
     return int(load_library().rpca_kernel_launches())
 
 
+def arm_wait_expiry(kernel, limit_ns, withhold_stage):
+    """Test hook: the next tensor-core launch of `kernel` (0 fused pass, 1 T
+    pass) leaves one TMA stage unissued and bounds its waits by limit_ns."""
+    _check(load_library().rpca_test_arm_wait_expiry(int(kernel), ctypes.c_uint64(int(limit_ns)),
+                                                     int(withhold_stage)))
+
+
 class PCA:
     """A context: rpca_init on construction, passes, finish, rerun."""
 
@@ -172,6 +218,7 @@ class PCA:
         once into a device copy that the later passes read."""
         lib = load_library()
         self.m, self.n, self.k, self.l, self.i, self.dtype = m, n, k, l, i, dtype
+        self.host_a = bool(host_a)
         flags = ((CENTER if center else 0) | (HOST_A if host_a else 0) | (SIMT if simt else 0)
                  | (ADJOINT if adjoint else 0) | (HOST_RESIDENT if host_resident else 0)
                  | (TIMING if timing else 0))
@@ -187,12 +234,26 @@ class PCA:
         _check(lib.rpca_init(ctypes.byref(self.ctx), ctypes.byref(self.prob)))
 
     def _matrix(self, A, col_scale=None, ld=None):
+        if tuple(A.shape) != (self.m, self.n):
+            raise ValueError("A is %s, the context was made for %d x %d" % (tuple(A.shape), self.m, self.n))
         if isinstance(A, np.ndarray):
+            if not self.host_a:
+                raise ValueError("a host array needs a context made with host_a=True")
+            if A.strides[1] != A.itemsize:
+                raise ValueError("A must have unit column stride")
             data = A.ctypes.data
             ld = A.strides[0] // A.itemsize if ld is None else ld
         else:
+            if self.n > 1 and A.stride(1) != 1:
+                raise ValueError("A must have unit column stride (row-major)")
+            if (A.device.type == "cuda") == self.host_a:
+                raise ValueError("A on %s does not match host_a=%s" % (A.device, self.host_a))
             data = A.data_ptr()
             ld = A.stride(0) if ld is None else ld
+        if col_scale is not None:
+            _check_vec(col_scale, "col_scale", self.n, _torch().float32, col_scale.device)
+            if col_scale.device.type != "cuda":
+                raise ValueError("col_scale must be a CUDA tensor")
         return Matrix(ctypes.c_void_p(data), ld, None if col_scale is None else col_scale.data_ptr())
 
     def passes(self, A, col_scale=None):
@@ -266,6 +327,8 @@ class PCA:
 
 def pca(A, k, l, i, seed=0, center=False, G=None, col_scale=None, simt=False):
     """Rank-k PCA of a device tensor A (FP64/FP32/BF16/FP8 bytes)."""
+    _check_mat(A, "A", _storage_dtypes())
+    _check_vec(col_scale, "col_scale", A.shape[1], _torch().float32, A.device)
     m, n = A.shape
     ctx = PCA(m, n, k, l, i, dtype_code(A), seed=seed, center=center, G=G, simt=simt)
     try:
@@ -372,12 +435,36 @@ class Batch:
 
 
 # --------------------------------------------------------------- single ops
+def _storage_dtypes():
+    torch = _torch()
+    return tuple(d for d in (torch.float64, torch.float32, torch.bfloat16, torch.uint8,
+                             getattr(torch, "float8_e4m3fn", None)) if d is not None)
+
+
+def _check_vec(v, name, n, dtype, device):
+    if v is None:
+        return
+    torch = _torch()
+    if not isinstance(v, torch.Tensor) or v.dtype != dtype or v.numel() < n or not v.is_contiguous():
+        raise ValueError("%s must be a contiguous %s vector of at least %d entries" % (name, dtype, n))
+    if v.device != device:
+        raise ValueError("%s is on %s, expected %s" % (name, v.device, device))
+
+
 def fused_pass(A, X, shift=None, col_scale=None, with_f=True, kernel=0):
     """H = A_c X (and F = A_c^T H): one Step-1 pass.  Returns (H, F)."""
     torch = _torch()
+    _check_shape(A, "A", _storage_dtypes())
     m, n = A.shape
-    p = X.shape[1]
     cdt = torch.float64 if A.dtype == torch.float64 else torch.float32
+    _check_shape(X, "X", (cdt,), rows=n)
+    if X.shape[0] != n:
+        raise ValueError("X has %d rows, A has %d columns" % (X.shape[0], n))
+    _check_device(A, "A")
+    _check_device(X, "X", A.device)
+    _check_vec(shift, "shift", n, cdt, A.device)
+    _check_vec(col_scale, "col_scale", n, torch.float32, A.device)
+    p = X.shape[1]
     H = torch.empty(m, p, dtype=cdt, device=A.device)
     F = torch.empty(n, p, dtype=cdt, device=A.device) if with_f else None
     _check(load_library().rpca_op_fused_pass(
@@ -389,10 +476,24 @@ def fused_pass(A, X, shift=None, col_scale=None, with_f=True, kernel=0):
 
 def fused_pass_noalloc(A, X, H=None, F=None, with_f=True):
     """The tensor-core fused pass (BF16 A, FP32 X) through the entry point
-    that allocates no device memory; H and F may be passed preallocated."""
+    that allocates no device memory; H and F may be passed preallocated.
+    Every argument is checked here (type, shape, strides, device) because
+    the C entry sees only pointers: raises ValueError."""
     torch = _torch()
+    _check_shape(A, "A", (torch.bfloat16,))
     m, n = A.shape
+    _check_shape(X, "X", (torch.float32,), rows=n)
+    if X.shape[0] != n:
+        raise ValueError("X has %d rows, A has %d columns" % (X.shape[0], n))
     p = X.shape[1]
+    if H is not None:
+        _check_shape(H, "H", (torch.float32,), rows=m, cols=p)
+    if F is not None:
+        _check_shape(F, "F", (torch.float32,), rows=n, cols=p)
+    _check_device(A, "A")
+    for t, nm in ((X, "X"), (H, "H"), (F, "F")):
+        if t is not None:
+            _check_device(t, nm, A.device)
     if H is None:
         H = torch.empty(m, p, dtype=torch.float32, device=A.device)
     if F is None and with_f:
@@ -406,9 +507,17 @@ def fused_pass_noalloc(A, X, H=None, F=None, with_f=True):
 def t_pass(A, Q, shift=None, col_scale=None, kernel=0):
     """T = A_c^T Q (Step 3)."""
     torch = _torch()
+    _check_shape(A, "A", _storage_dtypes())
     m, n = A.shape
-    w = Q.shape[1]
     cdt = torch.float64 if A.dtype == torch.float64 else torch.float32
+    _check_shape(Q, "Q", (cdt,), rows=m)
+    if Q.shape[0] != m:
+        raise ValueError("Q has %d rows, A has %d" % (Q.shape[0], m))
+    _check_device(A, "A")
+    _check_device(Q, "Q", A.device)
+    _check_vec(shift, "shift", n, cdt, A.device)
+    _check_vec(col_scale, "col_scale", n, torch.float32, A.device)
+    w = Q.shape[1]
     T = torch.empty(n, w, dtype=cdt, device=A.device)
     _check(load_library().rpca_op_t_pass(
         dtype_code(A), m, n, w, _ptr(A), A.stride(0), _ptr(col_scale), _ptr(shift), _ptr(Q),
@@ -419,6 +528,7 @@ def t_pass(A, Q, shift=None, col_scale=None, kernel=0):
 def qr_inplace(H, nblk, l):
     """Step 2 on H (m x nblk*l): H <- Q."""
     torch = _torch()
+    _check_mat(H, "H", (torch.float32, torch.float64), cols=nblk * l)
     f64 = 1 if H.dtype == torch.float64 else 0
     _check(load_library().rpca_op_qr(f64, H.shape[0], nblk, l, _ptr(H), H.stride(0), _stream_ptr()))
     return H
@@ -428,6 +538,8 @@ def gram(X, Y=None, kernel=0):
     """C = X^T Y (FP64) for FP32 device matrices."""
     torch = _torch()
     Y = X if Y is None else Y
+    _check_mat(X, "X", (torch.float32,))
+    _check_mat(Y, "Y", (torch.float32,), rows=X.shape[0], device=X.device)
     m, pp = X.shape
     q = Y.shape[1]
     C = torch.empty(pp, q, dtype=torch.float64, device=X.device)
@@ -439,10 +551,13 @@ def gram(X, Y=None, kernel=0):
 def apply(X, M, Y=None, alpha=1.0, beta=0.0, kernel=0):
     """Y = beta Y + alpha X M (X FP32, M FP64)."""
     torch = _torch()
+    _check_mat(X, "X", (torch.float32,))
     m, pp = X.shape
+    _check_mat(M, "M", (torch.float64,), rows=pp, device=X.device)
     q = M.shape[1]
     if Y is None:
         Y = torch.zeros(m, q, dtype=torch.float32, device=X.device)
+    _check_mat(Y, "Y", (torch.float32,), rows=m, cols=q, device=X.device)
     _check(load_library().rpca_op_apply(m, pp, q, _ptr(X), X.stride(0), _ptr(M), M.stride(0), alpha, beta,
                                         _ptr(Y), Y.stride(0), kernel, _stream_ptr()))
     return Y
@@ -451,6 +566,7 @@ def apply(X, M, Y=None, alpha=1.0, beta=0.0, kernel=0):
 def small_svd(T):
     """Step 4: T = Vt diag(S) W^T; returns (S, Vt, W)."""
     torch = _torch()
+    _check_mat(T, "T", (torch.float32, torch.float64))
     n, w = T.shape
     f64 = 1 if T.dtype == torch.float64 else 0
     S = torch.empty(w, dtype=torch.float64, device=T.device)

@@ -87,3 +87,16 @@ def test_noalloc_without_device():
     lib = rpca.load_library()
     d = ctypes.c_void_p(256)
     assert lib.rpca_op_fused_pass_noalloc(4096, 1000, 16, d, 1000, d, 16, d, 16, d, 16, None) == -4
+
+
+@pytest.mark.parametrize("kernel,limit,stage", [(2, 20_000_000, 0), (-1, 20_000_000, 0), (0, 10, 0),
+                                                (1, 3_000_000_000, 0), (0, 20_000_000, -2)])
+def test_wait_expiry_hook_checks_its_arguments(lib, kernel, limit, stage):
+    assert lib.rpca_test_arm_wait_expiry(kernel, limit, stage) == -1
+
+
+def test_wait_expiry_hook_arms_and_disarms(lib):
+    """Arming is host state only (no device work); withhold -1 re-arms the
+    default so no later launch is affected."""
+    assert lib.rpca_test_arm_wait_expiry(0, 2_000_000_000, -1) == 0
+    assert lib.rpca_test_arm_wait_expiry(1, 2_000_000_000, -1) == 0

@@ -11,6 +11,9 @@ from synth import generators as gen  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
+# BF16 storage: the tensor cores see X, H and Q rounded to BF16
+BF16_ANGLE = 1e-2
+
 
 def R():
     from paper_1007_5510_gb300 import rpca
@@ -47,7 +50,12 @@ def test_batch_matches_single_problems_and_oracle(dtype):
             assert np.max(np.abs(s - Ss.cpu().numpy()) / s) < tol, p
             Ao = As[p].float().cpu().double().numpy()
             Uo, So, Vo = ro.rpca(Ao, k, l, i, seed=100 + p, normalize=True)
-            assert np.max(np.abs(s - So) / So) < 1e-3, p
-            assert est.max_principal_angle(V.cpu().double().numpy(), Vo) < 1e-2, p
+            rel = np.max(np.abs(s - So) / So)
+            au = est.max_principal_angle(U.cpu().double().numpy(), Uo)
+            av = est.max_principal_angle(V.cpu().double().numpy(), Vo)
+            print("PARITY batch %s problem %d (%d x %d) sigma_rel %.3e angle_U %.3e angle_V %.3e"
+                  % (dtype, p, m, n, rel, au, av))
+            s_tol, a_tol = (1e-3, BF16_ANGLE) if dtype == "bf16" else (1e-4, 1e-3)
+            assert rel < s_tol and au < a_tol and av < a_tol, (p, rel, au, av)
     finally:
         b.close()

@@ -1,13 +1,17 @@
 """Parity at the full workload sizes, in the configuration bench.py times.
 
-fp32_center (200,000 x 2,000, centred) is small enough for the FP64 oracle
-itself.  The precision workload (1,000,000 x 4,096) is not: there the
-outputs are checked through relations that hold exactly at any size and
-that the oracle side evaluates one sampled entry at a time in FP64:
+fp32_center (200,000 x 2,000, centred) runs against the FP64 oracle.  The
+precision workload (1,000,000 x 4,096, k=50 l=60 i=2) runs against the FP64
+oracle too (two oracle runs of a few minutes each on the host cores, one on
+the FP32 values and one on the BF16 values, streamed by row blocks as in
+Section 4.2), and in addition through relations that hold exactly at any
+size:
   * A^T U = V Sigma (Section 3: T = A^T Q = V~ Sigma~ W^T and U = Q W, so
     A^T Q W = V~ Sigma~ column by column), on sampled columns of A;
   * U^T U = I and V^T V = I;
   * the spectral error of the BF16 path within 1.05x of the FP32 path's."""
+import concurrent.futures as cf
+
 import numpy as np
 import pytest
 
@@ -32,13 +36,12 @@ def test_fp32_center_full_size_matches_oracle():
     U, S, V = R().pca(torch.from_numpy(A).cuda(), k, l, i, seed=1007, center=True)
     A64 = A.astype(np.float64)
     Uo, So, Vo = ro.rpca(A64, k, l, i, seed=1007, center=True, normalize=True)
-    Ur, Sr, Vr = ro.rpca(A64, k, l, i, seed=1007, center=True, normalize=False)
-    spread = max(est.max_principal_angle(Uo, Ur), est.max_principal_angle(Vo, Vr))
     s = S.cpu().numpy()
-    assert np.max(np.abs(s - So) / So) <= 1e-4
-    tol = max(1e-3, 2 * spread)
-    assert est.max_principal_angle(U.cpu().double().numpy(), Uo) <= tol
-    assert est.max_principal_angle(V.cpu().double().numpy(), Vo) <= tol
+    rel = np.max(np.abs(s - So) / So)
+    au = est.max_principal_angle(U.cpu().double().numpy(), Uo)
+    av = est.max_principal_angle(V.cpu().double().numpy(), Vo)
+    print("PARITY fp32_center full size sigma_rel %.3e angle_U %.3e angle_V %.3e" % (rel, au, av))
+    assert rel <= 1e-4 and au <= 1e-3 and av <= 1e-3, (rel, au, av)
 
 
 def _spectral_error(A, U, S, V, iters=30, nvec=4):
@@ -98,3 +101,46 @@ def test_precision_full_size_bf16_error_within_5pct_of_fp32(precision_runs):
     e16 = _spectral_error(A32, *out["bf16"])
     e32 = _spectral_error(A32, *out["f32"])
     assert e16 <= 1.05 * e32, (e16, e32)
+
+
+# BF16 storage against the oracle on the same BF16 values (the tensor cores
+# see X, H and Q rounded to BF16)
+BF16_ANGLE = 1e-2
+
+
+def test_precision_full_size_matches_oracle(precision_runs):
+    """FP32 path against the FP64 oracle on the FP32 values (sigma 1e-4,
+    angles 1e-3 rad); BF16 path against the FP64 oracle on the BF16 values.
+    Also prints each path's error against the FP64 result on the FP32
+    matrix (the unquantised input)."""
+    cfg, A32, A16, out = precision_runs
+    m, n, k, l, i = cfg["m"], cfg["n"], cfg["k"], cfg["l"], cfg["i"]
+    A32h = A32.cpu()
+    A16h = A16.cpu()
+
+    def rows32(r0, r1):
+        return A32h[r0:r1].numpy()
+
+    def rows16(r0, r1):
+        return A16h[r0:r1].float().numpy()
+
+    # the two oracle runs overlap on the host cores (NumPy releases the GIL)
+    with cf.ThreadPoolExecutor(2) as ex:
+        f32 = ex.submit(ro.rpca, rows32, k, l, i, seed=1007, normalize=True, m=m, n=n)
+        f16 = ex.submit(ro.rpca, rows16, k, l, i, seed=1007, normalize=True, m=m, n=n)
+        o32, o16 = f32.result(), f16.result()
+    res = {}
+    for name, ref, lab in (("f32", o32, "vs oracle(FP32 values)"), ("bf16", o16, "vs oracle(BF16 values)"),
+                           ("bf16", o32, "vs oracle(FP32 values)")):
+        U, S, V = out[name]
+        s = S.cpu().numpy()
+        rel = float(np.max(np.abs(s - ref[1]) / ref[1]))
+        au = est.max_principal_angle(U.cpu().double().numpy(), ref[0])
+        av = est.max_principal_angle(V.cpu().double().numpy(), ref[2])
+        print("PARITY precision full size %s %s sigma_rel %.3e angle_U %.3e angle_V %.3e"
+              % (name, lab, rel, au, av))
+        res[(name, lab)] = (rel, au, av)
+    rel, au, av = res[("f32", "vs oracle(FP32 values)")]
+    assert rel <= 1e-4 and au <= 1e-3 and av <= 1e-3, (rel, au, av)
+    rel, au, av = res[("bf16", "vs oracle(BF16 values)")]
+    assert rel <= 1e-3 and au <= BF16_ANGLE and av <= BF16_ANGLE, (rel, au, av)

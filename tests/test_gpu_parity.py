@@ -4,8 +4,11 @@ Tolerances.  FP32 workloads: relative singular-value error <= 1e-4 and
 largest principal angle <= 1e-3 rad.  FP64 workload: 1e-10 and 1e-8 rad
 (rounding of the normalised FP64 iteration: span errors of the Cholesky QR
 basis ~ u kappa(H^(0)) ~ 1e-11, amplified by sigma_1 / (sigma_10 - sigma_11)
-~ 2e4 for the singular vectors).  Single passes: elementwise relative to the
-largest entry, 2e-5 (FP32 accumulation over <= a few thousand terms).
+~ 2e4 for the singular vectors).  BF16 storage, against the oracle on the
+same BF16 values: sigma <= 1e-3 and angles <= BF16_ANGLE, where the tensor
+cores see Q rounded to BF16 (2^-9 relative per entry).  Single passes:
+elementwise relative to the largest entry, 2e-5 (FP32 accumulation over <= a
+few thousand terms).
 """
 import numpy as np
 import pytest
@@ -15,6 +18,9 @@ pytestmark = pytest.mark.gpu
 
 from oracle import rpca_oracle as ro, estimator as est  # noqa: E402
 from synth import generators as gen  # noqa: E402
+
+# BF16 whole-method angle bound (see the module docstring)
+BF16_ANGLE = 1e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -182,11 +188,14 @@ def test_small_svd(f64, w):
 
 
 # ------------------------------------------------------------- whole method
-def _compare(U, S, V, Uo, So, Vo, s_tol, a_tol):
+def _compare(U, S, V, Uo, So, Vo, s_tol, a_tol, label=""):
+    """Relative singular-value error and the largest principal angles of U
+    and V against the oracle's (printed, then asserted)."""
     S = S.cpu().numpy()
     rel = np.max(np.abs(S - So) / So)
     au = est.max_principal_angle(U.cpu().double().numpy(), Uo)
     av = est.max_principal_angle(V.cpu().double().numpy(), Vo)
+    print("PARITY %s sigma_rel %.3e angle_U %.3e angle_V %.3e (bounds %.0e, %.0e)" % (label, rel, au, av, s_tol, a_tol))
     assert rel <= s_tol and au <= a_tol and av <= a_tol, (rel, au, av)
     return rel, au, av
 
@@ -197,7 +206,7 @@ def test_pca_fp64_small_workload():
     A = gen.workload_np("fp64_small")
     U, S, V = R().pca(_tt(A, torch.float64), cfg["k"], cfg["l"], cfg["i"], seed=1007)
     Uo, So, Vo = ro.rpca(A, cfg["k"], cfg["l"], cfg["i"], seed=1007, normalize=True)
-    _compare(U, S, V, Uo, So, Vo, 1e-10, 1e-8)
+    _compare(U, S, V, Uo, So, Vo, 1e-10, 1e-8, "fp64_small")
 
 
 @pytest.mark.parametrize("m,n,k,l,i", [(5000, 300, 10, 12, 2), (4099, 1031, 20, 22, 1), (1000, 64, 16, 20, 1)])
@@ -206,7 +215,7 @@ def test_pca_fp32_matches_oracle(m, n, k, l, i):
     A32 = A.astype(np.float32)
     U, S, V = R().pca(_tt(A32), k, l, i, seed=99)
     Uo, So, Vo = ro.rpca(A32.astype(np.float64), k, l, i, seed=99, normalize=True)
-    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "fp32 %dx%d" % (m, n))
 
 
 @pytest.mark.parametrize("dtype,m,n,k,l,i,r", [("f32", 3000, 400, 5, 10, 2, 8), ("f64", 2000, 300, 4, 9, 2, 7),
@@ -235,32 +244,22 @@ def test_pca_exactly_low_rank(dtype, m, n, k, l, i, r):
     assert np.abs(Vd.T @ Vd - np.eye(k)).max() < otol
 
 
-def oracle_spread(A64, k, l, i, seed, center):
-    """Largest principal angle between two FP64 realisations of the same
-    exact-arithmetic result (raw and normalised iteration).  Where the
-    Rayleigh-Ritz subspace is this sensitive to rounding, the 1e-3 rad FP32
-    tolerance is widened to twice this spread."""
-    Uo, So, Vo = ro.rpca(A64, k, l, i, seed=seed, center=center, normalize=True)
-    Ur, Sr, Vr = ro.rpca(A64, k, l, i, seed=seed, center=center, normalize=False)
-    spread = max(est.max_principal_angle(Uo, Ur), est.max_principal_angle(Vo, Vr))
-    return (Uo, So, Vo), spread
-
-
 def test_pca_centered_fp32_reduced():
-    """fp32_center construction at reduced size (m=20,000, n=500), centred."""
+    """fp32_center construction at reduced size (m=20,000, n=500), centred,
+    against the normalised FP64 oracle at the FP32 bounds."""
     A = gen.workload_np("fp32_center", m=20_000, n=500).astype(np.float32)
     U, S, V = R().pca(_tt(A), 20, 22, 2, seed=7, center=True)
-    (Uo, So, Vo), spread = oracle_spread(A.astype(np.float64), 20, 22, 2, 7, True)
-    _compare(U, S, V, Uo, So, Vo, 1e-4, max(1e-3, 2 * spread))
+    Uo, So, Vo = ro.rpca(A.astype(np.float64), 20, 22, 2, seed=7, center=True, normalize=True)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "fp32_center 20000x500")
 
 
 def test_pca_centered_fp64_reduced():
     """The centring corrections (shift in registers, rank-one terms) in FP64
-    reproduce the oracle's explicit centring."""
+    reproduce the oracle's explicit centring at the FP64 bounds."""
     A = gen.workload_np("fp32_center", m=20_000, n=500)
     U, S, V = R().pca(_tt(A, torch.float64), 20, 22, 2, seed=7, center=True)
     Uo, So, Vo = ro.rpca(A, 20, 22, 2, seed=7, center=True, normalize=True)
-    _compare(U, S, V, Uo, So, Vo, 1e-10, 1e-6)
+    _compare(U, S, V, Uo, So, Vo, 1e-10, 1e-8, "fp64_center 20000x500")
 
 
 def test_pca_transposed():
@@ -271,7 +270,7 @@ def test_pca_transposed():
     U, S, V = R().pca(_tt(A32), 6, 8, 1, seed=5)
     assert U.shape == (300, 6) and V.shape == (900, 6)
     Uo, So, Vo = ro.rpca(A32.astype(np.float64), 6, 8, 1, seed=5, normalize=True)
-    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "transposed")
 
 
 def test_explicit_G_equals_seed():
@@ -299,7 +298,7 @@ def test_host_streamed_tiles_match_device():
     U2, S2, V2 = R().pca(_tt(A), 10, 12, 2, seed=3)
     assert torch.allclose(S, S2, rtol=1e-5)
     Uo, So, Vo = ro.rpca(A.astype(np.float64), 10, 12, 2, seed=3, normalize=True)
-    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "host tiles")
 
 
 @pytest.mark.parametrize("dtype,m,n", [("f32", 5000, 256), ("bf16", 20_003, 1024)])
@@ -375,9 +374,19 @@ def test_fused_pass_tensor_cores_bf16(m, n, l, with_f):
     Ho, _ = ro.fused_pass_products(Ao, Xo)
     assert _rel(H.cpu().numpy(), Ho) < 2e-5
     if with_f:
+        Fg = F.cpu().numpy()
         Hb = gen.round_bf16_np(H.cpu().numpy()).astype(np.float64)
         Fo = ro.t_pass_product(Ao, Hb)
-        assert _rel(F.cpu().numpy(), Fo) < 2e-5
+        assert _rel(Fg, Fo) < 2e-5
+        # independent of the GPU's own H: against A^T H_o with the oracle's
+        # unrounded H_o.  The kernel multiplies by bf16(H), |bf16(H) - H| <=
+        # 2^-9 |H| per entry, and |H - H_o| <= 2e-5 max|H_o| (asserted above),
+        # so |F - A^T H_o| <= |A|^T (2^-9 |H_o| + 2e-5 max|H_o|) plus the FP32
+        # accumulation (2e-5 of max|F|).
+        Fo2 = ro.t_pass_product(Ao, Ho)
+        absA = np.abs(Ao)
+        bound = absA.T @ (2.0 ** -9 * np.abs(Ho) + 2e-5 * np.abs(Ho).max()) + 2e-5 * np.abs(Fo2).max()
+        assert np.all(np.abs(Fg - Fo2) <= bound)
 
 
 def test_pca_bf16_tensor_cores_vs_fp32():
@@ -392,8 +401,7 @@ def test_pca_bf16_tensor_cores_vs_fp32():
     U2, S2, V2 = R().pca(_tt(A32), k, l, i, seed=11)
     Aob = Ab.float().cpu().double().numpy()
     Uo, So, Vo = ro.rpca(Aob, k, l, i, seed=11, normalize=True)
-    rel = np.max(np.abs(S.cpu().numpy() - So) / So)
-    assert rel < 1e-3, rel
+    _compare(U, S, V, Uo, So, Vo, 1e-3, BF16_ANGLE, "bf16 whole method")
     e16 = est.spectral_error(A32.astype(np.float64), U.cpu().double().numpy(), S.cpu().numpy(), V.cpu().double().numpy())
     e32 = est.spectral_error(A32.astype(np.float64), U2.cpu().double().numpy(), S2.cpu().numpy(), V2.cpu().double().numpy())
     assert e16 <= 1.05 * e32, (e16, e32)
@@ -406,8 +414,8 @@ def test_pca_fp32_tensor_core_qr():
     A = gen.lowrank_np(m, n, 0.9 ** np.arange(n), seed=21) + 1e-4 * np.random.default_rng(21).standard_normal((m, n))
     A32 = A.astype(np.float32)
     U, S, V = R().pca(_tt(A32), k, l, i, seed=5)
-    (Uo, So, Vo), spread = oracle_spread(A32.astype(np.float64), k, l, i, 5, False)
-    _compare(U, S, V, Uo, So, Vo, 1e-4, max(1e-3, 2 * spread))
+    Uo, So, Vo = ro.rpca(A32.astype(np.float64), k, l, i, seed=5, normalize=True)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "fp32 tensor-core QR")
 
 
 # --------------------------------------- TF32 x3 tensor-core tall products
@@ -510,4 +518,4 @@ def test_pca_fp8_column_scaled_matches_oracle(m, n):
     U, S, V = R().pca(q, k, l, i, seed=5, col_scale=s)
     Adq = (q.view(torch.float8_e4m3fn).float() * s[None, :]).double().cpu().numpy()
     Uo, So, Vo = ro.rpca(Adq, k, l, i, seed=5, normalize=True)
-    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3)
+    _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "fp8 dequantised %dx%d" % (m, n))

@@ -33,6 +33,30 @@ def test_noalloc_matches_fused_pass_on_two_calls(m, n, p, with_f):
             assert F is None
 
 
+def test_noalloc_calls_allocate_no_device_memory():
+    """The property the entry exists for: after a first call (which looks up
+    the scratch address and loads the kernels), twenty more calls on the same
+    buffers leave the device's free memory unchanged.  torch's caching
+    allocator is not touched in between (every buffer exists beforehand)."""
+    import torch
+    rng = np.random.default_rng(7)
+    m, n, p = 20_000, 2048, 32
+    A = torch.from_numpy(rng.standard_normal((m, n)).astype(np.float32)).cuda().to(torch.bfloat16)
+    X = torch.from_numpy(rng.standard_normal((n, p)).astype(np.float32)).cuda()
+    H = torch.empty(m, p, device="cuda")
+    F = torch.empty(n, p, device="cuda")
+    R.fused_pass_noalloc(A, X, H=H, F=F)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    k0 = R.kernel_launches()
+    for _ in range(20):
+        R.fused_pass_noalloc(A, X, H=H, F=F)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert R.kernel_launches() - k0 >= 40            # the pass really ran (2 kernels per call)
+    assert free1 == free0, (free0, free1)
+
+
 def test_noalloc_rejects_n_beyond_scratch():
     import torch
     A = torch.zeros(128, 4104, dtype=torch.bfloat16, device="cuda")
