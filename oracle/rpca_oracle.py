@@ -21,8 +21,19 @@ c the FP64 column means).
 ``normalize=True`` is the reading of the Remark on over/underflow at the end
 of Section 3 (process a normalised iterate): after each F = A^T H^(j) the
 oracle replaces F by the Q factor of its thin QR (positive diagonal R), so
-H^(j+1) = A orth(F).  span(H) is unchanged in exact arithmetic.  This is the
-form the GPU path computes; the default (raw) form is the paper's literal one.
+H^(j+1) = A orth(F).  span(H) is unchanged in exact arithmetic.  The default
+(raw) form is the paper's literal one.
+
+``reorth=True`` (implies normalize) also takes out of F its components along
+every earlier n-side block before orthonormalising it (block Gram-Schmidt,
+applied twice), starting from X^(0) = orth(G): the block Lanczos form of the
+same Krylov space.  span(X^(0..j)) is K_j = span(G, A^T A G, ...,
+(A^T A)^j G) either way (K_{j+1} = K_j + A^T A X^(j)), so span(H) =
+A K_i is unchanged; but H = A [X^(0) .. X^(i)] with orthonormal
+[X^(0) .. X^(i)] has the condition number of A restricted to K_i, where the
+normalised blocks alone give the condition of a Krylov basis (measured:
+2e3 against 6 on the precision workload, 5e10 against 3e4 on the centred
+one).  This is the form the GPU path computes.
 """
 import numpy as np
 
@@ -86,12 +97,24 @@ class RowSource:
             yield r0, r1, B
 
     def column_means(self):
-        s = np.zeros(self.n)
+        """c = (1/m) sum_i A_i (Section 1's column means), by the corrected
+        two-pass algorithm (Chan, Golub and LeVeque, "Algorithms for
+        computing the sample variance", 1983): a first pass gives c0, a
+        second adds the mean of the residuals A_i - c0.  The residuals are
+        small where the columns carry a large offset, so c is the mean to
+        about one rounding of c itself; a plain sum of offset entries errs
+        by ~u log(m) |c|, which on a centred workload shifts the data by a
+        rank-one term large enough to move U."""
         saved, self.shift = self.shift, None
+        s = np.zeros(self.n)
         for _, _, B in self.blocks():
             s += B.sum(axis=0)
+        c0 = s / self.m
+        r = np.zeros(self.n)
+        for _, _, B in self.blocks():
+            r += (B - c0[None, :]).sum(axis=0)
         self.shift = saved
-        return s / self.m
+        return c0 + r / self.m
 
     # Products by row blocks, Section 4.2.
     def times(self, X):
@@ -175,7 +198,8 @@ def orth(F):
 # The algorithm
 # ----------------------------------------------------------------------------
 def rpca(A, k, l, i, G=None, seed=None, center=False, normalize=False,
-         m=None, n=None, block_rows=8192, col_scale=None, return_parts=False):
+         m=None, n=None, block_rows=8192, col_scale=None, return_parts=False,
+         reorth=False):
     """Rank-k approximation A ~ U diag(S) V^T by Section 3's Steps 1-6.
 
     A        ndarray (m x n) or callable rows(r0, r1) (then give m, n)
@@ -200,18 +224,19 @@ def rpca(A, k, l, i, G=None, seed=None, center=False, normalize=False,
         if center:
             At = At - At.mean(axis=0, keepdims=True)
         U, S, V, parts = _rpca_tall(At.T.copy(), k, l, i, G, seed,
-                                    normalize=normalize, block_rows=block_rows)
+                                    normalize=normalize, block_rows=block_rows,
+                                    reorth=reorth)
         parts["transposed"] = True
         return (V, S, U, parts) if return_parts else (V, S, U)
     U, S, V, parts = _rpca_tall(A, k, l, i, G, seed, center=center,
                                 normalize=normalize, block_rows=block_rows,
-                                col_scale=col_scale, m=m, n=n)
+                                col_scale=col_scale, m=m, n=n, reorth=reorth)
     parts["transposed"] = False
     return (U, S, V, parts) if return_parts else (U, S, V)
 
 
 def _rpca_tall(A, k, l, i, G, seed, center=False, normalize=False,
-               block_rows=8192, col_scale=None, m=None, n=None):
+               block_rows=8192, col_scale=None, m=None, n=None, reorth=False):
     src = RowSource(A, m=m, n=n, block_rows=block_rows, col_scale=col_scale)
     if center:
         src.shift = src.column_means()
@@ -227,13 +252,21 @@ def _rpca_tall(A, k, l, i, G, seed, center=False, normalize=False,
 
     # Step 1 (eqs. first_prod .. last_prod, product23)
     blocks = []
-    X = G
+    X = orth(G) if reorth else G
+    earlier = [X]
     for j in range(i + 1):
         Hj = src.times(X)                     # H^(j) = A X
         blocks.append(Hj)
         if j < i:
             F = src.t_times(Hj)               # F = A^T H^(j)
-            X = orth(F) if normalize else F   # H^(j+1) = A F
+            if reorth:
+                P = np.hstack(earlier)
+                for _twice in range(2):
+                    F = F - P @ (P.T @ F)     # out of span(X^(0..j))
+                X = orth(F)
+                earlier.append(X)
+            else:
+                X = orth(F) if normalize else F   # H^(j+1) = A F
     H = np.hstack(blocks)
     # Step 2 (eq. good_approx23)
     Q, R, perm = pivoted_qr(H)

@@ -1074,14 +1074,19 @@ void mat_add(int rows, int cols, const double* src, int64_t lds, double* dst, in
   count_launch();
 }
 
+// FP64 refinement steps after the FP32 Jacobi: each squares the error
+// relative to the gaps; two take an FP32-converged start to FP64 rounding.
+constexpr int kRefineSteps = 2;
+
 void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub, double* W, double* work,
                 uint32_t* dev_err, cudaStream_t st) {
   (void)kk;   // all w triplets are formed
-  // work layout (doubles): Bc [w*w], Jc [w*w], W0 [w*w], B64 [w*w]
+  // work layout (doubles): Bc [w*w], Jc [w*w], W0 [w*w], B64 [w*w], E [w*w]
   double* Bc = work;
   double* Jc = work + (size_t)w * w;
   double* W0 = work + 2 * (size_t)w * w;
   double* B64 = work + 3 * (size_t)w * w;
+  double* Ew = work + 4 * (size_t)w * w;
   if (f64) {
     const size_t mat = (size_t)w * w * sizeof(double);
     const size_t smem = 2 * mat <= 200 * 1024 ? 2 * mat : (mat <= 200 * 1024 ? mat : 0);
@@ -1102,13 +1107,16 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
       count_launch();
     }
     k_jacobi_w<float><<<w, 128, 0, st>>>(w, Jc32, W0);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    // FP64 refinement of the FP32 Jacobi vectors (Bc, Jc are free now)
+    refine_eigvecs64(w, B, W0, Bc, Jc, B64, Ew, kRefineSteps, st);
   }
   RPCA_CUDA_TRY(cudaGetLastError());
-  count_launch(f64 ? 2 : 1);
-  // B64 = B W0: singular values as column norms of B times unit approximate
-  // right singular vectors (second-order accurate).
-  if (f64) gemm_xm(true, w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st, nullptr);
-  else small_gemm_f32(w, w, w, B, w, W0, w, 1.0, 0.0, B64, w, st);
+  if (f64) count_launch(2);
+  // B64 = B W0 in FP64: singular values as column norms of B times unit
+  // right singular vectors (second-order accurate in their error).
+  gemm64_small(w, w, w, 1.0, B, w, false, W0, w, false, 0.0, nullptr, 0, B64, w, st);
   size_t smem = (size_t)w * (2 * sizeof(double) + sizeof(int));
   k_svd_finish<<<1, 256, smem, st>>>(w, B64, W0, S, Ub, W);
   RPCA_CUDA_TRY(cudaGetLastError());

@@ -139,8 +139,19 @@ void add_matrix(bool f64, int64_t rows, int cols, const void* src, int64_t lds, 
 void lowrank_out(bool f64, int64_t m, int64_t n, int r, const void* P, int64_t ldp, const void* Z, int64_t ldz,
                  void* G, int64_t ldg, cudaStream_t st);
 
+// work: 5 w^2 doubles.  FP32 paths: FP32 Jacobi sweeps, then FP64
+// refinement of the right singular vectors (k_small64.cu); FP64: FP64 Jacobi.
 void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub, double* W,
                 double* work, uint32_t* dev_err, cudaStream_t st);
+// C = alpha op(A) op(B) + beta D for small FP64 row-major matrices (D may
+// alias C).
+void gemm64_small(int M, int N, int K, double alpha, const double* A, int64_t lda, bool ta, const double* B,
+                  int64_t ldb, bool tb, double beta, const double* D, int64_t ldd, double* C, int64_t ldc,
+                  cudaStream_t st);
+// `steps` FP64 refinement steps of the eigenvectors X (w x w) of B^T B
+// (k_small64.cu); Xn, P, S, E: w x w scratch.
+void refine_eigvecs64(int w, const double* B, double* X, double* Xn, double* P, double* S, double* E, int steps,
+                      cudaStream_t st);
 
 // ------------------------------------------- tensor-core tall products
 // FP32-accurate (TF32 x3) products on FP32 data carried with a remainder

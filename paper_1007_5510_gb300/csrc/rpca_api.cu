@@ -175,7 +175,7 @@ static void reorth_after_shift(bool f64, int64_t m, int jl, int l, void* H, floa
   qr_gram(f64, m, jl, l, H, ld, Hj, ld, s.C, l, s, st, dev_err, g, true);
   qr_apply(f64, m, jl, l, H, Hlo, ld, s.C, l, -1.0, 1.0, Hj, Hjlo, ld, s, st, dev_err, g);
   qr_gram(f64, m, l, l, Hj, ld, Hj, ld, s.Gm, l, s, st, dev_err, g);
-  chol_small(l, s.Gm, l, s.Rk, s.Rinv, 1, piv_rel, shift_rel, qf, dev_err, st, !f64, g);
+  chol_small(l, s.Gm, l, s.Rk, s.Rinv, 1, piv_rel, shift_rel, qf, dev_err, st, false, g);
   qr_apply(f64, m, l, l, Hj, Hjlo, ld, s.Rinv, l, 1.0, 0.0, Hj, Hjlo, ld, s, st, dev_err, g);
 }
 
@@ -209,7 +209,7 @@ static void block_qr(bool f64, int64_t m, int nblk, int l, void* H, int64_t ld, 
     for (int pass = 0; pass < kCholPasses; ++pass) {
       const uint32_t* active = pass >= 2 ? qf + pass : nullptr;
       qr_gram(f64, m, l, l, Hj, ld, Hj, ld, s.Gm, l, s, st, dev_err, active);
-      chol_small(l, s.Gm, l, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st, !f64);
+      chol_small(l, s.Gm, l, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st, false);
       qr_apply(f64, m, l, l, Hj, Hjlo, ld, s.Rinv, l, 1.0, 0.0, Hj, Hjlo, ld, s, st, dev_err, active);
       if (R_out) left_mul(l, s.Rk, s.Racc, st);
     }
@@ -249,7 +249,7 @@ static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, vo
     for (int pass = 0; pass < kCholPasses; ++pass) {
       const uint32_t* active = pass >= 2 ? qf + pass : nullptr;
       need(gram_slices(m, prow, S, lds, 64 * j, 64, 64 * j, 64, s.G64, 64, st, dev_err, active));
-      chol_small(l, s.G64, 64, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st, true);
+      chol_small(l, s.G64, 64, s.Rk, s.Rinv, pass, piv_rel, shift_rel, qf, dev_err, st, false);
       need(apply_slices(m, prow, S, lds, 64 * j, 1, 64 * j, s.Rinv, l, l, l, 1.0, l, false, true, nullptr, 0, 0,
                         s.mt, st, dev_err, active));
     }
@@ -261,7 +261,7 @@ static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, vo
       need(apply_slices(m, prow, S, lds, 0, j, 64 * j, s.C64, 64 * j, 64, 64, -1.0, 0, true, true, nullptr, 0, 0,
                         s.mt, st, dev_err, g));
       need(gram_slices(m, prow, S, lds, 64 * j, 64, 64 * j, 64, s.G64, 64, st, dev_err, g));
-      chol_small(l, s.G64, 64, s.Rk, s.Rinv, 1, piv_rel, shift_rel, qf, dev_err, st, true, g);
+      chol_small(l, s.G64, 64, s.Rk, s.Rinv, 1, piv_rel, shift_rel, qf, dev_err, st, false, g);
       need(apply_slices(m, prow, S, lds, 64 * j, 1, 64 * j, s.Rinv, l, l, l, 1.0, l, false, true, nullptr, 0, 0,
                         s.mt, st, dev_err, g));
     }
@@ -289,18 +289,16 @@ static void svd_of_T(bool f64, int64_t n, int nblk, int l, int kk, void* T, void
   RPCA_CUDA_TRY(cudaMemcpyAsync(Tc, T, (size_t)n * w * es, cudaMemcpyDeviceToDevice, st));
   block_qr(f64, n, nblk, l, T, w, nullptr, ET, qs, dev_err, st, Tlo);
   qr_gram(f64, n, w, w, T, w, Tc, w, RT, w, qs, st, dev_err);
-  copy_matrix(true, true, w, w, RT, w, RT2, w, st);
-  if (f64) gemm_xm(true, w, w, w, ET, w, RT, w, -0.5, 1.0, RT2, w, st);
-  else small_gemm_f32(w, w, w, ET, w, RT, w, -0.5, 1.0, RT2, w, st);
+  // R_T' = (I - E_T/2) R_T in FP64
+  gemm64_small(w, w, w, -0.5, ET, w, false, RT, w, false, 1.0, RT, w, RT2, w, st);
   jacobi_svd(f64, w, kk, RT2, S, Ub, W, svdwork, dev_err, st);
 }
 
 // Mk (w x k) = (I - E/2) M[:, :k]  (first-order orthonormalisation applied
 // to the small factor)
 static void fold_fixup(bool f64, int w, int k, const double* E, const double* M, double* Mk, cudaStream_t st) {
-  copy_matrix(true, true, w, k, M, w, Mk, k, st);
-  if (f64) gemm_xm(true, w, w, k, E, w, M, w, -0.5, 1.0, Mk, k, st);
-  else small_gemm_f32(w, w, k, E, w, M, w, -0.5, 1.0, Mk, k, st);
+  (void)f64;
+  gemm64_small(w, k, w, -0.5, E, w, false, M, w, false, 1.0, M, w, Mk, k, st);
 }
 
 }  // namespace rpca
@@ -311,6 +309,10 @@ using namespace rpca;
 struct rpca_ctx {
   rpca_problem prob{};
   bool f64 = false, transposed = false, host_a = false, simt = false;
+  // block Lanczos form (every context but RPCA_ADJOINT ones): the n-side
+  // blocks X^(0..i) are kept orthonormal to each other in Xall (n x w)
+  bool reorth = false;
+  DevBuf Xall;
   // RPCA_HOST_RESIDENT: device copy of host A, valid once this run's first
   // pass has copied every tile
   bool resident = false, resident_valid = false;
@@ -489,9 +491,13 @@ void compute_shift(rpca_ctx* c, const rpca_matrix* Am) {
 }
 
 void reset_x(rpca_ctx* c) {
-  // X = G in the compute type, ld = ldx
-  copy_matrix(true, c->f64, c->n, c->l, c->G64.ptr, c->l, c->X.ptr, c->ldx, c->stream);
+  // X = G in the compute type, ld = ldx (the normalised iteration without
+  // reorthogonalisation; the block Lanczos form keeps X^(0) = orth(G) in Xall)
+  if (!c->reorth) copy_matrix(true, c->f64, c->n, c->l, c->G64.ptr, c->l, c->X.ptr, c->ldx, c->stream);
 }
+
+// n-side block j of the block Lanczos basis (Xall, ld w)
+static void* xall_block(rpca_ctx* c, int j) { return static_cast<char*>(c->Xall.ptr) + (size_t)j * c->l * c->cbytes(); }
 
 rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   if (!Am || !Am->data) throw Invalid("null matrix");
@@ -523,8 +529,10 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   if (j <= c->i) {
     // Step 1: pass j forms H^(j) = A_c X and (j < i) F = A_c^T H^(j)
     a.mode = (j < c->i) ? MODE_FUSED : MODE_H;
-    a.X = c->X.ptr;
-    a.ldx = c->ldx;
+    void* Xj = c->reorth ? xall_block(c, j) : c->X.ptr;
+    const int64_t ldxj = c->reorth ? c->w : c->ldx;
+    a.X = Xj;
+    a.ldx = ldxj;
     a.p = c->l;
     a.H = static_cast<char*>(c->H.ptr) + (size_t)j * c->l * es;
     a.ldh = c->w;
@@ -534,7 +542,7 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
     if (c->centered && j == 0 && c->i == 0) a.ones_col = c->l, a.mode = MODE_FUSED;
     if (c->centered && j > 0) {
       // corr = d^T X: H = A~ X - 1 (d^T X)   (A_c = A~ - 1 d^T)
-      vec_mat(f64, c->n, c->l, c->d.as<double>(), c->X.ptr, c->ldx, c->vtmp.as<double>(), st);
+      vec_mat(f64, c->n, c->l, c->d.as<double>(), Xj, ldxj, c->vtmp.as<double>(), st);
       cast_f64_to(f64, c->l, c->vtmp.as<double>(), c->corr.ptr, st);
       a.corr = c->corr.ptr;
     }
@@ -544,13 +552,25 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
     if (c->centered && j == 0) {
       // d = A~^T 1 / m = c - s;  H^(0) -= 1 (d^T G);  F -= m d (d^T G)
       column_to_vec(f64, c->n, c->F.ptr, c->ldx, c->l, 1.0 / (double)c->m, c->d.as<double>(), st);
-      vec_mat(f64, c->n, c->l, c->d.as<double>(), c->X.ptr, c->ldx, c->vtmp.as<double>(), st);
+      vec_mat(f64, c->n, c->l, c->d.as<double>(), Xj, ldxj, c->vtmp.as<double>(), st);
       sub_rowvec(f64, c->m, c->l, c->vtmp.as<double>(), c->H.ptr, c->w, st);
       if (j < c->i)
         rank1_sub(f64, c->n, c->l, (double)c->m, c->d.as<double>(), c->vtmp.as<double>(), c->F.ptr,
                   c->ldx, st);
     }
-    if (j < c->i) {
+    if (j < c->i && c->reorth) {
+      // block Lanczos: X^(j+1) = orth(F - X_{<=j} X_{<=j}^T F), the
+      // projection applied twice (same Krylov space as orth(F), far better
+      // conditioned H)
+      const int jl = (j + 1) * c->l;
+      for (int rep = 0; rep < 2; ++rep) {
+        qr_gram(f64, c->n, jl, c->l, c->Xall.ptr, c->w, c->F.ptr, c->ldx, c->qs.C, c->l, c->qs, st, c->dev_err());
+        qr_apply(f64, c->n, jl, c->l, c->Xall.ptr, nullptr, c->w, c->qs.C, c->l, -1.0, 1.0, c->F.ptr, nullptr,
+                 c->ldx, c->qs, st, c->dev_err());
+      }
+      block_qr(f64, c->n, 1, c->l, c->F.ptr, c->ldx, nullptr, nullptr, c->qs, c->dev_err(), st);
+      copy_matrix(f64, f64, c->n, c->l, c->F.ptr, c->ldx, xall_block(c, j + 1), c->w, st);
+    } else if (j < c->i) {
       // normalised iteration: X = orth(F)
       block_qr(f64, c->n, 1, c->l, c->F.ptr, c->ldx, nullptr, nullptr, c->qs, c->dev_err(), st);
       std::swap(c->X.ptr, c->F.ptr);
@@ -722,8 +742,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->Ub = s; s += w * w;
   c->W = s; s += w * w;
   c->S = s; s += w;
-  c->svdwork = s; s += 4 * w * w;
-  s += w * w;  // spare
+  c->svdwork = s; s += 5 * w * w;
   c->E = s; s += w * w;
   c->ET = s; s += w * w;
   c->RT2 = s; s += w * w;
@@ -798,6 +817,14 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   }
   c->G64.alloc(G.size() * sizeof(double));
   RPCA_CUDA_TRY(cudaMemcpy(c->G64.ptr, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
+  c->reorth = !c->adjoint;
+  if (c->reorth) {
+    // X^(0) = orth(G), once per context (G is fixed)
+    c->Xall.alloc((size_t)c->n * c->w * es);
+    copy_matrix(true, c->f64, c->n, c->l, c->G64.ptr, c->l, c->Xall.ptr, c->w, c->stream);
+    RPCA_CUDA_TRY(cudaMemsetAsync(c->err.ptr, 0, 64 * sizeof(uint32_t), c->stream));
+    block_qr(c->f64, c->n, 1, c->l, c->Xall.ptr, c->w, nullptr, nullptr, c->qs, c->dev_err(), c->stream);
+  }
   c->timing = (p->flags & RPCA_TIMING) != 0;
   if (c->timing) {
     const int nph = c->i + 5;
@@ -1469,7 +1496,7 @@ rpca_status rpca_op_small_svd(int32_t f64, int64_t n, int32_t w, const void* T, 
     double* ET = s; s += ww;
     double* Ub = s; s += ww;
     double* MV = s; s += ww;
-    double* work = s; s += 4 * ww;
+    double* work = s; s += 5 * ww;
     qs.qf = reinterpret_cast<uint32_t*>(s);
     uint32_t* err = qs.qf + kQfWords * nblk;
     RPCA_CUDA_TRY(cudaMemsetAsync(qs.qf, 0, ((size_t)kQfWords * nblk + 64) * sizeof(uint32_t), st));

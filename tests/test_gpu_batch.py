@@ -49,7 +49,7 @@ def test_batch_matches_single_problems_and_oracle(dtype):
             Us, Ss, Vs = rpca.pca(As[p], k, l, i, seed=100 + p)
             assert np.max(np.abs(s - Ss.cpu().numpy()) / s) < tol, p
             Ao = As[p].float().cpu().double().numpy()
-            Uo, So, Vo = ro.rpca(Ao, k, l, i, seed=100 + p, normalize=True)
+            Uo, So, Vo = ro.rpca(Ao, k, l, i, seed=100 + p, reorth=True)
             rel = np.max(np.abs(s - So) / So)
             au = est.max_principal_angle(U.cpu().double().numpy(), Uo)
             av = est.max_principal_angle(V.cpu().double().numpy(), Vo)

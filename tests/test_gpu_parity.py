@@ -205,7 +205,7 @@ def test_pca_fp64_small_workload():
     cfg = gen.CONFIGS["fp64_small"]
     A = gen.workload_np("fp64_small")
     U, S, V = R().pca(_tt(A, torch.float64), cfg["k"], cfg["l"], cfg["i"], seed=1007)
-    Uo, So, Vo = ro.rpca(A, cfg["k"], cfg["l"], cfg["i"], seed=1007, normalize=True)
+    Uo, So, Vo = ro.rpca(A, cfg["k"], cfg["l"], cfg["i"], seed=1007, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-10, 1e-8, "fp64_small")
 
 
@@ -214,7 +214,7 @@ def test_pca_fp32_matches_oracle(m, n, k, l, i):
     A = gen.lowrank_np(m, n, np.arange(1, n + 1) ** -1.0, seed=m) + 1e-4 * np.random.default_rng(1).standard_normal((m, n))
     A32 = A.astype(np.float32)
     U, S, V = R().pca(_tt(A32), k, l, i, seed=99)
-    Uo, So, Vo = ro.rpca(A32.astype(np.float64), k, l, i, seed=99, normalize=True)
+    Uo, So, Vo = ro.rpca(A32.astype(np.float64), k, l, i, seed=99, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "fp32 %dx%d" % (m, n))
 
 
@@ -235,7 +235,7 @@ def test_pca_exactly_low_rank(dtype, m, n, k, l, i, r):
             At = At.to(torch.bfloat16)
     U, S, V = R().pca(At, k, l, i, seed=5)
     Aref = At.double().cpu().numpy()
-    Uo, So, Vo = ro.rpca(Aref, k, l, i, seed=5, normalize=True)
+    Uo, So, Vo = ro.rpca(Aref, k, l, i, seed=5, reorth=True)
     tol = {"f64": 1e-10, "f32": 1e-4, "bf16": 1e-3}[dtype]
     assert np.max(np.abs(S.cpu().numpy() - So) / So) < tol
     Ud, Vd = U.cpu().double().numpy(), V.cpu().double().numpy()
@@ -249,7 +249,7 @@ def test_pca_centered_fp32_reduced():
     against the normalised FP64 oracle at the FP32 bounds."""
     A = gen.workload_np("fp32_center", m=20_000, n=500).astype(np.float32)
     U, S, V = R().pca(_tt(A), 20, 22, 2, seed=7, center=True)
-    Uo, So, Vo = ro.rpca(A.astype(np.float64), 20, 22, 2, seed=7, center=True, normalize=True)
+    Uo, So, Vo = ro.rpca(A.astype(np.float64), 20, 22, 2, seed=7, center=True, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "fp32_center 20000x500")
 
 
@@ -258,7 +258,7 @@ def test_pca_centered_fp64_reduced():
     reproduce the oracle's explicit centring at the FP64 bounds."""
     A = gen.workload_np("fp32_center", m=20_000, n=500)
     U, S, V = R().pca(_tt(A, torch.float64), 20, 22, 2, seed=7, center=True)
-    Uo, So, Vo = ro.rpca(A, 20, 22, 2, seed=7, center=True, normalize=True)
+    Uo, So, Vo = ro.rpca(A, 20, 22, 2, seed=7, center=True, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-10, 1e-8, "fp64_center 20000x500")
 
 
@@ -269,7 +269,7 @@ def test_pca_transposed():
     A32 = A.astype(np.float32)
     U, S, V = R().pca(_tt(A32), 6, 8, 1, seed=5)
     assert U.shape == (300, 6) and V.shape == (900, 6)
-    Uo, So, Vo = ro.rpca(A32.astype(np.float64), 6, 8, 1, seed=5, normalize=True)
+    Uo, So, Vo = ro.rpca(A32.astype(np.float64), 6, 8, 1, seed=5, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "transposed")
 
 
@@ -297,7 +297,7 @@ def test_host_streamed_tiles_match_device():
         ctx.close()
     U2, S2, V2 = R().pca(_tt(A), 10, 12, 2, seed=3)
     assert torch.allclose(S, S2, rtol=1e-5)
-    Uo, So, Vo = ro.rpca(A.astype(np.float64), 10, 12, 2, seed=3, normalize=True)
+    Uo, So, Vo = ro.rpca(A.astype(np.float64), 10, 12, 2, seed=3, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "host tiles")
 
 
@@ -400,7 +400,7 @@ def test_pca_bf16_tensor_cores_vs_fp32():
     U, S, V = R().pca(Ab, k, l, i, seed=11)
     U2, S2, V2 = R().pca(_tt(A32), k, l, i, seed=11)
     Aob = Ab.float().cpu().double().numpy()
-    Uo, So, Vo = ro.rpca(Aob, k, l, i, seed=11, normalize=True)
+    Uo, So, Vo = ro.rpca(Aob, k, l, i, seed=11, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-3, BF16_ANGLE, "bf16 whole method")
     e16 = est.spectral_error(A32.astype(np.float64), U.cpu().double().numpy(), S.cpu().numpy(), V.cpu().double().numpy())
     e32 = est.spectral_error(A32.astype(np.float64), U2.cpu().double().numpy(), S2.cpu().numpy(), V2.cpu().double().numpy())
@@ -414,7 +414,7 @@ def test_pca_fp32_tensor_core_qr():
     A = gen.lowrank_np(m, n, 0.9 ** np.arange(n), seed=21) + 1e-4 * np.random.default_rng(21).standard_normal((m, n))
     A32 = A.astype(np.float32)
     U, S, V = R().pca(_tt(A32), k, l, i, seed=5)
-    Uo, So, Vo = ro.rpca(A32.astype(np.float64), k, l, i, seed=5, normalize=True)
+    Uo, So, Vo = ro.rpca(A32.astype(np.float64), k, l, i, seed=5, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "fp32 tensor-core QR")
 
 
@@ -517,5 +517,5 @@ def test_pca_fp8_column_scaled_matches_oracle(m, n):
     k, l, i = 10, 12, 2
     U, S, V = R().pca(q, k, l, i, seed=5, col_scale=s)
     Adq = (q.view(torch.float8_e4m3fn).float() * s[None, :]).double().cpu().numpy()
-    Uo, So, Vo = ro.rpca(Adq, k, l, i, seed=5, normalize=True)
+    Uo, So, Vo = ro.rpca(Adq, k, l, i, seed=5, reorth=True)
     _compare(U, S, V, Uo, So, Vo, 1e-4, 1e-3, "fp8 dequantised %dx%d" % (m, n))

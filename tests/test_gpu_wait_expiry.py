@@ -82,5 +82,5 @@ def test_whole_pca_wait_expiry_then_normal_run(R):
         R.pca(Ab, k, l, i, seed=3)
     assert e.value.status == -6
     U, S, V = R.pca(Ab, k, l, i, seed=3)
-    Uo, So, Vo = ro.rpca(Ab.float().cpu().double().numpy(), k, l, i, seed=3, normalize=True)
+    Uo, So, Vo = ro.rpca(Ab.float().cpu().double().numpy(), k, l, i, seed=3, reorth=True)
     assert np.max(np.abs(S.cpu().numpy() - So) / So) < 1e-3

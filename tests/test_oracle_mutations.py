@@ -93,6 +93,25 @@ def test_planted_power_step_drop_is_caught(monkeypatch):
     assert caught
 
 
+def test_planted_plain_mean_is_caught(monkeypatch):
+    """A single-pass streamed sum (no correction pass) misses the exactly
+    rounded mean on offset columns."""
+    import math
+
+    def plain(self):
+        t = np.zeros(self.n)
+        for _, _, B in self.blocks():
+            t += B.sum(axis=0)
+        return t / self.m
+    monkeypatch.setattr(ro.RowSource, "column_means", plain)
+    rng = np.random.default_rng(12)
+    m, n = 60_000, 7
+    A = 1e6 * (1.0 + np.arange(n))[None, :] + 1e-3 * rng.standard_normal((m, n))
+    c = ro.RowSource(A, block_rows=64).column_means()
+    exact = np.array([math.fsum(A[:, j]) / m for j in range(n)])
+    assert not np.all(np.abs(c - exact) <= 4 * np.spacing(np.abs(exact)))
+
+
 def test_planted_rng_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(philox, "_M0", np.uint64(0xD2511F55))
     out = philox.philox4x32_10(np.zeros((1, 4), np.uint32), (np.uint32(0), np.uint32(0)))

@@ -156,6 +156,57 @@ def test_normalised_iteration_is_the_accurate_one(small_run):
     np.testing.assert_allclose(S2, S, rtol=1e-5)
 
 
+def test_reorthogonalised_iteration_spans_the_same_space():
+    """Block Lanczos reorthogonalisation (every new n-side block taken out of
+    the span of the earlier ones) changes no span: on a moderately
+    conditioned problem it agrees with the raw and normalised forms to
+    rounding, and it is exact where Q spans range(A)."""
+    A, G, k, l, i = _rand_problem(10, i=2)
+    U, S, V = ro.rpca(A, k, l, i, G=G)
+    U2, S2, V2 = ro.rpca(A, k, l, i, G=G, reorth=True)
+    np.testing.assert_allclose(S2, S, rtol=1e-10)
+    assert est.max_principal_angle(U, U2) < 1e-8
+    assert est.max_principal_angle(V, V2) < 1e-8
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((40, 30))
+    U3, S3, V3 = ro.rpca(B, 4, 15, 1, seed=11, reorth=True)
+    np.testing.assert_allclose(S3, np.linalg.svd(B, compute_uv=False)[:4], rtol=1e-12)
+
+
+def test_reorthogonalised_krylov_block_conditioning():
+    """H = A [X^(0) .. X^(i)] with orthonormal blocks: its singular values
+    lie in [sigma_min(A), sigma_max(A)] (a product with an orthonormal
+    matrix compresses A), so kappa(H) <= kappa(A) -- whatever the spectrum
+    decay that makes the normalised Krylov blocks nearly dependent."""
+    sig = 0.5 ** np.arange(40)                    # kappa(A) = 2^39
+    A = gen.lowrank_np(500, 40, sig, seed=3)
+    _, _, _, parts = ro.rpca(A, 4, 6, 3, seed=2, reorth=True, return_parts=True)
+    H = np.hstack(parts["H"])
+    sv = np.linalg.svd(H, compute_uv=False)
+    assert sv[0] <= sig[0] * (1 + 1e-12) and sv[-1] >= sig[-1] * (1 - 1e-6)
+    _, _, _, pn = ro.rpca(A, 4, 6, 3, seed=2, normalize=True, return_parts=True)
+    svn = np.linalg.svd(np.hstack(pn["H"]), compute_uv=False)
+    assert sv[0] / sv[-1] < 1e-3 * svn[0] / svn[-1]
+
+
+def test_reorthogonalised_form_is_the_accurate_one_on_the_centred_workload():
+    """The centred j^-2 workload makes the normalised Krylov blocks nearly
+    dependent (kappa(H) ~ 7e10), so in FP64 their U moves by ~1e-7 rad when
+    only the order of the row sums changes (a row permutation); the
+    reorthogonalised form (kappa(H) ~ 2e4) moves by ~1e-12: its result is
+    set by the data, not by rounding."""
+    A = gen.workload_np("fp32_center", m=8000, n=400)
+    p = np.random.default_rng(3).permutation(A.shape[0])
+    U, S, V = ro.rpca(A, 20, 22, 2, seed=7, center=True, reorth=True)
+    U2, S2, V2 = ro.rpca(A[p], 20, 22, 2, seed=7, center=True, reorth=True)
+    assert est.max_principal_angle(U[p], U2) < 1e-10
+    assert est.max_principal_angle(V, V2) < 1e-10
+    np.testing.assert_allclose(S2, S, rtol=1e-13)
+    Un, _, _ = ro.rpca(A, 20, 22, 2, seed=7, center=True, normalize=True)
+    Un2, _, _ = ro.rpca(A[p], 20, 22, 2, seed=7, center=True, normalize=True)
+    assert est.max_principal_angle(Un[p], Un2) > 100 * est.max_principal_angle(U[p], U2)
+
+
 # --------------------------------------------------------------- invariances
 def _rand_problem(seed=0, m=300, n=120, k=6, l=8, i=1):  # noqa: E302
     A = gen.lowrank_np(m, n, 0.8 ** np.arange(n), seed) + 1e-3 * np.random.default_rng(seed).standard_normal((m, n))
@@ -204,6 +255,20 @@ def test_centering_shift_invariance_and_definition():
     assert est.max_principal_angle(V2, V) < 1e-8
     # centred left vectors are orthogonal to the ones vector
     assert np.abs(U.sum(axis=0)).max() < 1e-10
+
+
+def test_column_means_match_the_exactly_rounded_mean():
+    """Section 1's column means on columns with a large offset: within a few
+    roundings of the exact mean (math.fsum is an exactly rounded sum), where a
+    plain streamed sum errs by ~u log(m) |offset|."""
+    import math
+    rng = np.random.default_rng(12)
+    m, n = 60_000, 7
+    A = 1e6 * (1.0 + np.arange(n))[None, :] + 1e-3 * rng.standard_normal((m, n))
+    src = ro.RowSource(A, block_rows=64)
+    c = src.column_means()
+    exact = np.array([math.fsum(A[:, j]) / m for j in range(n)])
+    assert np.all(np.abs(c - exact) <= 4 * np.spacing(np.abs(exact)))
 
 
 def test_transpose_rule():
