@@ -56,10 +56,11 @@ enum CvtSrc : int {
   SRC_BF16_SH = 3,  // BF16 with a shift: v = a*scale - shift, split hi/lo
 };
 template <int S> struct SrcInfo;
-template <> struct SrcInfo<SRC_F32> { static constexpr int EB = 4, NA = 2; };
-template <> struct SrcInfo<SRC_FP8> { static constexpr int EB = 1, NA = 1; };
-template <> struct SrcInfo<SRC_FP8_SH> { static constexpr int EB = 1, NA = 2; };
-template <> struct SrcInfo<SRC_BF16_SH> { static constexpr int EB = 2, NA = 2; };
+// NA: BF16 slices per converted element (2: hi and lo; 1: exact in BF16)
+template <> struct SrcInfo<SRC_F32> { static constexpr int NA = 2; };
+template <> struct SrcInfo<SRC_FP8> { static constexpr int NA = 1; };
+template <> struct SrcInfo<SRC_FP8_SH> { static constexpr int NA = 2; };
+template <> struct SrcInfo<SRC_BF16_SH> { static constexpr int NA = 2; };
 
 // Offset of 16-byte chunk j of row r in a 128-byte-swizzled tile (TMA
 // SWIZZLE_128B; the tile starts on a 1024-byte boundary).
@@ -162,9 +163,6 @@ __device__ __forceinline__ void convert_row(const unsigned char* raw, int R, int
   }
 }
 
-// Named barrier over the 4 warps of a 128-thread group (ids 1..).
-__device__ __forceinline__ void bar128(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
-
 template <int N>
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[N]) {
   static_assert(N == 16, "16 columns per load");
@@ -177,5 +175,707 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[N]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+
+// ------------------------------------------------------------------ H pass
+struct HcParams {
+  int64_t m, n;
+  int l;                 // real columns of X / H
+  int ones_col;          // -1, or the H16 column (< 64) set to 1 (centring: F gets A~^T 1)
+  int nkb;               // stages per panel (K steps of 64 G columns)
+  int nstages;
+  uint32_t stage_bytes;
+  const float* scale;    // per-column scale applied by the converter (or null)
+  const float* shift;    // per-column shift (or null)
+  const float* corr;     // l values subtracted from every H row (or null)
+  float* H;              // m x l FP32 (ldh), or null
+  int64_t ldh;
+  __nv_bfloat16* H16;    // hi plane then lo plane (plane16 elements apart), m x 64, or null
+  int64_t plane16;
+  uint32_t* dev_err;
+  uint64_t wait_ns;
+  int64_t withhold;      // wait-expiry test hook (-1: none)
+};
+
+constexpr int HC_THREADS = 384;
+
+// Stage geometry of the H pass (bytes): raw A tile(s), converted tiles
+// (FP32: in place), then the X^T boxes (G groups x NSX slices, L rows x
+// 128 B each).
+template <int SRC> struct HcGeom {
+  static constexpr int G = (SRC == SRC_FP8 || SRC == SRC_FP8_SH) ? 2 : 1;   // 64-column groups per stage
+  static constexpr uint32_t RAW = SRC == SRC_F32 ? 32768u : 16384u;
+  static constexpr bool INPLACE = SRC == SRC_F32;
+  static constexpr uint32_t OUT = INPLACE ? 0u : (uint32_t)G * SrcInfo<SRC>::NA * 16384u;
+  __device__ __forceinline__ static uint32_t hi(int g) {
+    return INPLACE ? 0u : RAW + (uint32_t)g * SrcInfo<SRC>::NA * 16384u;
+  }
+  __device__ __forceinline__ static uint32_t lo(int g) { return hi(g) + 16384u; }
+};
+
+template <int SRC, int L, int NSX>
+__global__ void __launch_bounds__(HC_THREADS, 1)
+k_hpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX0,
+            const __grid_constant__ CUtensorMap tmX1, const HcParams p) {
+  using Geo = HcGeom<SRC>;
+  constexpr int G = Geo::G;
+  constexpr int NA = SrcInfo<SRC>::NA;
+  constexpr uint32_t XB = L * 128;                         // one X^T box: L rows x 64 BF16
+  constexpr uint32_t XOFF = Geo::RAW + Geo::OUT;           // X boxes after the A tiles
+  constexpr uint32_t TX = Geo::RAW + (uint32_t)G * NSX * XB;
+  constexpr uint32_t TMEM_COLS = (2 * L <= 32) ? 32 : (2 * L <= 64) ? 64 : 128;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = p.nstages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_bytes);
+  uint64_t* conv = full + S;
+  uint64_t* empty = conv + S;
+  uint64_t* tfull = empty + S;      // [2]
+  uint64_t* tempty = tfull + 2;     // [2]
+  uint64_t* done = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t lim = p.wait_ns;
+  const int64_t npan = (p.m + 127) / 128;
+  const int64_t my_pan = (npan > blockIdx.x) ? (npan - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&conv[s], 4);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int x = 0; x < 2; ++x) {
+      tc::mbar_init(&tfull[x], 1);
+      tc::mbar_init(&tempty[x], 4);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+    tc::tma_prefetch(&tmA);
+    tc::tma_prefetch(&tmX0);
+    if (NSX == 2) tc::tma_prefetch(&tmX1);
+  }
+  if (warp == 2) {
+    tc::tmem_alloc(tmem_slot, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ TMA
+      const int64_t withheld = blockIdx.x == 0 ? p.withhold : -1;
+      const uint64_t pol = tc::l2_policy_evict_first();      // A is read once
+      int64_t q = 0;
+      bool ok = true;
+      for (int64_t it = 0; ok && it < my_pan; ++it) {
+        const int32_t r0 = (int32_t)((blockIdx.x + it * gridDim.x) * 128);
+        for (int kb = 0; kb < p.nkb; ++kb, ++q) {
+          const int s = (int)(q % S);
+          if (!tc::mbar_wait(&empty[s], (uint32_t)(((q / S) & 1) ^ 1), p.dev_err, abort_flag, false, lim)) {
+            ok = false;
+            break;
+          }
+          if (q == withheld) continue;             // wait-expiry test: never arrives
+          unsigned char* st = smem + (size_t)s * p.stage_bytes;
+          const int32_t c0 = kb * 64 * G;
+          tc::mbar_arrive_expect_tx(&full[s], TX);
+          if constexpr (SRC == SRC_F32) {
+            tc::tma_load_2d_hint(st, &tmA, &full[s], c0, r0, pol);
+            tc::tma_load_2d_hint(st + 16384, &tmA, &full[s], c0 + 32, r0, pol);
+          } else {
+            tc::tma_load_2d_hint(st, &tmA, &full[s], c0, r0, pol);
+          }
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            tc::tma_load_2d(st + XOFF + (uint32_t)(g * NSX) * XB, &tmX0, &full[s], c0 + 64 * g, 0);
+            if (NSX == 2) tc::tma_load_2d(st + XOFF + (uint32_t)(g * NSX + 1) * XB, &tmX1, &full[s], c0 + 64 * g, 0);
+          }
+        }
+      }
+      for (int64_t qq = (q > S ? q - S : 0); qq < q; ++qq) {
+        if (qq == withheld) continue;
+        volatile int never = 0;
+        tc::mbar_wait(&full[qq % S], (uint32_t)((qq / S) & 1), nullptr, &never);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA
+      constexpr uint32_t idesc = tc::idesc_make(1u, 0u, 0u, 128u, (uint32_t)L);
+      int64_t q = 0;
+      bool ok = true;
+      for (int64_t it = 0; ok && it < my_pan; ++it) {
+        const int ab = (int)(it & 1);
+        if (!tc::mbar_wait(&tempty[ab], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag, false, lim)) break;
+        tc::tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(ab * L);
+        for (int kb = 0; kb < p.nkb; ++kb, ++q) {
+          const int s = (int)(q % S);
+          if (!tc::mbar_wait(&conv[s], (uint32_t)((q / S) & 1), p.dev_err, abort_flag, false, lim)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t sb = tc::smem_u32(smem + (size_t)s * p.stage_bytes);
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const uint64_t ah = tc::sdesc_sw128(sb + Geo::hi(g), 16, 1024);
+            const uint64_t al = tc::sdesc_sw128(sb + Geo::lo(g), 16, 1024);
+            const uint64_t x0 = tc::sdesc_sw128(sb + XOFF + (uint32_t)(g * NSX) * XB, 16, 1024);
+            const uint64_t x1 = tc::sdesc_sw128(sb + XOFF + (uint32_t)(g * NSX + 1) * XB, 16, 1024);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t acc = (kb > 0 || g > 0 || kk > 0) ? 1u : 0u;
+              tc::mma_f16(d, tc::sdesc_add(ah, kk * 32), tc::sdesc_add(x0, kk * 32), idesc, acc);
+              if (NA == 2) tc::mma_f16(d, tc::sdesc_add(al, kk * 32), tc::sdesc_add(x0, kk * 32), idesc, 1u);
+              if (NSX == 2) tc::mma_f16(d, tc::sdesc_add(ah, kk * 32), tc::sdesc_add(x1, kk * 32), idesc, 1u);
+            }
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&tfull[ab]);
+      }
+      tc::mma_commit(done);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // --------------------------------------------------------- converters
+    const int r = tid - 128;                       // tile row
+    int64_t q = 0;
+    bool ok = true;
+    for (int64_t it = 0; ok && it < my_pan; ++it) {
+      for (int kb = 0; kb < p.nkb; ++kb, ++q) {
+        const int s = (int)(q % S);
+        if (!tc::mbar_wait(&full[s], (uint32_t)((q / S) & 1), p.dev_err, abort_flag, false, lim)) {
+          ok = false;
+          break;
+        }
+        unsigned char* st = smem + (size_t)s * p.stage_bytes;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int64_t cg = (int64_t)kb * 64 * G + 64 * g;
+          convert_row<SRC>(st, 128, g, st + Geo::hi(g), st + Geo::lo(g), r, p.scale ? p.scale + cg : nullptr,
+                           p.shift ? p.shift + cg : nullptr, (int)(p.n - cg > 64 ? 64 : p.n - cg));
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&conv[s]);
+      }
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;
+    const int row = 32 * quad + lane;
+    for (int64_t it = 0; it < my_pan; ++it) {
+      const int ab = (int)(it & 1);
+      if (!tc::mbar_wait(&tfull[ab], (uint32_t)((it >> 1) & 1), p.dev_err, abort_flag, false, lim)) break;
+      tc::tc_fence_after();
+      const int64_t grow = (blockIdx.x + it * gridDim.x) * 128 + row;
+      float v[L];
+#pragma unroll
+      for (int c16 = 0; c16 < L; c16 += 16) {
+        uint32_t u[16];
+        tmem_ld32<16>(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(ab * L + c16), u);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[c16 + q] = __uint_as_float(u[q]);
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[ab]);   // the accumulator may be reused
+#pragma unroll
+      for (int c = 0; c < L; ++c) {
+        if (p.corr && c < p.l) v[c] -= __ldg(p.corr + c);
+        if (c >= p.l) v[c] = 0.f;
+      }
+      if (grow < p.m) {
+        if (p.H) {
+          float* hrow = p.H + grow * p.ldh;
+          const bool vec = ((reinterpret_cast<uintptr_t>(hrow) | (uintptr_t)(p.ldh * 4)) & 15) == 0;
+#pragma unroll
+          for (int c = 0; c < L; c += 4) {
+            if (vec && c + 3 < p.l) {
+              *reinterpret_cast<float4*>(hrow + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (c + q < p.l) hrow[c + q] = v[c + q];
+            }
+          }
+        }
+        if (p.H16) {
+          uint4* hi = reinterpret_cast<uint4*>(p.H16 + grow * 64);
+          uint4* lo = reinterpret_cast<uint4*>(p.H16 + p.plane16 + grow * 64);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float t[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int c = 8 * j + q;
+              t[q] = c < L ? v[c < L ? c : 0] : 0.f;
+              if (c == p.ones_col) t[q] = 1.f;
+            }
+            uint4 h, l;
+            split8(t, h, l);
+            hi[j] = h;
+            lo[j] = l;
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (warp == 1 && lane == 0) {
+    volatile int never = 0;
+    tc::mbar_wait(done, 0, nullptr, &never);       // every MMA has completed
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// X (n x l FP32, ldx) -> X^T slices (L x n64 BF16 each): hi = bf16(v),
+// lo = bf16(v - hi), v = X[r][j] * fold[r] (fold: the FP8 column scale, or
+// null).
+__global__ void k_xt_split(int64_t n, int l, int L, int64_t n64, const float* __restrict__ X, int64_t ldx,
+                           const float* __restrict__ fold, __nv_bfloat16* __restrict__ Xh,
+                           __nv_bfloat16* __restrict__ Xl) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L * n64) return;
+  const int j = (int)(e / n64);
+  const int64_t r = e % n64;
+  float v = (j < l && r < n) ? X[r * ldx + j] : 0.f;
+  if (fold && r < n) v *= fold[r];
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  Xh[e] = h;
+  if (Xl) Xl[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// ---------------------------------------------------------------- T pass
+constexpr int TC_KSUB = 32;          // rows per stage
+constexpr int TC_THREADS = 256;
+constexpr uint32_t TC_BOX = TC_KSUB * 128;   // one 32-row, 128-byte box
+
+struct TcParams {
+  int64_t m, n;
+  int p;                 // columns of the result (compact)
+  int npad;              // MMA N: columns of Y as stored (multiple of 16, <= 256)
+  int nyb;               // 64-column boxes of Y per slice
+  int qblk;              // > 0: Y is block-padded (block b of qblk columns at 64 b)
+  int nslab, ngroup, nstages;
+  uint32_t stage_bytes;
+  const float* scale;    // converter scale (or null)
+  const float* shift;    // converter shift (or null)
+  const float* rowscale; // result row r multiplied by rowscale[r] (FP8 folding), or null
+  void* T;               // n x p (ldt), TF, accumulated with atomics
+  int64_t ldt;
+  uint32_t* dev_err;
+  uint64_t wait_ns;
+  int64_t withhold;
+};
+
+// Stage geometry of the T pass (bytes from the stage base).  Group g is the
+// 64 columns [64 g, 64 g + 64) of the slab; its hi (and lo) tile is 32 rows
+// x 128 B in the layout of a BF16 TMA box.
+template <int SRC, int NT> struct TcGeom {
+  static constexpr int NG = 2 * NT;
+  static constexpr uint32_t RAW = SRC == SRC_F32 ? NG * 2 * TC_BOX                // 2 FP32 boxes per group
+                                  : SRC == SRC_BF16_SH ? NG * TC_BOX                // 1 BF16 box per group
+                                                       : NT * TC_BOX;               // 1 FP8 box per 2 groups
+  static constexpr bool INPLACE = SRC == SRC_F32;
+  static constexpr int NA = SrcInfo<SRC>::NA;
+  static constexpr uint32_t OUT = INPLACE ? 0u : (uint32_t)NG * NA * TC_BOX;
+  // FP32 in place: group g at 2 g boxes, hi then lo; otherwise after RAW
+  __device__ __forceinline__ static uint32_t hi(int g) {
+    return INPLACE ? (uint32_t)(2 * g) * TC_BOX : RAW + (uint32_t)(g * NA) * TC_BOX;
+  }
+  __device__ __forceinline__ static uint32_t lo(int g) { return hi(g) + TC_BOX; }
+  // distance between the hi tiles of groups 2t and 2t + 1 (the MMA's LBO)
+  static constexpr uint32_t LBO = (INPLACE ? 2 : NA) * TC_BOX;
+  // raw location of group g's data and, for FP8, which half of the box
+  __device__ __forceinline__ static uint32_t raw(int g) {
+    return SRC == SRC_F32 ? (uint32_t)(2 * g) * TC_BOX : SRC == SRC_BF16_SH ? (uint32_t)g * TC_BOX
+                                                                           : (uint32_t)(g >> 1) * TC_BOX;
+  }
+};
+
+template <int SRC, int NT, typename TF, int NSY>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmY0,
+            const __grid_constant__ CUtensorMap tmY1, const TcParams p) {
+  using Geo = TcGeom<SRC, NT>;
+  constexpr int NA = SrcInfo<SRC>::NA;
+  const uint32_t YOFF = Geo::RAW + Geo::OUT;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = p.nstages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_bytes);
+  uint64_t* conv = full + S;
+  uint64_t* empty = conv + S;
+  uint64_t* done = empty + S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t lim = p.wait_ns;
+  const int slab = blockIdx.x % p.nslab;
+  const int group = blockIdx.x / p.nslab;
+  if (group >= p.ngroup) return;
+  const int64_t nsub = (p.m + TC_KSUB - 1) / TC_KSUB;
+  const int64_t my_subs = (nsub > group) ? (nsub - group + p.ngroup - 1) / p.ngroup : 0;
+  const int ncols = NT * p.npad;
+  const uint32_t tmem_cols = ncols <= 32 ? 32 : ncols <= 64 ? 64 : ncols <= 128 ? 128 : ncols <= 256 ? 256 : 512;
+  const uint32_t TX = Geo::RAW + (uint32_t)(NSY * p.nyb) * TC_BOX;
+  const int32_t col0 = slab * NT * 128;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&conv[s], 4);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+    tc::tma_prefetch(&tmA);
+    tc::tma_prefetch(&tmY0);
+    if (NSY == 2) tc::tma_prefetch(&tmY1);
+  }
+  if (warp == 2) {
+    tc::tmem_alloc(tmem_slot, tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // -------------------------------------------------------------- TMA
+    const int64_t withheld = blockIdx.x == 0 ? p.withhold : -1;
+    const uint64_t pol = tc::l2_policy_evict_first();
+    int64_t it = 0;
+    for (; it < my_subs; ++it) {
+      const int s = (int)(it % S);
+      if (!tc::mbar_wait(&empty[s], (uint32_t)(((it / S) & 1) ^ 1), p.dev_err, abort_flag, false, lim)) break;
+      if (it == withheld) continue;
+      unsigned char* st = smem + (size_t)s * p.stage_bytes;
+      const int32_t r0 = (int32_t)((group + it * p.ngroup) * TC_KSUB);
+      tc::mbar_arrive_expect_tx(&full[s], TX);
+      if constexpr (SRC == SRC_F32) {
+        for (int b = 0; b < 4 * NT; ++b) tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 32 * b, r0, pol);
+      } else if constexpr (SRC == SRC_BF16_SH) {
+        for (int b = 0; b < 2 * NT; ++b) tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 64 * b, r0, pol);
+      } else {
+        for (int b = 0; b < NT; ++b) tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 128 * b, r0, pol);
+      }
+      for (int b = 0; b < p.nyb; ++b) {
+        tc::tma_load_2d(st + YOFF + (uint32_t)b * TC_BOX, &tmY0, &full[s], 64 * b, r0);
+        if (NSY == 2) tc::tma_load_2d(st + YOFF + (uint32_t)(p.nyb + b) * TC_BOX, &tmY1, &full[s], 64 * b, r0);
+      }
+    }
+    for (int64_t jt = (it > S ? it - S : 0); jt < it; ++jt) {
+      if (jt == withheld) continue;
+      volatile int never = 0;
+      tc::mbar_wait(&full[jt % S], (uint32_t)((jt / S) & 1), nullptr, &never);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // -------------------------------------------------------------- MMA
+    const uint32_t idesc = tc::idesc_make(1u, 1u, 1u, 128u, (uint32_t)p.npad);
+    for (int64_t it = 0; it < my_subs; ++it) {
+      const int s = (int)(it % S);
+      if (!tc::mbar_wait(&conv[s], (uint32_t)((it / S) & 1), p.dev_err, abort_flag, false, lim)) break;
+      tc::tc_fence_after();
+      const uint32_t sb = tc::smem_u32(smem + (size_t)s * p.stage_bytes);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const uint64_t ah = tc::sdesc_sw128(sb + Geo::hi(2 * t), Geo::LBO, 1024);
+        const uint64_t al = tc::sdesc_sw128(sb + Geo::lo(2 * t), Geo::LBO, 1024);
+        const uint64_t y0 = tc::sdesc_sw128(sb + YOFF, TC_BOX, 1024);
+        const uint64_t y1 = tc::sdesc_sw128(sb + YOFF + (uint32_t)p.nyb * TC_BOX, TC_BOX, 1024);
+        const uint32_t d = tmem + (uint32_t)(t * p.npad);
+#pragma unroll
+        for (int kk = 0; kk < TC_KSUB / 16; ++kk) {
+          const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+          tc::mma_f16(d, tc::sdesc_add(ah, kk * 2048), tc::sdesc_add(y0, kk * 2048), idesc, acc);
+          if (NA == 2) tc::mma_f16(d, tc::sdesc_add(al, kk * 2048), tc::sdesc_add(y0, kk * 2048), idesc, 1u);
+          if (NSY == 2) tc::mma_f16(d, tc::sdesc_add(ah, kk * 2048), tc::sdesc_add(y1, kk * 2048), idesc, 1u);
+        }
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(done);
+  } else if (warp >= 4) {
+    // --------------------------------------------------------- converters
+    const int e = tid - 128;
+    const int r = e & (TC_KSUB - 1), g = e / TC_KSUB;     // row and 64-column group
+    const bool mine = g < Geo::NG;
+    for (int64_t it = 0; it < my_subs; ++it) {
+      const int s = (int)(it % S);
+      if (!tc::mbar_wait(&full[s], (uint32_t)((it / S) & 1), p.dev_err, abort_flag, false, lim)) break;
+      unsigned char* st = smem + (size_t)s * p.stage_bytes;
+      if (mine) {
+        const int64_t cg = (int64_t)col0 + 64 * g;
+        convert_row<SRC>(st + Geo::raw(g), TC_KSUB, g & 1, st + Geo::hi(g), st + Geo::lo(g), r,
+                         p.scale ? p.scale + cg : nullptr, p.shift ? p.shift + cg : nullptr,
+                         (int)(p.n - cg < 0 ? 0 : (p.n - cg > 64 ? 64 : p.n - cg)));
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&conv[s]);
+    }
+  }
+  __syncwarp();
+  // ---------------------------------------------------------------- epilogue
+  bool ok = false;
+  if (warp < 4) {
+    ok = (my_subs == 0) ? false : tc::mbar_wait(done, 0, p.dev_err, abort_flag, false, lim);
+    ok = __all_sync(0xffffffffu, ok);
+    tc::tc_fence_after();
+  }
+  if (warp < 4 && ok) {
+    TF* T = static_cast<TF*>(p.T);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int64_t row = (int64_t)col0 + t * 128 + warp * 32 + lane;   // row of T = column of A
+      const float rs = (p.rowscale && row < p.n) ? p.rowscale[row] : 1.f;
+      for (int c16 = 0; c16 < p.npad; c16 += 16) {
+        uint32_t u[16];
+        tmem_ld32<16>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * p.npad + c16), u);
+        if (row < p.n) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int c = c16 + q;
+            const float v = __uint_as_float(u[q]) * rs;
+            if (p.qblk > 0) {
+              if ((c & 63) < p.qblk && (c >> 6) * p.qblk + (c & 63) < p.p)
+                atomicAdd(&T[row * p.ldt + (c >> 6) * p.qblk + (c & 63)], (TF)v);
+            } else if (c < p.p) {
+              atomicAdd(&T[row * p.ldt + c], (TF)v);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (warp == 1 && lane == 0) {
+    volatile int never = 0;
+    tc::mbar_wait(done, 0, nullptr, &never);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+// ------------------------------------------------------------------- host
+// Q (FP32 m x w, ldq) -> two BF16 planes (hi, lo) of m x wq, zero-padded.
+__global__ void k_split_planes(int64_t m, int w, int wq, const float* __restrict__ Q, int64_t ldq,
+                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * wq) return;
+  const int64_t r = e / wq;
+  const int c = (int)(e % wq);
+  const float v = c < w ? Q[r * ldq + c] : 0.f;
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[e] = h;
+  lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+template <typename K>
+void set_smem(K kern, size_t smem) {
+  RPCA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+
+constexpr size_t CVT_SMEM_LIMIT = 227 * 1024;
+
+CUtensorMapDataType a_tmap_type(int src) {
+  return src == SRC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                        : src == SRC_BF16_SH ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+}
+size_t a_elem(int src) { return src == SRC_F32 ? 4 : src == SRC_BF16_SH ? 2 : 1; }
+
+template <int SRC, int L, int NSX>
+bool launch_hpass(const PassArgs& a, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t n64,
+                  __nv_bfloat16* H16, int64_t plane16, cudaStream_t st, uint32_t* dev_err, const WaitTest& wt) {
+  using Geo = HcGeom<SRC>;
+  CUtensorMap tmA, tmX0, tmX1;
+  const uint32_t abox_cols = SRC == SRC_F32 ? 32 : SRC == SRC_BF16_SH ? 64 : 128;
+  if (!make_tmap_2d(&tmA, a.A, a_tmap_type(SRC), a_elem(SRC), a.m, a.n, a.lda, 128, abox_cols)) return false;
+  if (!make_tmap_2d(&tmX0, Xh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, L, n64, n64, L, 64)) return false;
+  if (!make_tmap_2d(&tmX1, NSX == 2 ? Xl : Xh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, L, n64, n64, L, 64))
+    return false;
+  HcParams p;
+  p.m = a.m;
+  p.n = a.n;
+  p.l = a.p;
+  p.ones_col = a.ones_col;
+  p.nkb = (int)cdiv(a.n, 64 * Geo::G);
+  p.stage_bytes = (uint32_t)round_up(Geo::RAW + Geo::OUT + (uint32_t)Geo::G * NSX * L * 128, 1024);
+  p.nstages = (int)std::min<size_t>(8, (CVT_SMEM_LIMIT - 2048) / p.stage_bytes);
+  if (p.nstages < 2) return false;
+  p.scale = SRC == SRC_FP8 ? nullptr : a.scale;
+  p.shift = static_cast<const float*>(a.shift);
+  p.corr = static_cast<const float*>(a.corr);
+  p.H = static_cast<float*>(a.H);
+  p.ldh = a.ldh;
+  p.H16 = H16;
+  p.plane16 = plane16;
+  p.dev_err = dev_err;
+  p.wait_ns = wt.limit_ns;
+  p.withhold = wt.withhold;
+  const size_t smem = 1024 + (size_t)p.nstages * p.stage_bytes + 256;
+  auto kern = k_hpass_cvt<SRC, L, NSX>;
+  set_smem(kern, smem);
+  const int64_t npan = cdiv(a.m, 128);
+  const int grid = (int)std::min<int64_t>(npan, num_sms());
+  kern<<<grid, HC_THREADS, smem, st>>>(tmA, tmX0, tmX1, p);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  if (getenv("RPCA_DEBUG"))
+    fprintf(stderr, "[rpca] hpass-cvt src=%d L=%d nsx=%d grid=%d stages=%d stage=%u\n", SRC, L, NSX, grid, p.nstages,
+            p.stage_bytes);
+  return true;
+}
+
+// T (n x p) (+)= A_c^T Y, Y = NSY BF16 planes (m x ldy, plane stride `plane`)
+// with nyb 64-column boxes; qblk > 0: block-padded Y.
+template <int SRC, int NSY>
+bool launch_tpass(const PassArgs& a, const __nv_bfloat16* Y, int64_t ldy, int64_t plane, int nyb, int npad, int qblk,
+                  bool f_f64, cudaStream_t st, uint32_t* dev_err, const WaitTest& wt) {
+  const int NT = (2 * npad <= 512) ? 2 : 1;
+  CUtensorMap tmA, tmY0, tmY1;
+  const uint32_t abox_cols = SRC == SRC_F32 ? 32 : SRC == SRC_BF16_SH ? 64 : 128;
+  if (!make_tmap_2d(&tmA, a.A, a_tmap_type(SRC), a_elem(SRC), a.m, a.n, a.lda, TC_KSUB, abox_cols)) return false;
+  if (!make_tmap_2d(&tmY0, Y, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.m, ldy, ldy, TC_KSUB, 64)) return false;
+  if (!make_tmap_2d(&tmY1, NSY == 2 ? Y + plane : Y, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.m, ldy, ldy, TC_KSUB, 64))
+    return false;
+  TcParams p;
+  p.m = a.m;
+  p.n = a.n;
+  p.p = a.mode == MODE_T ? a.p : a.p + (a.ones_col >= 0 ? 1 : 0);
+  p.npad = npad;
+  p.nyb = nyb;
+  p.qblk = qblk;
+  const uint32_t raw_out = NT == 2 ? TcGeom<SRC, 2>::RAW + TcGeom<SRC, 2>::OUT : TcGeom<SRC, 1>::RAW + TcGeom<SRC, 1>::OUT;
+  p.stage_bytes = (uint32_t)round_up(raw_out + (uint32_t)(NSY * nyb) * TC_BOX, 1024);
+  p.nstages = (int)std::min<size_t>(8, (CVT_SMEM_LIMIT - 2048) / p.stage_bytes);
+  if (p.nstages < 2) return false;
+  p.nslab = (int)cdiv(a.n, NT * 128);
+  const int sms = num_sms();
+  p.ngroup = std::max(1, std::min<int>((int)cdiv(a.m, TC_KSUB), sms / p.nslab));
+  p.scale = SRC == SRC_FP8 ? nullptr : a.scale;
+  p.shift = static_cast<const float*>(a.shift);
+  p.rowscale = SRC == SRC_FP8 ? a.scale : nullptr;
+  p.T = a.F;
+  p.ldt = a.ldf;
+  p.dev_err = dev_err;
+  p.wait_ns = wt.limit_ns;
+  p.withhold = wt.withhold;
+  const size_t smem = 1024 + (size_t)p.nstages * p.stage_bytes + 256;
+  dim3 grid(p.nslab * p.ngroup);
+  if (f_f64) {
+    auto kern = NT == 2 ? k_tpass_cvt<SRC, 2, double, NSY> : k_tpass_cvt<SRC, 1, double, NSY>;
+    set_smem(kern, smem);
+    kern<<<grid, TC_THREADS, smem, st>>>(tmA, tmY0, tmY1, p);
+  } else {
+    auto kern = NT == 2 ? k_tpass_cvt<SRC, 2, float, NSY> : k_tpass_cvt<SRC, 1, float, NSY>;
+    set_smem(kern, smem);
+    kern<<<grid, TC_THREADS, smem, st>>>(tmA, tmY0, tmY1, p);
+  }
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  if (getenv("RPCA_DEBUG"))
+    fprintf(stderr, "[rpca] tpass-cvt src=%d NT=%d nsy=%d npad=%d nyb=%d grid=%d stages=%d stage=%u\n", SRC, NT, NSY,
+            npad, nyb, p.nslab * p.ngroup, p.nstages, p.stage_bytes);
+  return true;
+}
+
+template <int SRC>
+bool pass_cvt_src(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
+  const int64_t n64 = round_up(a.n, 128);
+  unsigned char* work = static_cast<unsigned char*>(a.work);
+  if (a.mode == MODE_T) {
+    // Y = Q: the sliced QR's first two BF16 slices when given, else Q in
+    // FP32 split into two planes here
+    const __nv_bfloat16* Y;
+    int64_t ldy, plane;
+    int qblk;
+    if (a.q16) {
+      if (!a.q16_plane) return false;
+      Y = static_cast<const __nv_bfloat16*>(a.q16);
+      ldy = a.q16_ld;
+      plane = a.q16_plane;
+      qblk = a.q_blk;
+    } else {
+      const int wq = (int)round_up(a.p, 64);
+      if (wq > 256) return false;
+      if ((size_t)2 * a.m * wq * 2 > a.work_bytes) return false;
+      __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(work);
+      __nv_bfloat16* lo = hi + (size_t)a.m * wq;
+      const int64_t cnt = a.m * wq;
+      k_split_planes<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(a.m, a.p, wq, static_cast<const float*>(a.H), a.ldh,
+                                                              hi, lo);
+      RPCA_CUDA_TRY(cudaGetLastError());
+      count_launch();
+      Y = hi;
+      ldy = wq;
+      plane = (int64_t)a.m * wq;
+      qblk = 0;
+    }
+    const int nyb = (int)(ldy / 64);
+    const int npad = qblk > 0 ? (int)ldy : (int)round_up(a.p, 16);
+    if (npad > 256) return false;
+    const size_t fes = a.f_f64 ? 8 : 4;
+    if (!a.accumulate_f) RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * fes, 0, a.p * fes, a.n, st));
+    return launch_tpass<SRC, 2>(a, Y, ldy, plane, nyb, npad, qblk, a.f_f64, st, dev_err, take_wait_test(1));
+  }
+  // Step 1 pass: X^T slices, H pass, then (fused) F = A_c^T H from the BF16
+  // slices of H
+  const int need = a.p + (a.ones_col >= 0 ? 1 : 0);
+  const int L = need <= 16 ? 16 : need <= 32 ? 32 : need <= 64 ? 64 : 0;
+  if (!L) return false;
+  const size_t xt_bytes = (size_t)2 * L * n64 * 2;
+  const bool fused = a.mode == MODE_FUSED && a.F;
+  const size_t h16_bytes = fused ? (size_t)2 * a.m * 64 * 2 : 0;
+  if (xt_bytes + h16_bytes + 256 > a.work_bytes) return false;
+  __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(work);
+  __nv_bfloat16* Xl = Xh + (size_t)L * n64;
+  __nv_bfloat16* H16 = fused ? reinterpret_cast<__nv_bfloat16*>(work + round_up(xt_bytes, 256)) : nullptr;
+  {
+    const int64_t cnt = (int64_t)L * n64;
+    k_xt_split<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(a.n, a.p, L, n64, static_cast<const float*>(a.X), a.ldx,
+                                                         SRC == SRC_FP8 ? a.scale : nullptr, Xh, Xl);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  const WaitTest wt = take_wait_test(0);
+  bool ok;
+  if (L == 16) ok = launch_hpass<SRC, 16, 2>(a, Xh, Xl, n64, H16, (int64_t)a.m * 64, st, dev_err, wt);
+  else if (L == 32) ok = launch_hpass<SRC, 32, 2>(a, Xh, Xl, n64, H16, (int64_t)a.m * 64, st, dev_err, wt);
+  else ok = launch_hpass<SRC, 64, 2>(a, Xh, Xl, n64, H16, (int64_t)a.m * 64, st, dev_err, wt);
+  if (!ok || !fused) return ok;
+  if (!a.accumulate_f) RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * 4, 0, need * 4, a.n, st));
+  const WaitTest none = {2000000000ull, -1};
+  return launch_tpass<SRC, 2>(a, H16, 64, (int64_t)a.m * 64, 1, L, 0, false, st, dev_err, none);
+}
+
 }  // namespace
+
+// Whether the converting tensor-core kernels take this pass (see the top of
+// the file), and the pass itself.
+bool pass_cvt(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
+  if (a.dtype != RPCA_F32) return false;
+  if (a.mode != MODE_T && a.mode != MODE_H && a.mode != MODE_FUSED) return false;
+  if (!a.work) return false;
+  if (a.ones_col >= 0 && a.ones_col != a.p) return false;
+  return pass_cvt_src<SRC_F32>(a, st, dev_err);
+}
+
 }  // namespace rpca

@@ -33,6 +33,7 @@ struct PassArgs {
   const void* q16 = nullptr;
   int64_t q16_ld = 0;
   int q_blk = 0;
+  int64_t q16_plane = 0;         // elements between BF16 slice planes of Q (0: one slice)
 };
 
 // Test hook of the bounded-wait path (rpca_test_arm_wait_expiry): the next
@@ -50,6 +51,9 @@ void launch_pass_simt(const PassArgs& a, cudaStream_t st);
 bool launch_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
 // Fused Step-1 pass on tensor cores (k_fused_rr.cu); false if unsupported.
 bool fused_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
+// Passes over FP32 A on tensor cores through converter warps (BF16 hi/lo
+// slices of A and of the small operand; k_stream_cvt.cu); false if unsupported.
+bool pass_cvt(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
 
 // ---------------------------------------------------------------- linalg
 // C (p x q, FP64, ldc) (+)= X^T Y over rows [0, m); X m x p (ldx), Y m x q.

@@ -409,6 +409,28 @@ void validate(const rpca_problem* p) {
   if ((p->flags & RPCA_HOST_A) && p->n > p->m) throw Invalid("RPCA_HOST_A needs n <= m");
 }
 
+// Device scratch of the tensor-core passes: the BF16 copy of Q (T pass),
+// or, for FP32 A (converter kernels), two BF16 planes of Q, or the X^T
+// slices plus the two BF16 planes of H that the F pass reads.
+size_t tc_work_bytes(rpca_dtype dt, int64_t m, int64_t n, int w) {
+  size_t b = (size_t)m * round_up(w, 64) * 2;
+  if (dt == RPCA_F32) {
+    b = std::max<size_t>((size_t)2 * m * round_up(w, 64) * 2,
+                         (size_t)2 * 64 * round_up(n, 128) * 2 + 256 + (size_t)2 * m * 64 * 2);
+  }
+  return b + 4096;
+}
+
+// Will the T pass of an FP32 context read the first two BF16 slices of the
+// sliced Q directly (converter kernel; TMA-aligned A)?
+bool tpass_f32_slices_ok(const rpca_ctx* c, const rpca_matrix* Am) {
+  if (c->prob.dtype != RPCA_F32 || !c->sliced || c->simt || c->adjoint) return false;
+  if (c->host_a) return (c->n * 4) % 16 == 0;
+  const void* A = c->transposed ? c->At.ptr : Am->data;
+  const int64_t lda = c->transposed ? c->n : Am->ld;
+  return (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda * 4) % 16 == 0;
+}
+
 // One streamed pass over the working matrix (device-resident or tiles).
 // Will the T pass run on the BF16 tensor-core kernel (TMA-aligned A, no
 // centring shift or column scale)?
@@ -586,10 +608,11 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   // The BF16 tensor-core T pass reads slice 1 of the sliced Q (= RNE_bf16(Q));
   // every other T pass reads Q in FP32.
   const bool t16 = c->sliced && tpass_bf16_ok(c, Am);
+  const bool t32s = tpass_f32_slices_ok(c, Am);
   c->tic(c->i + 1);
   if (c->sliced)
     block_qr_sliced(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows, c->E,
-                    !t16 || c->adjoint, c->qs, c->dev_err(), st);
+                    !(t16 || t32s) || c->adjoint, c->qs, c->dev_err(), st);
   else
     block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->E, c->qs, c->dev_err(), st,
              c->Hlo.as<float>());
@@ -598,10 +621,12 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   a.p = c->w;
   a.H = c->H.ptr;
   a.ldh = c->w;
-  if (t16) {
+  if (t16 || t32s) {
     a.q16 = c->Hs.ptr;
     a.q16_ld = (c->i + 1) * 64;
     a.q_blk = c->l;
+    // FP32: Q = slice 1 + slice 2 (the third slice is below 2^-17 of Q)
+    if (t32s) a.q16_plane = c->hs_rows * (c->i + 1) * 64;
   }
   a.F = c->T64.ptr;   // FP64 accumulation across row blocks
   a.ldf = c->w;
@@ -751,7 +776,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->qs.qf = reinterpret_cast<uint32_t*>(s);
   RPCA_CUDA_TRY(cudaMemsetAsync(c->qs.qf, 0, qf_words * sizeof(uint32_t), c->stream));
   if (c->transposed) c->At.alloc((size_t)c->m * c->n * dtype_bytes(p->dtype));
-  if (!c->simt) c->work.alloc((size_t)c->m * round_up(c->w, 64) * 2 + 4096);
+  if (!c->simt) c->work.alloc(tc_work_bytes(p->dtype, c->m, c->n, c->w));
   if (!c->f64) {
     c->mt.alloc(2 * 256 * 256 * sizeof(float));
     c->qs.mt = c->mt.as<float>();
@@ -1314,7 +1339,7 @@ rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t p
     err.alloc(64 * sizeof(uint32_t));
     RPCA_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, 64 * sizeof(uint32_t), st));
     if (kernel != 1 && dtype != RPCA_F64) {
-      work.alloc((size_t)64 * round_up(n, 8) * 2 + 4096);
+      work.alloc(dtype == RPCA_F32 ? tc_work_bytes(dtype, m, n, 64) : (size_t)64 * round_up(n, 8) * 2 + 4096);
       a.work = work.ptr;
       a.work_bytes = work.bytes;
     }
@@ -1344,7 +1369,7 @@ rpca_status rpca_op_t_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t w, co
     err.alloc(64 * sizeof(uint32_t));
     RPCA_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, 64 * sizeof(uint32_t), st));
     if (kernel != 1 && dtype != RPCA_F64) {
-      work.alloc((size_t)m * round_up(w, 64) * 2 + 4096);
+      work.alloc(tc_work_bytes(dtype, m, n, w));
       a.work = work.ptr;
       a.work_bytes = work.bytes;
     }

@@ -389,6 +389,65 @@ def test_fused_pass_tensor_cores_bf16(m, n, l, with_f):
         assert np.all(np.abs(Fg - Fo2) <= bound)
 
 
+# ---------------------------- tensor-core passes over FP32 A (converters)
+@pytest.mark.parametrize("m,n,l", [(1000, 512, 12), (5000, 4096, 60), (777, 1000, 22), (3001, 2000, 30),
+                                   (300, 64, 20), (40_001, 2600, 63)])
+@pytest.mark.parametrize("with_f", [True, False])
+def test_fused_pass_tensor_cores_f32(m, n, l, with_f):
+    """FP32 A on the tensor cores: converter warps split A and X into BF16
+    hi/lo slices (hi*hi + lo*hi + hi*lo, FP32 accumulation), then F from
+    the hi/lo slices of H.  Against the oracle on the FP32 values."""
+    rng = np.random.default_rng(m + n + l + 1)
+    A = rng.standard_normal((m, n))
+    X = rng.standard_normal((n, l))
+    At, Ao = _stored(A, "f32")
+    H, F = R().fused_pass(At, _tt(X), with_f=with_f, kernel=2)
+    torch.cuda.synchronize()
+    Ho, Fo = ro.fused_pass_products(Ao, X.astype(np.float32).astype(np.float64))
+    eh = _rel(H.cpu().numpy(), Ho)
+    print("PARITY fused f32 tc %dx%d l=%d H %.2e" % (m, n, l, eh), end="")
+    assert eh < 3e-5
+    if with_f:
+        ef = _rel(F.cpu().numpy(), Fo)
+        print(" F %.2e" % ef, end="")
+        assert ef < 5e-5
+    print()
+
+
+@pytest.mark.parametrize("m,n,l", [(20_000, 500, 22), (4099, 1031, 20)])
+def test_fused_pass_tensor_cores_f32_shift_and_scale(m, n, l):
+    """The centring shift and a per-column scale applied by the converter:
+    A_c = A diag(c) - 1 s^T in FP32 before the split."""
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, n)) * 0.01 + 3.0
+    X = rng.standard_normal((n, l))
+    c = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    A32 = A.astype(np.float32)
+    s = (A32[:128].astype(np.float64) * c).mean(axis=0).astype(np.float32)
+    H, F = R().fused_pass(_tt(A32), _tt(X), shift=_tt(s), col_scale=_tt(c), kernel=2)
+    torch.cuda.synchronize()
+    Ho, Fo = ro.fused_pass_products(A32.astype(np.float64), X.astype(np.float32).astype(np.float64),
+                                    shift=s.astype(np.float64), col_scale=c.astype(np.float64))
+    eh, ef = _rel(H.cpu().numpy(), Ho), _rel(F.cpu().numpy(), Fo)
+    print("PARITY fused f32 tc shift+scale %dx%d H %.2e F %.2e" % (m, n, eh, ef))
+    assert eh < 5e-5 and ef < 1e-4
+
+
+@pytest.mark.parametrize("m,n,w", [(3001, 512, 66), (5000, 520, 180), (20000, 4096, 180), (777, 256, 24)])
+def test_t_pass_tensor_cores_f32(m, n, w):
+    """T = A^T Q for FP32 A on the tensor cores (A and Q as BF16 hi/lo)."""
+    rng = np.random.default_rng(m + w + 1)
+    A = rng.standard_normal((m, n))
+    Q = np.linalg.qr(rng.standard_normal((m, w)))[0]
+    At, Ao = _stored(A, "f32")
+    T = R().t_pass(At, _tt(Q), kernel=2)
+    torch.cuda.synchronize()
+    To = ro.t_pass_product(Ao, Q.astype(np.float32).astype(np.float64))
+    e = _rel(T.cpu().numpy(), To)
+    print("PARITY t pass f32 tc %dx%d w=%d %.2e" % (m, n, w, e))
+    assert e < 5e-5
+
+
 def test_pca_bf16_tensor_cores_vs_fp32():
     """Whole method on BF16 storage (tensor-core passes) against the oracle on
     the same BF16 values, and its spectral error against the FP32 path's."""
