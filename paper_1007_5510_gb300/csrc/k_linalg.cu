@@ -1130,6 +1130,45 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
   }
 }
 
+// Step 4 from the Gram matrix G = T^T T (FP32-class paths).  FP32 Jacobi
+// sweeps on a shifted FP32 Cholesky factor of G give approximate right
+// singular vectors of T to a loose tolerance; the FP64 refinement against G
+// itself then takes them to FP64 accuracy (each step squares the error), and
+// sigma_j^2 are the diagonal of the refined X^T G X.  With the
+// reorthogonalised Krylov blocks T is well conditioned (its singular values
+// are those of A on the Krylov space), so forming G loses nothing the
+// tolerances can see.
+constexpr double kGramJacobiTol = 1e-4;
+constexpr int kGramRefineSteps = 3;
+
+void svd_from_gram(int w, const double* G, double* S, double* Vs, double* W, double* work, uint32_t* dev_err,
+                   cudaStream_t st) {
+  const size_t ww = (size_t)w * w;
+  double* B = work;
+  float* Jc32 = reinterpret_cast<float*>(work + ww);
+  double* X = work + 2 * ww;
+  double* Xn = work + 3 * ww;
+  double* P = work + 4 * ww;
+  double* Sm = work + 5 * ww;
+  double* E = B;                                   // B is free once the sweeps are done
+  chol32_shift(w, G, B, st);
+  if (getenv("RPCA_JACOBI_SINGLE") || !jacobi_cluster_f32(w, B, Jc32, kGramJacobiTol, 40, dev_err, st)) {
+    const size_t mat = ww * sizeof(float);
+    const size_t smem = 2 * mat <= 200 * 1024 ? 2 * mat : (mat <= 200 * 1024 ? mat : 0);
+    RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_jacobi<float><<<1, 1024, smem, st>>>(w, B, reinterpret_cast<float*>(Xn), Jc32, kGramJacobiTol, 40, dev_err);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  k_jacobi_w<float><<<w, 128, 0, st>>>(w, Jc32, X);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  refine_eigvecs64(w, G, X, Xn, P, Sm, E, kGramRefineSteps, st, true);
+  gemm64_small(w, w, w, 1.0, G, w, false, X, w, false, 0.0, nullptr, 0, P, w, st);     // G X
+  gemm64_small(w, w, w, 1.0, X, w, true, P, w, false, 0.0, nullptr, 0, Sm, w, st);    // X^T G X
+  eig_finish(w, Sm, X, S, Vs, W, st);
+}
+
 void small_gemm_f32(int m, int p, int q, const double* X, int64_t ldx, const double* M, int64_t ldm,
                     double alpha, double beta, double* Y, int64_t ldy, cudaStream_t st) {
   if (m <= 0 || q <= 0) return;

@@ -128,7 +128,87 @@ k_refine_correction(int w, const double* __restrict__ S, const double* __restric
   }
 }
 
+// B (upper triangular, w x w, FP64 container) with B^T B = G + delta I to
+// FP32 accuracy: right-looking Cholesky in FP32 in shared memory, one CTA.
+// It only preconditions Step 4 (its output seeds the FP32 Jacobi sweeps,
+// whose vectors are then refined in FP64 against G itself), so a shift
+// delta = 1e-6 max diag(G) keeps it defined whatever G's conditioning: the
+// shift moves every eigenvalue by delta and no eigenvector.
+__global__ void __launch_bounds__(1024) k_chol32_shift(int w, const double* __restrict__ G, double* __restrict__ B) {
+  extern __shared__ float cm[];                 // w x ws
+  const int ws = w | 1;
+  __shared__ float dmax, piv;
+  const int tid = threadIdx.x;
+  if (tid == 0) dmax = 0.f;
+  __syncthreads();
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int i = e / w, j = e % w;
+    cm[i * ws + j] = (float)G[e];
+    if (i == j) atomicMax(reinterpret_cast<int*>(&dmax), __float_as_int(fmaxf((float)G[e], 0.f)));
+  }
+  __syncthreads();
+  const float delta = 1e-6f * dmax;
+  for (int i = tid; i < w; i += blockDim.x) cm[i * ws + i] += delta;
+  __syncthreads();
+  for (int k = 0; k < w; ++k) {
+    if (tid == 0) piv = sqrtf(fmaxf(cm[k * ws + k], delta));
+    __syncthreads();
+    const float d = piv, inv = 1.f / piv;
+    for (int j = k + tid; j < w; j += blockDim.x) cm[k * ws + j] = (j == k) ? d : cm[k * ws + j] * inv;
+    __syncthreads();
+    const int r = w - k - 1;
+    for (int e = tid; e < r * r; e += blockDim.x) {
+      const int i = k + 1 + e / r, j = k + 1 + e % r;
+      if (j >= i) cm[i * ws + j] -= cm[k * ws + i] * cm[k * ws + j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int i = e / w, j = e % w;
+    B[e] = j >= i ? (double)cm[i * ws + j] : 0.0;
+  }
+}
+
+// Eigenvalues lambda_j = S_jj of the refined S = X^T G X, sorted
+// descending: sigma_j = sqrt(lambda_j) (S_out), W = X with its columns in
+// that order, and Vs = W diag(1/sigma) (the factor that takes T to its left
+// singular vectors, V = T W Sigma^-1).  One CTA.
+__global__ void k_eig_finish(int w, const double* __restrict__ Sm, const double* __restrict__ X,
+                             double* __restrict__ S_out, double* __restrict__ Vs, double* __restrict__ W) {
+  extern __shared__ double sig[];
+  int* pos = reinterpret_cast<int*>(sig + w);
+  for (int c = threadIdx.x; c < w; c += blockDim.x) sig[c] = sqrt(fmax(Sm[(int64_t)c * w + c], 0.0));
+  __syncthreads();
+  for (int c = threadIdx.x; c < w; c += blockDim.x) {
+    int rank = 0;
+    for (int o = 0; o < w; ++o) rank += (sig[o] > sig[c]) || (sig[o] == sig[c] && o < c);
+    pos[c] = rank;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+    const int r = e / w, c = e % w;
+    const int d = pos[c];
+    W[(int64_t)r * w + d] = X[e];
+    Vs[(int64_t)r * w + d] = sig[c] > 0.0 ? X[e] / sig[c] : 0.0;
+  }
+  for (int c = threadIdx.x; c < w; c += blockDim.x) S_out[pos[c]] = sig[c];
+}
+
 }  // namespace
+
+void chol32_shift(int w, const double* G, double* B, cudaStream_t st) {
+  const size_t smem = (size_t)w * (w | 1) * sizeof(float);
+  RPCA_CUDA_TRY(cudaFuncSetAttribute(k_chol32_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_chol32_shift<<<1, 1024, smem, st>>>(w, G, B);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void eig_finish(int w, const double* Sm, const double* X, double* S, double* Vs, double* W, cudaStream_t st) {
+  k_eig_finish<<<1, 256, (size_t)w * (sizeof(double) + sizeof(int)), st>>>(w, Sm, X, S, Vs, W);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
 
 void gemm64_small(int M, int N, int K, double alpha, const double* A, int64_t lda, bool ta, const double* B,
                   int64_t ldb, bool tb, double beta, const double* D, int64_t ldd, double* C, int64_t ldc,
@@ -142,12 +222,15 @@ void gemm64_small(int M, int N, int K, double alpha, const double* A, int64_t ld
 }
 
 void refine_eigvecs64(int w, const double* B, double* X, double* Xn, double* P, double* S, double* E, int steps,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool gram_given) {
   double* cur = X;
   double* nxt = Xn;
   for (int it = 0; it < steps; ++it) {
-    gemm64_small(w, w, w, 1.0, B, w, false, cur, w, false, 0.0, nullptr, 0, P, w, st);   // P = B X
-    gemm64_small(w, w, w, 1.0, P, w, true, P, w, false, 0.0, nullptr, 0, S, w, st);     // S = P^T P
+    gemm64_small(w, w, w, 1.0, B, w, false, cur, w, false, 0.0, nullptr, 0, P, w, st);   // P = B X (or G X)
+    if (gram_given)
+      gemm64_small(w, w, w, 1.0, cur, w, true, P, w, false, 0.0, nullptr, 0, S, w, st);  // S = X^T G X
+    else
+      gemm64_small(w, w, w, 1.0, P, w, true, P, w, false, 0.0, nullptr, 0, S, w, st);   // S = P^T P
     gemm64_small(w, w, w, 1.0, cur, w, true, cur, w, false, 0.0, nullptr, 0, E, w, st); // X^T X
     k_refine_correction<<<1, 1024, (size_t)w * sizeof(double), st>>>(w, S, E, E);
     RPCA_CUDA_TRY(cudaGetLastError());

@@ -54,6 +54,7 @@ enum CvtSrc : int {
   SRC_FP8 = 1,      // FP8-e4m3, no shift: widened exactly (scale folded outside)
   SRC_FP8_SH = 2,   // FP8-e4m3 with a shift: v = a*scale - shift, split hi/lo
   SRC_BF16_SH = 3,  // BF16 with a shift: v = a*scale - shift, split hi/lo
+  SRC_BF16 = 4,     // BF16 as stored (T pass only): no conversion
 };
 template <int S> struct SrcInfo;
 // NA: BF16 slices per converted element (2: hi and lo; 1: exact in BF16)
@@ -61,6 +62,7 @@ template <> struct SrcInfo<SRC_F32> { static constexpr int NA = 2; };
 template <> struct SrcInfo<SRC_FP8> { static constexpr int NA = 1; };
 template <> struct SrcInfo<SRC_FP8_SH> { static constexpr int NA = 2; };
 template <> struct SrcInfo<SRC_BF16_SH> { static constexpr int NA = 2; };
+template <> struct SrcInfo<SRC_BF16> { static constexpr int NA = 1; };
 
 // Offset of 16-byte chunk j of row r in a 128-byte-swizzled tile (TMA
 // SWIZZLE_128B; the tile starts on a 1024-byte boundary).
@@ -197,6 +199,11 @@ struct HcParams {
 };
 
 constexpr int HC_THREADS = 384;
+// K stages per accumulation chunk of the H pass: each chunk is summed in
+// tensor memory from zero and the chunks are added in FP32 registers
+// (rounding to nearest), which bounds the accumulator's biased rounding
+// (see TC_FL below) to one chunk.
+constexpr int HC_FLK = 8;
 
 // Stage geometry of the H pass (bytes): raw A tile(s), converted tiles
 // (FP32: in place), then the X^T boxes (G groups x NSX slices, L rows x
@@ -311,12 +318,20 @@ k_hpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       constexpr uint32_t idesc = tc::idesc_make(1u, 0u, 0u, 128u, (uint32_t)L);
       int64_t q = 0;
       bool ok = true;
+      int64_t gch = 0;                           // accumulation chunks so far
       for (int64_t it = 0; ok && it < my_pan; ++it) {
-        const int ab = (int)(it & 1);
-        if (!tc::mbar_wait(&tempty[ab], (uint32_t)(((it >> 1) & 1) ^ 1), p.dev_err, abort_flag, false, lim)) break;
-        tc::tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(ab * L);
+        int ab = 0;
+        uint32_t d = tmem;
         for (int kb = 0; kb < p.nkb; ++kb, ++q) {
+          if (kb % HC_FLK == 0) {
+            ab = (int)(gch & 1);
+            if (!tc::mbar_wait(&tempty[ab], (uint32_t)(((gch >> 1) & 1) ^ 1), p.dev_err, abort_flag, false, lim)) {
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+            d = tmem + (uint32_t)(ab * L);
+          }
           const int s = (int)(q % S);
           if (!tc::mbar_wait(&conv[s], (uint32_t)((q / S) & 1), p.dev_err, abort_flag, false, lim)) {
             ok = false;
@@ -332,16 +347,18 @@ k_hpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const uint64_t x1 = tc::sdesc_sw128(sb + XOFF + (uint32_t)(g * NSX + 1) * XB, 16, 1024);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t acc = (kb > 0 || g > 0 || kk > 0) ? 1u : 0u;
+              const uint32_t acc = ((kb % HC_FLK) > 0 || g > 0 || kk > 0) ? 1u : 0u;
               tc::mma_f16(d, tc::sdesc_add(ah, kk * 32), tc::sdesc_add(x0, kk * 32), idesc, acc);
               if (NA == 2) tc::mma_f16(d, tc::sdesc_add(al, kk * 32), tc::sdesc_add(x0, kk * 32), idesc, 1u);
               if (NSX == 2) tc::mma_f16(d, tc::sdesc_add(ah, kk * 32), tc::sdesc_add(x1, kk * 32), idesc, 1u);
             }
           }
           tc::mma_commit(&empty[s]);
+          if (kb % HC_FLK == HC_FLK - 1 || kb == p.nkb - 1) {
+            tc::mma_commit(&tfull[ab]);
+            ++gch;
+          }
         }
-        if (!ok) break;
-        tc::mma_commit(&tfull[ab]);
       }
       tc::mma_commit(done);
     }
@@ -373,22 +390,33 @@ k_hpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // ------------------------------------------------------------ epilogue
     const int quad = warp & 3;
     const int row = 32 * quad + lane;
-    for (int64_t it = 0; it < my_pan; ++it) {
-      const int ab = (int)(it & 1);
-      if (!tc::mbar_wait(&tfull[ab], (uint32_t)((it >> 1) & 1), p.dev_err, abort_flag, false, lim)) break;
-      tc::tc_fence_after();
+    const int nch = (p.nkb + HC_FLK - 1) / HC_FLK;     // chunks per panel
+    int64_t gch = 0;
+    bool ok = true;
+    for (int64_t it = 0; ok && it < my_pan; ++it) {
       const int64_t grow = (blockIdx.x + it * gridDim.x) * 128 + row;
       float v[L];
 #pragma unroll
-      for (int c16 = 0; c16 < L; c16 += 16) {
-        uint32_t u[16];
-        tmem_ld32<16>(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(ab * L + c16), u);
+      for (int c = 0; c < L; ++c) v[c] = 0.f;
+      for (int ch = 0; ch < nch; ++ch, ++gch) {
+        const int ab = (int)(gch & 1);
+        if (!tc::mbar_wait(&tfull[ab], (uint32_t)((gch >> 1) & 1), p.dev_err, abort_flag, false, lim)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[c16 + q] = __uint_as_float(u[q]);
+        for (int c16 = 0; c16 < L; c16 += 16) {
+          uint32_t u[16];
+          tmem_ld32<16>(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(ab * L + c16), u);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[c16 + q] += __uint_as_float(u[q]);
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&tempty[ab]);   // the accumulator may be reused
       }
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&tempty[ab]);   // the accumulator may be reused
+      if (!ok) break;
 #pragma unroll
       for (int c = 0; c < L; ++c) {
         if (p.corr && c < p.l) v[c] -= __ldg(p.corr + c);
@@ -459,8 +487,16 @@ __global__ void k_xt_split(int64_t n, int l, int L, int64_t n64, const float* __
 
 // ---------------------------------------------------------------- T pass
 constexpr int TC_KSUB = 32;          // rows per stage
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 384;
 constexpr uint32_t TC_BOX = TC_KSUB * 128;   // one 32-row, 128-byte box
+// Sub-panels per accumulation chunk: the tensor cores' FP32 accumulation
+// loses about one unit in the last place of the running sum per MMA, with a
+// bias (it does not round to nearest), so a sum over ~1e5 rows drifts by a
+// few 1e-4.  Each chunk of TC_FL sub-panels (256 rows) is therefore
+// accumulated in tensor memory from zero and then added, rounding to
+// nearest, into FP32 sums in shared memory; the drift of one chunk is a few
+// 1e-6 and the chunk sums random-walk.
+constexpr int TC_FL = 8;
 
 struct TcParams {
   int64_t m, n;
@@ -486,40 +522,52 @@ struct TcParams {
 template <int SRC, int NT> struct TcGeom {
   static constexpr int NG = 2 * NT;
   static constexpr uint32_t RAW = SRC == SRC_F32 ? NG * 2 * TC_BOX                // 2 FP32 boxes per group
-                                  : SRC == SRC_BF16_SH ? NG * TC_BOX                // 1 BF16 box per group
-                                                       : NT * TC_BOX;               // 1 FP8 box per 2 groups
-  static constexpr bool INPLACE = SRC == SRC_F32;
+                                  : (SRC == SRC_BF16_SH || SRC == SRC_BF16) ? NG * TC_BOX   // 1 BF16 box
+                                                                           : NT * TC_BOX;   // FP8: 1 box / 2 groups
+  static constexpr bool INPLACE = SRC == SRC_F32 || SRC == SRC_BF16;
   static constexpr int NA = SrcInfo<SRC>::NA;
   static constexpr uint32_t OUT = INPLACE ? 0u : (uint32_t)NG * NA * TC_BOX;
-  // FP32 in place: group g at 2 g boxes, hi then lo; otherwise after RAW
+  // FP32 in place: group g at 2 g boxes, hi then lo; BF16: the raw boxes
+  // themselves; otherwise after RAW
   __device__ __forceinline__ static uint32_t hi(int g) {
-    return INPLACE ? (uint32_t)(2 * g) * TC_BOX : RAW + (uint32_t)(g * NA) * TC_BOX;
+    return SRC == SRC_BF16 ? (uint32_t)g * TC_BOX
+           : INPLACE       ? (uint32_t)(2 * g) * TC_BOX
+                           : RAW + (uint32_t)(g * NA) * TC_BOX;
   }
   __device__ __forceinline__ static uint32_t lo(int g) { return hi(g) + TC_BOX; }
   // distance between the hi tiles of groups 2t and 2t + 1 (the MMA's LBO)
-  static constexpr uint32_t LBO = (INPLACE ? 2 : NA) * TC_BOX;
-  // raw location of group g's data and, for FP8, which half of the box
+  static constexpr uint32_t LBO = (SRC == SRC_BF16 ? 1 : INPLACE ? 2 : NA) * TC_BOX;
+  // raw location of group g's data (FP8: half g & 1 of box g >> 1)
   __device__ __forceinline__ static uint32_t raw(int g) {
-    return SRC == SRC_F32 ? (uint32_t)(2 * g) * TC_BOX : SRC == SRC_BF16_SH ? (uint32_t)g * TC_BOX
-                                                                           : (uint32_t)(g >> 1) * TC_BOX;
+    return SRC == SRC_F32 ? (uint32_t)(2 * g) * TC_BOX
+           : (SRC == SRC_BF16_SH || SRC == SRC_BF16) ? (uint32_t)g * TC_BOX
+                                                     : (uint32_t)(g >> 1) * TC_BOX;
   }
 };
 
+// Roles (12 warps): warp 0 lane 0 TMA, warp 1 lane 0 MMA, warp 2 owns the
+// tensor memory, warps 4-7 convert (not for plain BF16), warps 8-11 drain
+// the accumulator chunks into the shared-memory sums and finally add those
+// to T.  NB accumulator buffers in tensor memory (2 when they fit).
 template <int SRC, int NT, typename TF, int NSY>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmY0,
             const __grid_constant__ CUtensorMap tmY1, const TcParams p) {
   using Geo = TcGeom<SRC, NT>;
   constexpr int NA = SrcInfo<SRC>::NA;
+  constexpr bool CONVERT = SRC != SRC_BF16;
   const uint32_t YOFF = Geo::RAW + Geo::OUT;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = p.nstages;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_bytes);
+  float* accs = reinterpret_cast<float*>(smem + (size_t)S * p.stage_bytes);   // [NT][npad][128]
+  uint64_t* full = reinterpret_cast<uint64_t*>(accs + (size_t)NT * p.npad * 128);
   uint64_t* conv = full + S;
   uint64_t* empty = conv + S;
-  uint64_t* done = empty + S;
+  uint64_t* cfull = empty + S;      // [2] chunk accumulated in buffer b
+  uint64_t* cempty = cfull + 2;     // [2] buffer b drained
+  uint64_t* done = cempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -530,7 +578,10 @@ k_tpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if (group >= p.ngroup) return;
   const int64_t nsub = (p.m + TC_KSUB - 1) / TC_KSUB;
   const int64_t my_subs = (nsub > group) ? (nsub - group + p.ngroup - 1) / p.ngroup : 0;
-  const int ncols = NT * p.npad;
+  const int64_t nchunks = (my_subs + TC_FL - 1) / TC_FL;
+  const int acc_cols = NT * p.npad;
+  const int NB = 2 * acc_cols <= 512 ? 2 : 1;
+  const int ncols = NB * acc_cols;
   const uint32_t tmem_cols = ncols <= 32 ? 32 : ncols <= 64 ? 64 : ncols <= 128 ? 128 : ncols <= 256 ? 256 : 512;
   const uint32_t TX = Geo::RAW + (uint32_t)(NSY * p.nyb) * TC_BOX;
   const int32_t col0 = slab * NT * 128;
@@ -541,6 +592,10 @@ k_tpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       tc::mbar_init(&conv[s], 4);
       tc::mbar_init(&empty[s], 1);
     }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&cfull[b], 1);
+      tc::mbar_init(&cempty[b], 4);
+    }
     tc::mbar_init(done, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -548,6 +603,8 @@ k_tpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     tc::tma_prefetch(&tmY0);
     if (NSY == 2) tc::tma_prefetch(&tmY1);
   }
+  if (warp >= 8)
+    for (int e = tid - 256; e < acc_cols * 128; e += 128) accs[e] = 0.f;
   if (warp == 2) {
     tc::tmem_alloc(tmem_slot, tmem_cols);
     tc::tmem_relinquish();
@@ -570,11 +627,14 @@ k_tpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       const int32_t r0 = (int32_t)((group + it * p.ngroup) * TC_KSUB);
       tc::mbar_arrive_expect_tx(&full[s], TX);
       if constexpr (SRC == SRC_F32) {
-        for (int b = 0; b < 4 * NT; ++b) tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 32 * b, r0, pol);
-      } else if constexpr (SRC == SRC_BF16_SH) {
-        for (int b = 0; b < 2 * NT; ++b) tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 64 * b, r0, pol);
+        for (int b = 0; b < 4 * NT; ++b)
+          tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 32 * b, r0, pol);
+      } else if constexpr (SRC == SRC_BF16_SH || SRC == SRC_BF16) {
+        for (int b = 0; b < 2 * NT; ++b)
+          tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 64 * b, r0, pol);
       } else {
-        for (int b = 0; b < NT; ++b) tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 128 * b, r0, pol);
+        for (int b = 0; b < NT; ++b)
+          tc::tma_load_2d_hint(st + (uint32_t)b * TC_BOX, &tmA, &full[s], col0 + 128 * b, r0, pol);
       }
       for (int b = 0; b < p.nyb; ++b) {
         tc::tma_load_2d(st + YOFF + (uint32_t)b * TC_BOX, &tmY0, &full[s], 64 * b, r0);
@@ -590,8 +650,14 @@ k_tpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // -------------------------------------------------------------- MMA
     const uint32_t idesc = tc::idesc_make(1u, 1u, 1u, 128u, (uint32_t)p.npad);
     for (int64_t it = 0; it < my_subs; ++it) {
+      const int64_t ch = it / TC_FL;
+      const int b = (int)(ch % NB);
+      const bool first = (it % TC_FL) == 0;
+      if (first && !tc::mbar_wait(&cempty[b], (uint32_t)(((ch / NB) & 1) ^ 1), p.dev_err, abort_flag, false, lim))
+        break;
       const int s = (int)(it % S);
-      if (!tc::mbar_wait(&conv[s], (uint32_t)((it / S) & 1), p.dev_err, abort_flag, false, lim)) break;
+      uint64_t* ready = CONVERT ? &conv[s] : &full[s];
+      if (!tc::mbar_wait(ready, (uint32_t)((it / S) & 1), p.dev_err, abort_flag, false, lim)) break;
       tc::tc_fence_after();
       const uint32_t sb = tc::smem_u32(smem + (size_t)s * p.stage_bytes);
 #pragma unroll
@@ -600,74 +666,87 @@ k_tpass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint64_t al = tc::sdesc_sw128(sb + Geo::lo(2 * t), Geo::LBO, 1024);
         const uint64_t y0 = tc::sdesc_sw128(sb + YOFF, TC_BOX, 1024);
         const uint64_t y1 = tc::sdesc_sw128(sb + YOFF + (uint32_t)p.nyb * TC_BOX, TC_BOX, 1024);
-        const uint32_t d = tmem + (uint32_t)(t * p.npad);
+        const uint32_t d = tmem + (uint32_t)(b * acc_cols + t * p.npad);
 #pragma unroll
         for (int kk = 0; kk < TC_KSUB / 16; ++kk) {
-          const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+          const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
           tc::mma_f16(d, tc::sdesc_add(ah, kk * 2048), tc::sdesc_add(y0, kk * 2048), idesc, acc);
           if (NA == 2) tc::mma_f16(d, tc::sdesc_add(al, kk * 2048), tc::sdesc_add(y0, kk * 2048), idesc, 1u);
           if (NSY == 2) tc::mma_f16(d, tc::sdesc_add(ah, kk * 2048), tc::sdesc_add(y1, kk * 2048), idesc, 1u);
         }
       }
       tc::mma_commit(&empty[s]);
+      if ((it % TC_FL) == TC_FL - 1 || it == my_subs - 1) tc::mma_commit(&cfull[b]);
     }
     tc::mma_commit(done);
-  } else if (warp >= 4) {
+  } else if (warp >= 4 && warp < 8) {
     // --------------------------------------------------------- converters
-    const int e = tid - 128;
-    const int r = e & (TC_KSUB - 1), g = e / TC_KSUB;     // row and 64-column group
-    const bool mine = g < Geo::NG;
-    for (int64_t it = 0; it < my_subs; ++it) {
-      const int s = (int)(it % S);
-      if (!tc::mbar_wait(&full[s], (uint32_t)((it / S) & 1), p.dev_err, abort_flag, false, lim)) break;
-      unsigned char* st = smem + (size_t)s * p.stage_bytes;
-      if (mine) {
-        const int64_t cg = (int64_t)col0 + 64 * g;
-        convert_row<SRC>(st + Geo::raw(g), TC_KSUB, g & 1, st + Geo::hi(g), st + Geo::lo(g), r,
-                         p.scale ? p.scale + cg : nullptr, p.shift ? p.shift + cg : nullptr,
-                         (int)(p.n - cg < 0 ? 0 : (p.n - cg > 64 ? 64 : p.n - cg)));
+    if (CONVERT) {
+      const int e = tid - 128;
+      const int r = e & (TC_KSUB - 1), g = e / TC_KSUB;     // row and 64-column group
+      const bool mine = g < Geo::NG;
+      for (int64_t it = 0; it < my_subs; ++it) {
+        const int s = (int)(it % S);
+        if (!tc::mbar_wait(&full[s], (uint32_t)((it / S) & 1), p.dev_err, abort_flag, false, lim)) break;
+        unsigned char* st = smem + (size_t)s * p.stage_bytes;
+        if (mine) {
+          const int64_t cg = (int64_t)col0 + 64 * g;
+          if constexpr (SRC != SRC_BF16)
+            convert_row<SRC>(st + Geo::raw(g), TC_KSUB, g & 1, st + Geo::hi(g), st + Geo::lo(g), r,
+                             p.scale ? p.scale + cg : nullptr, p.shift ? p.shift + cg : nullptr,
+                             (int)(p.n - cg < 0 ? 0 : (p.n - cg > 64 ? 64 : p.n - cg)));
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&conv[s]);
       }
-      tc::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&conv[s]);
     }
-  }
-  __syncwarp();
-  // ---------------------------------------------------------------- epilogue
-  bool ok = false;
-  if (warp < 4) {
-    ok = (my_subs == 0) ? false : tc::mbar_wait(done, 0, p.dev_err, abort_flag, false, lim);
-    ok = __all_sync(0xffffffffu, ok);
-    tc::tc_fence_after();
-  }
-  if (warp < 4 && ok) {
-    TF* T = static_cast<TF*>(p.T);
+  } else if (warp >= 8) {
+    // ------------------------------------ chunk drains, then the output
+    const int quad = warp & 3;
+    const int row = 32 * quad + lane;             // accumulator lane = slab column
+    bool ok = true;
+    for (int64_t ch = 0; ch < nchunks; ++ch) {
+      const int b = (int)(ch % NB);
+      if (!tc::mbar_wait(&cfull[b], (uint32_t)((ch / NB) & 1), p.dev_err, abort_flag, false, lim)) {
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      for (int t = 0; t < NT; ++t)
+        for (int c16 = 0; c16 < p.npad; c16 += 16) {
+          uint32_t u[16];
+          tmem_ld32<16>(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * acc_cols + t * p.npad + c16), u);
+          float* a = accs + ((size_t)(t * p.npad + c16) * 128 + row);
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int64_t row = (int64_t)col0 + t * 128 + warp * 32 + lane;   // row of T = column of A
-      const float rs = (p.rowscale && row < p.n) ? p.rowscale[row] : 1.f;
-      for (int c16 = 0; c16 < p.npad; c16 += 16) {
-        uint32_t u[16];
-        tmem_ld32<16>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * p.npad + c16), u);
-        if (row < p.n) {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int c = c16 + q;
-            const float v = __uint_as_float(u[q]) * rs;
-            if (p.qblk > 0) {
-              if ((c & 63) < p.qblk && (c >> 6) * p.qblk + (c & 63) < p.p)
-                atomicAdd(&T[row * p.ldt + (c >> 6) * p.qblk + (c & 63)], (TF)v);
-            } else if (c < p.p) {
-              atomicAdd(&T[row * p.ldt + c], (TF)v);
-            }
+          for (int q = 0; q < 16; ++q) a[(size_t)q * 128] += __uint_as_float(u[q]);
+        }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&cempty[b]);
+    }
+    if (ok && my_subs > 0) {
+      TF* T = static_cast<TF*>(p.T);
+      for (int t = 0; t < NT; ++t) {
+        const int64_t trow = (int64_t)col0 + t * 128 + row;     // row of T = column of A
+        if (trow >= p.n) continue;
+        const float rs = p.rowscale ? p.rowscale[trow] : 1.f;
+        for (int c = 0; c < p.npad; ++c) {
+          const float v = accs[(size_t)(t * p.npad + c) * 128 + row] * rs;
+          if (p.qblk > 0) {
+            if ((c & 63) < p.qblk && (c >> 6) * p.qblk + (c & 63) < p.p)
+              atomicAdd(&T[trow * p.ldt + (c >> 6) * p.qblk + (c & 63)], (TF)v);
+          } else if (c < p.p) {
+            atomicAdd(&T[trow * p.ldt + c], (TF)v);
           }
         }
       }
     }
   }
+  __syncwarp();
   if (warp == 1 && lane == 0) {
     volatile int never = 0;
-    tc::mbar_wait(done, 0, nullptr, &never);
+    tc::mbar_wait(done, 0, nullptr, &never);       // every MMA has completed
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -685,7 +764,7 @@ __global__ void k_split_planes(int64_t m, int w, int wq, const float* __restrict
   const float v = c < w ? Q[r * ldq + c] : 0.f;
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   hi[e] = h;
-  lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  if (lo) lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
 template <typename K>
@@ -697,9 +776,10 @@ constexpr size_t CVT_SMEM_LIMIT = 227 * 1024;
 
 CUtensorMapDataType a_tmap_type(int src) {
   return src == SRC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                        : src == SRC_BF16_SH ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+         : (src == SRC_BF16_SH || src == SRC_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT8;
 }
-size_t a_elem(int src) { return src == SRC_F32 ? 4 : src == SRC_BF16_SH ? 2 : 1; }
+size_t a_elem(int src) { return src == SRC_F32 ? 4 : (src == SRC_BF16_SH || src == SRC_BF16) ? 2 : 1; }
 
 template <int SRC, int L, int NSX>
 bool launch_hpass(const PassArgs& a, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t n64,
@@ -749,9 +829,11 @@ bool launch_hpass(const PassArgs& a, const __nv_bfloat16* Xh, const __nv_bfloat1
 template <int SRC, int NSY>
 bool launch_tpass(const PassArgs& a, const __nv_bfloat16* Y, int64_t ldy, int64_t plane, int nyb, int npad, int qblk,
                   bool f_f64, cudaStream_t st, uint32_t* dev_err, const WaitTest& wt) {
-  const int NT = (2 * npad <= 512) ? 2 : 1;
+  // two slabs per CTA when two tensor-memory buffers of both still fit and
+  // the shared-memory sums stay small; else one slab
+  const int NT = (npad <= 64) ? 2 : 1;
   CUtensorMap tmA, tmY0, tmY1;
-  const uint32_t abox_cols = SRC == SRC_F32 ? 32 : SRC == SRC_BF16_SH ? 64 : 128;
+  const uint32_t abox_cols = SRC == SRC_F32 ? 32 : (SRC == SRC_BF16_SH || SRC == SRC_BF16) ? 64 : 128;
   if (!make_tmap_2d(&tmA, a.A, a_tmap_type(SRC), a_elem(SRC), a.m, a.n, a.lda, TC_KSUB, abox_cols)) return false;
   if (!make_tmap_2d(&tmY0, Y, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.m, ldy, ldy, TC_KSUB, 64)) return false;
   if (!make_tmap_2d(&tmY1, NSY == 2 ? Y + plane : Y, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.m, ldy, ldy, TC_KSUB, 64))
@@ -765,8 +847,9 @@ bool launch_tpass(const PassArgs& a, const __nv_bfloat16* Y, int64_t ldy, int64_
   p.qblk = qblk;
   const uint32_t raw_out = NT == 2 ? TcGeom<SRC, 2>::RAW + TcGeom<SRC, 2>::OUT : TcGeom<SRC, 1>::RAW + TcGeom<SRC, 1>::OUT;
   p.stage_bytes = (uint32_t)round_up(raw_out + (uint32_t)(NSY * nyb) * TC_BOX, 1024);
-  p.nstages = (int)std::min<size_t>(8, (CVT_SMEM_LIMIT - 2048) / p.stage_bytes);
-  if (p.nstages < 2) return false;
+  const size_t acc_bytes = (size_t)NT * npad * 128 * sizeof(float);
+  if (acc_bytes + 2048 + 2 * (size_t)p.stage_bytes > CVT_SMEM_LIMIT) return false;
+  p.nstages = (int)std::min<size_t>(8, (CVT_SMEM_LIMIT - 2048 - acc_bytes) / p.stage_bytes);
   p.nslab = (int)cdiv(a.n, NT * 128);
   const int sms = num_sms();
   p.ngroup = std::max(1, std::min<int>((int)cdiv(a.m, TC_KSUB), sms / p.nslab));
@@ -778,7 +861,7 @@ bool launch_tpass(const PassArgs& a, const __nv_bfloat16* Y, int64_t ldy, int64_
   p.dev_err = dev_err;
   p.wait_ns = wt.limit_ns;
   p.withhold = wt.withhold;
-  const size_t smem = 1024 + (size_t)p.nstages * p.stage_bytes + 256;
+  const size_t smem = 1024 + (size_t)p.nstages * p.stage_bytes + acc_bytes + 256;
   dim3 grid(p.nslab * p.ngroup);
   if (f_f64) {
     auto kern = NT == 2 ? k_tpass_cvt<SRC, 2, double, NSY> : k_tpass_cvt<SRC, 1, double, NSY>;
@@ -866,16 +949,48 @@ bool pass_cvt_src(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   return launch_tpass<SRC, 2>(a, H16, 64, (int64_t)a.m * 64, 1, L, 0, false, st, dev_err, none);
 }
 
+// T pass over BF16 A as stored (no conversion), Q in one BF16 slice: the
+// sliced QR's first slice, or Q (FP32) rounded here.
+bool tpass_bf16_chunked(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
+  const __nv_bfloat16* Y;
+  int64_t ldy;
+  int qblk;
+  if (a.q16) {
+    Y = static_cast<const __nv_bfloat16*>(a.q16);
+    ldy = a.q16_ld;
+    qblk = a.q_blk;
+  } else {
+    const int wq = (int)round_up(a.p, 64);
+    if (wq > 256 || (size_t)a.m * wq * 2 > a.work_bytes) return false;
+    __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(a.work);
+    const int64_t cnt = a.m * wq;
+    k_split_planes<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(a.m, a.p, wq, static_cast<const float*>(a.H), a.ldh, hi,
+                                                            nullptr);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    Y = hi;
+    ldy = wq;
+    qblk = 0;
+  }
+  const int nyb = (int)(ldy / 64);
+  const int npad = qblk > 0 ? (int)ldy : (int)round_up(a.p, 16);
+  if (npad > 256) return false;
+  const size_t fes = a.f_f64 ? 8 : 4;
+  if (!a.accumulate_f) RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * fes, 0, a.p * fes, a.n, st));
+  return launch_tpass<SRC_BF16, 1>(a, Y, ldy, 0, nyb, npad, qblk, a.f_f64, st, dev_err, take_wait_test(1));
+}
+
 }  // namespace
 
 // Whether the converting tensor-core kernels take this pass (see the top of
 // the file), and the pass itself.
 bool pass_cvt(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
-  if (a.dtype != RPCA_F32) return false;
   if (a.mode != MODE_T && a.mode != MODE_H && a.mode != MODE_FUSED) return false;
   if (!a.work) return false;
   if (a.ones_col >= 0 && a.ones_col != a.p) return false;
-  return pass_cvt_src<SRC_F32>(a, st, dev_err);
+  if (a.dtype == RPCA_F32) return pass_cvt_src<SRC_F32>(a, st, dev_err);
+  if (a.dtype == RPCA_BF16 && a.mode == MODE_T && !a.shift && !a.scale) return tpass_bf16_chunked(a, st, dev_err);
+  return false;
 }
 
 }  // namespace rpca

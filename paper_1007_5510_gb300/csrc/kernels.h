@@ -152,10 +152,21 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
 void gemm64_small(int M, int N, int K, double alpha, const double* A, int64_t lda, bool ta, const double* B,
                   int64_t ldb, bool tb, double beta, const double* D, int64_t ldd, double* C, int64_t ldc,
                   cudaStream_t st);
-// `steps` FP64 refinement steps of the eigenvectors X (w x w) of B^T B
-// (k_small64.cu); Xn, P, S, E: w x w scratch.
+// `steps` FP64 refinement steps of the eigenvectors X (w x w) of B^T B, or
+// of B itself when gram_given (B = a symmetric Gram G) (k_small64.cu); Xn,
+// P, S, E: w x w scratch.  On return S holds X^T M X of the last step's
+// input only when steps > 0.
 void refine_eigvecs64(int w, const double* B, double* X, double* Xn, double* P, double* S, double* E, int steps,
-                      cudaStream_t st);
+                      cudaStream_t st, bool gram_given = false);
+// B (upper triangular FP64 container) with B^T B = G + 1e-6 max diag(G) I,
+// FP32 Cholesky (a preconditioner only; w <= 224).
+void chol32_shift(int w, const double* G, double* B, cudaStream_t st);
+// sigma_j = sqrt(S_jj) sorted descending, W = X reordered, Vs = W Sigma^-1.
+void eig_finish(int w, const double* Sm, const double* X, double* S, double* Vs, double* W, cudaStream_t st);
+// Step 4 from the Gram of T (FP32-class paths): S, W (right singular
+// vectors of T) and Vs = W Sigma^-1 with V = T Vs; work: 6 w^2 doubles.
+void svd_from_gram(int w, const double* G, double* S, double* Vs, double* W, double* work, uint32_t* dev_err,
+                   cudaStream_t st);
 
 // ------------------------------------------- tensor-core tall products
 // FP32-accurate (TF32 x3) products on FP32 data carried with a remainder

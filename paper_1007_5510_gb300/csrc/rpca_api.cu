@@ -421,6 +421,10 @@ size_t tc_work_bytes(rpca_dtype dt, int64_t m, int64_t n, int w) {
   return b + 4096;
 }
 
+// Step 4 from the Gram of T (FP32-class storage; the single-CTA Cholesky
+// preconditioner takes w <= 192), else from a QR of T.
+bool gram_step4(const rpca_ctx* c) { return !c->f64 && c->w <= 192 && !c->adjoint && c->reorth; }
+
 // Will the T pass of an FP32 context read the first two BF16 slices of the
 // sliced Q directly (converter kernel; TMA-aligned A)?
 bool tpass_f32_slices_ok(const rpca_ctx* c, const rpca_matrix* Am) {
@@ -634,10 +638,25 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   c->tic(c->i + 2);
   run_pass(c, Am, a);
   c->toc(c->i + 2);
+  const bool q_in_h = !(c->sliced && (t16 || t32s) && !c->adjoint);   // Q also in H (FP32)
+  if (gram_step4(c)) {
+    // T = A~^T Q - d (1^T Q), kept in FP64 for the Gram of Step 4; the
+    // first-order orthonormalisation (I - E/2) is applied to that Gram and
+    // to the small factor instead of to T
+    if (c->centered) {
+      if (q_in_h) col_sums(f64, c->m, c->w, c->H.ptr, c->w, c->q1.as<double>(), st);
+      else col_sums_slices(c->m, c->hs_rows, c->i + 1, c->l, c->Hs.ptr, c->q1.as<double>(), st);
+      rank1_sub(true, c->n, c->w, 1.0, c->d.as<double>(), c->q1.as<double>(), c->T64.ptr, c->w, st);
+    }
+    copy_matrix(true, f64, c->n, c->w, c->T64.ptr, c->w, c->T.ptr, c->w, st);
+    c->next_pass = c->i + 2;
+    return RPCA_OK;
+  }
   copy_matrix(true, f64, c->n, c->w, c->T64.ptr, c->w, c->T.ptr, c->w, st);
   if (c->centered) {
     // T = A~^T Q - d (1^T Q)
-    col_sums(f64, c->m, c->w, c->H.ptr, c->w, c->q1.as<double>(), st);
+    if (q_in_h) col_sums(f64, c->m, c->w, c->H.ptr, c->w, c->q1.as<double>(), st);
+    else col_sums_slices(c->m, c->hs_rows, c->i + 1, c->l, c->Hs.ptr, c->q1.as<double>(), st);
     rank1_sub(f64, c->n, c->w, 1.0, c->d.as<double>(), c->q1.as<double>(), c->T.ptr, c->w, st);
   }
   // T <- T (I - E/2): the Rayleigh-Ritz matrix of the orthonormalised basis
@@ -656,16 +675,28 @@ void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, in
   // Step 4: T = Q_T R_T; with E_T = Q_T^T Q_T - I, T = (Q_T (I - E_T/2))
   // ((I + E_T/2) R_T) to first order; R_T' = Ub S W^T  =>  V~ = Q_T (I - E_T/2) Ub
   const int w = c->w, k = c->k;
+  const bool g4 = gram_step4(c);
   c->tic(c->i + 3);
-  svd_of_T(f64, c->n, c->i + 1, c->l, c->k, c->T.ptr, c->Tc.ptr, c->Tlo.as<float>(), c->ET, c->RT, c->RT2, c->S, c->Ub,
-           c->W, c->svdwork, c->qs, c->dev_err(), st);
+  if (g4) {
+    // Step 4 from G = T^T T (FP64): G' = (I - E/2) G (I - E/2) is the Gram
+    // of the Rayleigh-Ritz matrix of the orthonormalised basis; its
+    // eigenvectors W are T's right singular vectors and V = T (I - E/2) W / sigma
+    gram(true, c->n, w, w, c->T64.ptr, w, c->T64.ptr, w, c->RT, w, false, st);
+    gemm64_small(w, w, w, -0.5, c->E, w, false, c->RT, w, false, 1.0, c->RT, w, c->RT2, w, st);
+    gemm64_small(w, w, w, -0.5, c->RT2, w, false, c->E, w, false, 1.0, c->RT2, w, c->RT, w, st);
+    svd_from_gram(w, c->RT, c->S, c->Ub, c->W, c->svdwork, c->dev_err(), st);
+  } else {
+    svd_of_T(f64, c->n, c->i + 1, c->l, c->k, c->T.ptr, c->Tc.ptr, c->Tlo.as<float>(), c->ET, c->RT, c->RT2, c->S,
+             c->Ub, c->W, c->svdwork, c->qs, c->dev_err(), st);
+  }
   c->toc(c->i + 3);
   c->tic(c->i + 4);
-  // Steps 5-6: U = Q (I - E/2) W[:, :k], V = Q_T (I - E_T/2) Ub[:, :k]
+  // Steps 5-6: U = Q (I - E/2) W[:, :k], V = Q_T (I - E_T/2) Ub[:, :k] (QR
+  // form) or V = T (I - E/2) Ub[:, :k] with Ub = W / sigma (Gram form)
   // (working orientation; swapped back when the problem was transposed)
-  fold_fixup(f64, w, k, c->ET, c->Ub, c->MV, st);
+  fold_fixup(f64, w, k, g4 ? c->E : c->ET, c->Ub, c->MV, st);
   fold_fixup(f64, w, k, c->E, c->W, c->MU, st);
-  const bool tlo = c->Tlo.ptr && c->n >= kTcMinRows;
+  const bool tlo = !g4 && c->Tlo.ptr && c->n >= kTcMinRows;
   const bool hlo = c->Hlo.ptr && c->m >= kTcMinRows;
   qr_apply(f64, c->n, w, k, c->T.ptr, tlo ? c->Tlo.as<float>() : nullptr, w, c->MV, k, 1.0, 0.0, c->outV.ptr,
            nullptr, k, c->qs, st, c->dev_err());
@@ -754,7 +785,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->outU.alloc((size_t)c->m * c->k * es);
   c->outV.alloc((size_t)c->n * c->k * es);
   const size_t w = c->w, l = c->l;
-  const size_t small_doubles = w * l + 4 * l * l + w * w * 4 + w + 4 * w * w + 3 * w * w + 2 * w * c->k;
+  const size_t small_doubles = w * l + 4 * l * l + w * w * 4 + w + 5 * w * w + 3 * w * w + 2 * w * c->k;
   const size_t qf_words = (size_t)kQfWords * (c->i + 1);   // the most blocks any QR here has
   c->small.alloc(small_doubles * sizeof(double) + qf_words * sizeof(uint32_t));
   double* s = c->small.as<double>();
@@ -767,7 +798,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->Ub = s; s += w * w;
   c->W = s; s += w * w;
   c->S = s; s += w;
-  c->svdwork = s; s += 5 * w * w;
+  c->svdwork = s; s += 6 * w * w;
   c->E = s; s += w * w;
   c->ET = s; s += w * w;
   c->RT2 = s; s += w * w;
