@@ -1138,8 +1138,10 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
 // reorthogonalised Krylov blocks T is well conditioned (its singular values
 // are those of A on the Krylov space), so forming G loses nothing the
 // tolerances can see.
-constexpr double kGramJacobiTol = 1e-4;
-constexpr int kGramRefineSteps = 3;
+// The FP32 sweeps run to FP32 convergence: near the edge of a cluster of
+// singular values a loose sweep tolerance leaves vector errors of
+// tolerance / relative gap, outside the refinement's quadratic basin.
+constexpr int kGramRefineSteps = 2;
 
 void svd_from_gram(int w, const double* G, double* S, double* Vs, double* W, double* work, uint32_t* dev_err,
                    cudaStream_t st) {
@@ -1151,6 +1153,7 @@ void svd_from_gram(int w, const double* G, double* S, double* Vs, double* W, dou
   double* P = work + 4 * ww;
   double* Sm = work + 5 * ww;
   double* E = B;                                   // B is free once the sweeps are done
+  const double kGramJacobiTol = 4.0 * std::sqrt((double)w) * 5.96e-8;
   chol32_shift(w, G, B, st);
   if (getenv("RPCA_JACOBI_SINGLE") || !jacobi_cluster_f32(w, B, Jc32, kGramJacobiTol, 40, dev_err, st)) {
     const size_t mat = ww * sizeof(float);

@@ -492,11 +492,11 @@ constexpr uint32_t TC_BOX = TC_KSUB * 128;   // one 32-row, 128-byte box
 // Sub-panels per accumulation chunk: the tensor cores' FP32 accumulation
 // loses about one unit in the last place of the running sum per MMA, with a
 // bias (it does not round to nearest), so a sum over ~1e5 rows drifts by a
-// few 1e-4.  Each chunk of TC_FL sub-panels (256 rows) is therefore
+// few 1e-4.  Each chunk of TC_FL sub-panels (512 rows) is therefore
 // accumulated in tensor memory from zero and then added, rounding to
 // nearest, into FP32 sums in shared memory; the drift of one chunk is a few
 // 1e-6 and the chunk sums random-walk.
-constexpr int TC_FL = 8;
+constexpr int TC_FL = 16;
 
 struct TcParams {
   int64_t m, n;

@@ -267,8 +267,7 @@ static bool tpass_bf16(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
 
 bool launch_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   if (a.dtype == RPCA_F32) return pass_cvt(a, st, dev_err);
-  // BF16 T pass: the chunked-accumulation kernel (k_stream_cvt.cu) first
-  if (a.mode == MODE_T) return pass_cvt(a, st, dev_err) || tpass_bf16(a, st, dev_err);
+  if (a.mode == MODE_T) return tpass_bf16(a, st, dev_err);
   return fused_pass_tc(a, st, dev_err);
 }
 

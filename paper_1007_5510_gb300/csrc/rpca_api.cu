@@ -276,6 +276,78 @@ static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, vo
   if (fp32_out) unslice_blocks(m, prow, nblk, l, S, H, ld, st);
 }
 
+// Step 2 on H held in three exact BF16 slices as ONE Cholesky QR of all
+// w = nblk l columns: the FP64 Gram G = H^T H (upper block triangle from
+// the slices), the FP64 Cholesky G = R^T R by l x l blocks (k_chol on the
+// diagonal blocks, FP64 products for the rest), then Q = H R^-1 block column
+// by block column, the last first, in place.  With the block Lanczos form of
+// Step 1 the columns of H are far from dependent (kappa(H) is that of A on
+// the Krylov space), so one pass leaves Q^T Q - I at the rounding of the
+// apply, which the first-order correction with the measured E_out absorbs.
+// The factorisation is checked before H is touched: when a diagonal block
+// needed a shifted Cholesky (numerical rank loss) this returns false with H
+// unchanged, and the block path with its shifted passes runs instead.  The
+// check reads one word on the host, so this path is not used while the
+// stream is being captured.
+static bool block_qr_sliced_whole(int64_t m, int nblk, int l, float* H, int64_t ld, void* S, int64_t prow,
+                                  double* E_out, bool fp32_out, const QrScratch& s, double* G, double* R,
+                                  double* Rinv, double* tmp, uint32_t* dev_err, cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RPCA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return false;
+  const int lds = nblk * 64, w = nblk * l;
+  const double piv_rel = 1e-5, shift_rel = 1e-5;
+  auto need = [](bool ok) {
+    if (!ok) throw Invalid("sliced tensor-core QR: unsupported shape");
+  };
+  slice_blocks(m, prow, nblk, l, H, ld, S, st);
+  need(gram_slices(m, prow, S, lds, 0, lds, 0, lds, s.Cfull, lds, st, dev_err, nullptr, true));
+  compact_sq(nblk, l, s.Cfull, lds, G, st);
+  RPCA_CUDA_TRY(cudaMemsetAsync(R, 0, (size_t)w * w * sizeof(double), st));
+  RPCA_CUDA_TRY(cudaMemsetAsync(Rinv, 0, (size_t)w * w * sizeof(double), st));
+  auto blk = [&](double* M, int b, int c) { return M + (size_t)b * l * w + (size_t)c * l; };
+  for (int b = 0; b < nblk; ++b) {
+    // G_bb - sum_{a<b} R_ab^T R_ab, factored; R_bc = R_bb^-T (G_bc - sum_{a<b} R_ab^T R_ac)
+    copy_matrix(true, true, l, l, blk(G, b, b), w, s.Gm, l, st);
+    for (int a = 0; a < b; ++a)
+      gemm64_small(l, l, l, -1.0, blk(R, a, b), w, true, blk(R, a, b), w, false, 1.0, s.Gm, l, s.Gm, l, st);
+    chol_small(l, s.Gm, l, s.Rk, s.Rinv, 0, piv_rel, shift_rel, s.qf + kQfWords * b, dev_err, st, false);
+    copy_matrix(true, true, l, l, s.Rk, l, blk(R, b, b), w, st);
+    copy_matrix(true, true, l, l, s.Rinv, l, blk(Rinv, b, b), w, st);
+    for (int c = b + 1; c < nblk; ++c) {
+      copy_matrix(true, true, l, l, blk(G, b, c), w, tmp, l, st);
+      for (int a = 0; a < b; ++a)
+        gemm64_small(l, l, l, -1.0, blk(R, a, b), w, true, blk(R, a, c), w, false, 1.0, tmp, l, tmp, l, st);
+      gemm64_small(l, l, l, 1.0, s.Rinv, l, true, tmp, l, false, 0.0, nullptr, 0, blk(R, b, c), w, st);
+    }
+  }
+  // any shifted diagonal block: leave H to the block path
+  std::vector<uint32_t> qf((size_t)kQfWords * nblk);
+  RPCA_CUDA_TRY(cudaMemcpyAsync(qf.data(), s.qf, qf.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int b = 0; b < nblk; ++b)
+    if (qf[(size_t)kQfWords * b + 1]) return false;
+  // R^-1 (upper): Rinv_bc = -R_bb^-1 sum_{b<a<=c} R_ba Rinv_ac, from the diagonal outwards
+  for (int c = 1; c < nblk; ++c)
+    for (int b = c - 1; b >= 0; --b) {
+      RPCA_CUDA_TRY(cudaMemsetAsync(tmp, 0, (size_t)l * l * sizeof(double), st));
+      for (int a = b + 1; a <= c; ++a)
+        gemm64_small(l, l, l, 1.0, blk(R, b, a), w, false, blk(Rinv, a, c), w, false, 1.0, tmp, l, tmp, l, st);
+      gemm64_small(l, l, l, -1.0, blk(Rinv, b, b), w, false, tmp, l, false, 0.0, nullptr, 0, blk(Rinv, b, c), w, st);
+    }
+  // Q_j = sum_{b<=j} H_b Rinv_bj, last block first (each reads the blocks at or before it)
+  for (int j = nblk - 1; j >= 0; --j)
+    need(apply_slices(m, prow, S, lds, 0, j + 1, 64 * j, Rinv + (size_t)j * l, (j + 1) * l, l, w, 1.0, l, false,
+                      true, nullptr, 0, 0, s.mt, st, dev_err, nullptr));
+  if (E_out) {
+    need(gram_slices(m, prow, S, lds, 0, lds, 0, lds, s.Cfull, lds, st, dev_err, nullptr, true));
+    compact_sq(nblk, l, s.Cfull, lds, E_out, st);
+    sub_identity(nblk * l, E_out, st);
+  }
+  if (fp32_out) unslice_blocks(m, prow, nblk, l, S, H, ld, st);
+  return true;
+}
+
 // Step 4 on T (n x w, ld w, compute type): T = Q_T R_T with Q_T from the
 // block QR (in place of T) and R_T = Q_T^T T_orig (FP64-accumulated Gram);
 // with E_T = Q_T^T Q_T - I the orthonormal basis is Q_T (I - E_T/2) to first
@@ -614,12 +686,21 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   const bool t16 = c->sliced && tpass_bf16_ok(c, Am);
   const bool t32s = tpass_f32_slices_ok(c, Am);
   c->tic(c->i + 1);
-  if (c->sliced)
-    block_qr_sliced(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows, c->E,
-                    !(t16 || t32s) || c->adjoint, c->qs, c->dev_err(), st);
-  else
+  const bool q32 = !(t16 || t32s) || c->adjoint;
+  if (c->sliced) {
+    // the whole-H Cholesky QR's scratch (G, R, R^-1, one block): Step 4's
+    // work area, free until then
+    const size_t ww = (size_t)c->w * c->w;
+    double* sw = c->svdwork;
+    if (!(c->reorth && block_qr_sliced_whole(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows,
+                                             c->E, q32, c->qs, sw, sw + 2 * ww, sw + ww, sw + 3 * ww, c->dev_err(),
+                                             st)))
+      block_qr_sliced(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows, c->E, q32, c->qs,
+                      c->dev_err(), st);
+  } else {
     block_qr(f64, c->m, c->i + 1, c->l, c->H.ptr, c->w, nullptr, c->E, c->qs, c->dev_err(), st,
              c->Hlo.as<float>());
+  }
   c->toc(c->i + 1);
   a.mode = MODE_T;
   a.p = c->w;
