@@ -268,6 +268,18 @@ rpca_status rpca_batch_run(rpca_batch* b, const rpca_matrix* A, void* const* U,
                            const int64_t* ldu, double* const* S, void* const* V,
                            const int64_t* ldv);
 
+/* The adjoint of rpca_backward for every problem of a batch whose problems
+ * were all created with RPCA_ADJOINT, after a completed rpca_batch_run:
+ * dA[p] (m_p x n_p, ldda[p], device) = sum_j dS[p][j] d sigma_j / dA for
+ * problem p, dS[p] its k FP64 values in device memory, A[p] the same
+ * matrices as in the run.  The problems' backward passes run concurrently
+ * on the batch's streams, ordered after the work queued on
+ * problems[0].stream; synchronises and reports the first failing problem
+ * (rpca_batch_last_error).  RPCA_EINVAL if a problem lacks RPCA_ADJOINT.
+ * (The paper has no gradient; see rpca_backward.) */
+rpca_status rpca_batch_backward(rpca_batch* b, const rpca_matrix* A, const double* const* dS, void* const* dA,
+                                const int64_t* ldda);
+
 /* Frees the batch (NULL is a no-op). */
 void rpca_batch_destroy(rpca_batch* b);
 

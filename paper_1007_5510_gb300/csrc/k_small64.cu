@@ -66,17 +66,20 @@ k_gemm64_small(int M, int N, int K, double alpha, const double* __restrict__ A, 
 }
 
 // One refinement step's correction E (w x w) from S = X^T M X and
-// Gx = X^T X (R = I - Gx), as derived at the top of this file.  One CTA.
+// Gx = X^T X (R = I - Gx), as derived at the top of this file.  First the
+// eigenvalue estimates lambda_i and the threshold delta (one CTA), then E
+// elementwise (many CTAs; E may alias Gx: each element is read, then
+// written, by the same thread).
 __global__ void __launch_bounds__(1024)
-k_refine_correction(int w, const double* __restrict__ S, const double* __restrict__ Gx, double* __restrict__ E) {
-  extern __shared__ double lam[];            // w values
+k_refine_stats(int w, const double* __restrict__ S, const double* __restrict__ Gx, double* __restrict__ lam_out) {
   __shared__ double red_s[32], red_r[32], lmax_s[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   double off_s = 0.0, off_r = 0.0, lmax = 0.0;
   for (int i = tid; i < w; i += blockDim.x) {
     const double g = Gx[(int64_t)i * w + i];
-    lam[i] = g > 0.0 ? S[(int64_t)i * w + i] / g : 0.0;     // S_ii / (1 - R_ii)
-    lmax = fmax(lmax, fabs(lam[i]));
+    const double lam = g > 0.0 ? S[(int64_t)i * w + i] / g : 0.0;     // S_ii / (1 - R_ii)
+    lam_out[i] = lam;
+    lmax = fmax(lmax, fabs(lam));
   }
   for (int e = tid; e < w * w; e += blockDim.x) {
     const int i = e / w, j = e % w;
@@ -105,31 +108,32 @@ k_refine_correction(int w, const double* __restrict__ S, const double* __restric
       b += __shfl_xor_sync(0xffffffffu, b, o);
       c = fmax(c, __shfl_xor_sync(0xffffffffu, c, o));
     }
-    if (lane == 0) {
-      red_s[0] = a;
-      red_r[0] = b;
-      lmax_s[0] = c;
-    }
-  }
-  __syncthreads();
-  // first-order terms are reliable only for gaps well above their size
-  const double delta = 2.0 * (sqrt(red_s[0]) + lmax_s[0] * sqrt(red_r[0]));
-  for (int e = tid; e < w * w; e += blockDim.x) {
-    const int i = e / w, j = e % w;
-    const double r = (i == j ? 1.0 : 0.0) - Gx[e];
-    double v;
-    if (i == j) {
-      v = 0.5 * r;
-    } else {
-      const double gap = lam[j] - lam[i];
-      v = fabs(gap) > delta ? (S[e] + lam[j] * r) / gap : 0.5 * r;
-    }
-    E[e] = v;
+    // first-order terms are reliable only for gaps well above their size
+    if (lane == 0) lam_out[w] = 2.0 * (sqrt(a) + c * sqrt(b));
   }
 }
 
+__global__ void k_refine_apply(int w, const double* __restrict__ S, const double* Gx,
+                               const double* __restrict__ lam, double* E) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= w * w) return;
+  const int i = e / w, j = e % w;
+  const double delta = lam[w];
+  const double r = (i == j ? 1.0 : 0.0) - Gx[e];
+  double v;
+  if (i == j) {
+    v = 0.5 * r;
+  } else {
+    const double gap = lam[j] - lam[i];
+    v = fabs(gap) > delta ? (S[e] + lam[j] * r) / gap : 0.5 * r;
+  }
+  E[e] = v;
+}
+
 // B (upper triangular, w x w, FP64 container) with B^T B = G + delta I to
-// FP32 accuracy: right-looking Cholesky in FP32 in shared memory, one CTA.
+// FP32 accuracy: right-looking Cholesky in FP32 in shared memory, one CTA
+// of 32 x 32 threads (thread (ty, tx) updates rows ty + 32 a, columns
+// tx + 32 b of the trailing matrix, no index division in the loop).
 // It only preconditions Step 4 (its output seeds the FP32 Jacobi sweeps,
 // whose vectors are then refined in FP64 against G itself), so a shift
 // delta = 1e-6 max diag(G) keeps it defined whatever G's conditioning: the
@@ -137,8 +141,8 @@ k_refine_correction(int w, const double* __restrict__ S, const double* __restric
 __global__ void __launch_bounds__(1024) k_chol32_shift(int w, const double* __restrict__ G, double* __restrict__ B) {
   extern __shared__ float cm[];                 // w x ws
   const int ws = w | 1;
-  __shared__ float dmax, piv;
-  const int tid = threadIdx.x;
+  __shared__ float dmax, rowk[256];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   if (tid == 0) dmax = 0.f;
   __syncthreads();
   for (int e = tid; e < w * w; e += blockDim.x) {
@@ -151,15 +155,18 @@ __global__ void __launch_bounds__(1024) k_chol32_shift(int w, const double* __re
   for (int i = tid; i < w; i += blockDim.x) cm[i * ws + i] += delta;
   __syncthreads();
   for (int k = 0; k < w; ++k) {
-    if (tid == 0) piv = sqrtf(fmaxf(cm[k * ws + k], delta));
+    // row k of R: r_kk = sqrt(c_kk), r_kj = c_kj / r_kk (kept in rowk)
+    const float d = sqrtf(fmaxf(cm[k * ws + k], delta));
+    for (int j = k + tid; j < w; j += blockDim.x) {
+      const float v = (j == k) ? d : cm[k * ws + j] / d;
+      rowk[j] = v;
+      cm[k * ws + j] = v;
+    }
     __syncthreads();
-    const float d = piv, inv = 1.f / piv;
-    for (int j = k + tid; j < w; j += blockDim.x) cm[k * ws + j] = (j == k) ? d : cm[k * ws + j] * inv;
-    __syncthreads();
-    const int r = w - k - 1;
-    for (int e = tid; e < r * r; e += blockDim.x) {
-      const int i = k + 1 + e / r, j = k + 1 + e % r;
-      if (j >= i) cm[i * ws + j] -= cm[k * ws + i] * cm[k * ws + j];
+    // trailing update c_ij -= r_ki r_kj for k < i <= j
+    for (int i = k + 1 + ty; i < w; i += 32) {
+      const float ri = rowk[i];
+      for (int j = i + tx; j < w; j += 32) cm[i * ws + j] -= ri * rowk[j];
     }
     __syncthreads();
   }
@@ -172,26 +179,32 @@ __global__ void __launch_bounds__(1024) k_chol32_shift(int w, const double* __re
 // Eigenvalues lambda_j = S_jj of the refined S = X^T G X, sorted
 // descending: sigma_j = sqrt(lambda_j) (S_out), W = X with its columns in
 // that order, and Vs = W diag(1/sigma) (the factor that takes T to its left
-// singular vectors, V = T W Sigma^-1).  One CTA.
+// singular vectors, V = T W Sigma^-1).  CTA c moves column c.
 __global__ void k_eig_finish(int w, const double* __restrict__ Sm, const double* __restrict__ X,
                              double* __restrict__ S_out, double* __restrict__ Vs, double* __restrict__ W) {
-  extern __shared__ double sig[];
-  int* pos = reinterpret_cast<int*>(sig + w);
-  for (int c = threadIdx.x; c < w; c += blockDim.x) sig[c] = sqrt(fmax(Sm[(int64_t)c * w + c], 0.0));
-  __syncthreads();
-  for (int c = threadIdx.x; c < w; c += blockDim.x) {
-    int rank = 0;
-    for (int o = 0; o < w; ++o) rank += (sig[o] > sig[c]) || (sig[o] == sig[c] && o < c);
-    pos[c] = rank;
+  const int c = blockIdx.x;
+  __shared__ int rank;
+  __shared__ double sc;
+  if (threadIdx.x == 0) {
+    rank = 0;
+    sc = sqrt(fmax(Sm[(int64_t)c * w + c], 0.0));
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-    const int r = e / w, c = e % w;
-    const int d = pos[c];
-    W[(int64_t)r * w + d] = X[e];
-    Vs[(int64_t)r * w + d] = sig[c] > 0.0 ? X[e] / sig[c] : 0.0;
+  int r = 0;
+  for (int o = threadIdx.x; o < w; o += blockDim.x) {
+    const double so = sqrt(fmax(Sm[(int64_t)o * w + o], 0.0));
+    r += (so > sc) || (so == sc && o < c);
   }
-  for (int c = threadIdx.x; c < w; c += blockDim.x) S_out[pos[c]] = sig[c];
+  atomicAdd(&rank, r);
+  __syncthreads();
+  const int d = rank;
+  const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+  for (int row = threadIdx.x; row < w; row += blockDim.x) {
+    const double x = X[(int64_t)row * w + c];
+    W[(int64_t)row * w + d] = x;
+    Vs[(int64_t)row * w + d] = x * inv;
+  }
+  if (threadIdx.x == 0) S_out[d] = sc;
 }
 
 }  // namespace
@@ -205,7 +218,7 @@ void chol32_shift(int w, const double* G, double* B, cudaStream_t st) {
 }
 
 void eig_finish(int w, const double* Sm, const double* X, double* S, double* Vs, double* W, cudaStream_t st) {
-  k_eig_finish<<<1, 256, (size_t)w * (sizeof(double) + sizeof(int)), st>>>(w, Sm, X, S, Vs, W);
+  k_eig_finish<<<w, 128, 0, st>>>(w, Sm, X, S, Vs, W);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
 }
@@ -232,9 +245,12 @@ void refine_eigvecs64(int w, const double* B, double* X, double* Xn, double* P, 
     else
       gemm64_small(w, w, w, 1.0, P, w, true, P, w, false, 0.0, nullptr, 0, S, w, st);   // S = P^T P
     gemm64_small(w, w, w, 1.0, cur, w, true, cur, w, false, 0.0, nullptr, 0, E, w, st); // X^T X
-    k_refine_correction<<<1, 1024, (size_t)w * sizeof(double), st>>>(w, S, E, E);
+    // lambda (w values) and delta in the first row of Xn, free until the update
+    k_refine_stats<<<1, 1024, 0, st>>>(w, S, E, nxt);
     RPCA_CUDA_TRY(cudaGetLastError());
-    count_launch();
+    k_refine_apply<<<(unsigned)cdiv((int64_t)w * w, 256), 256, 0, st>>>(w, S, E, nxt, E);
+    RPCA_CUDA_TRY(cudaGetLastError());
+    count_launch(2);
     gemm64_small(w, w, w, 1.0, cur, w, false, E, w, false, 1.0, cur, w, nxt, w, st);    // X (I + E)
     std::swap(cur, nxt);
   }

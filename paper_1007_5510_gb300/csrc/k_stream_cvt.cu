@@ -989,7 +989,11 @@ bool pass_cvt(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   if (!a.work) return false;
   if (a.ones_col >= 0 && a.ones_col != a.p) return false;
   if (a.dtype == RPCA_F32) return pass_cvt_src<SRC_F32>(a, st, dev_err);
-  if (a.dtype == RPCA_BF16 && a.mode == MODE_T && !a.shift && !a.scale) return tpass_bf16_chunked(a, st, dev_err);
+  if (a.dtype == RPCA_FP8E4M3) {
+    if (!a.scale) return false;
+    return a.shift ? pass_cvt_src<SRC_FP8_SH>(a, st, dev_err) : pass_cvt_src<SRC_FP8>(a, st, dev_err);
+  }
+  if (a.dtype == RPCA_BF16 && (a.shift || a.scale)) return pass_cvt_src<SRC_BF16_SH>(a, st, dev_err);
   return false;
 }
 

@@ -266,7 +266,9 @@ static bool tpass_bf16(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
 }
 
 bool launch_pass_tc(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
-  if (a.dtype == RPCA_F32) return pass_cvt(a, st, dev_err);
+  // FP32, FP8 and shifted or scaled BF16: the converter kernels (k_stream_cvt.cu)
+  if (a.dtype == RPCA_F32 || a.dtype == RPCA_FP8E4M3 || (a.dtype == RPCA_BF16 && (a.shift || a.scale)))
+    return pass_cvt(a, st, dev_err);
   if (a.mode == MODE_T) return tpass_bf16(a, st, dev_err);
   return fused_pass_tc(a, st, dev_err);
 }

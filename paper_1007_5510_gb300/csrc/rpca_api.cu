@@ -985,7 +985,7 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
 //   H-bar^(j-1) += A F-bar^(j-1),  R^(j-1) = X^(j)T F^(j-1) = H^(j)T H^(j-1).
 // A-bar is the thin product P Z^T with
 //   P = [U, H-bar^(0..i), H^(0..i-1)],  Z = [V C, X^(0..i), F-bar^(0..i-1)].
-rpca_status do_backward(rpca_ctx* c, const rpca_matrix* Am, const double* dS, void* dA, int64_t ldda) {
+void do_backward_enqueue(rpca_ctx* c, const rpca_matrix* Am, const double* dS, void* dA, int64_t ldda) {
   if (!c->adjoint) throw Invalid("context created without RPCA_ADJOINT");
   if (!c->fwd_done) throw Invalid("backward before a completed run");
   if (!Am || !Am->data || !dS || !dA) throw Invalid("null pointer");
@@ -1004,6 +1004,10 @@ rpca_status do_backward(rpca_ctx* c, const rpca_matrix* Am, const double* dS, vo
   base.m = m;
   base.n = n;
   base.scale = Am->col_scale;
+  // the re-streams of A run on the tensor-core kernels where the storage
+  // type and layout allow (BF16, FP32, FP8 converters), else on CUDA cores
+  base.work = c->work.ptr;
+  base.work_bytes = c->work.bytes;
   auto pass_h = [&](const void* X, int64_t ldx, int p, void* Hout, int64_t ldh) {   // Hout = A X
     PassArgs a = base;
     a.mode = MODE_H;
@@ -1012,7 +1016,7 @@ rpca_status do_backward(rpca_ctx* c, const rpca_matrix* Am, const double* dS, vo
     a.p = p;
     a.H = Hout;
     a.ldh = ldh;
-    launch_pass_simt(a, st);
+    if (c->simt || p > 64 || !launch_pass_tc(a, st, c->dev_err())) launch_pass_simt(a, st);
   };
   auto pass_t = [&](const void* Y, int64_t ldy, int p, double* Out, int64_t ldo) {   // Out = A^T Y (FP64)
     PassArgs a = base;
@@ -1023,7 +1027,7 @@ rpca_status do_backward(rpca_ctx* c, const rpca_matrix* Am, const double* dS, vo
     a.F = Out;
     a.ldf = ldo;
     a.f_f64 = true;
-    launch_pass_simt(a, st);
+    if (c->simt || !launch_pass_tc(a, st, c->dev_err())) launch_pass_simt(a, st);
   };
   double* s = c->bsmall.as<double>();
   double* Mk = s; s += (size_t)k * w;
@@ -1087,10 +1091,15 @@ rpca_status do_backward(rpca_ctx* c, const rpca_matrix* Am, const double* dS, vo
     copy_matrix(f64, f64, n, l, at(c->Fb, (size_t)(j - 1) * n * l), l, at(c->Zf, (size_t)(k + w + (j - 1) * l)), r, st);
   }
   lowrank_out(f64, m, n, r, c->Pf.ptr, r, c->Zf.ptr, r, dA, ldda, st);
+}
+
+rpca_status do_backward(rpca_ctx* c, const rpca_matrix* Am, const double* dS, void* dA, int64_t ldda) {
+  do_backward_enqueue(c, Am, dS, dA, ldda);
   uint32_t flags = 0;
-  RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+  RPCA_CUDA_TRY(cudaMemcpyAsync(&flags, c->dev_err(), sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  RPCA_CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (flags & DEV_ERR_BREAKDOWN) return fail(c, RPCA_EBREAKDOWN, "a small factor of the adjoint is singular");
+  if (flags & DEV_ERR_TIMEOUT) return fail(c, RPCA_ETIMEOUT, "a device-side wait timed out");
   return RPCA_OK;
 }
 
@@ -1382,6 +1391,33 @@ rpca_status rpca_batch_run(rpca_batch* b, const rpca_matrix* A, void* const* U, 
     RPCA_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
     b->key = key;
     return RPCA_OK;
+  });
+}
+
+rpca_status rpca_batch_backward(rpca_batch* b, const rpca_matrix* A, const double* const* dS, void* const* dA,
+                                const int64_t* ldda) {
+  if (!b || !A || !dS || !dA || !ldda) return RPCA_EINVAL;
+  return bguarded(b, [&] {
+    const size_t count = b->ctx.size();
+    for (size_t p = 0; p < count; ++p)
+      if (!b->ctx[p]->adjoint) throw Invalid("problem " + std::to_string(p) + " was created without RPCA_ADJOINT");
+    // the problems' backward passes run on the batch's streams, after the
+    // caller's queued work, and the caller's stream waits for all of them
+    RPCA_CUDA_TRY(cudaEventRecord(b->ev_in, b->caller));
+    RPCA_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+    RPCA_CUDA_TRY(cudaEventRecord(b->ev_fork, b->origin));
+    for (auto st : b->streams) RPCA_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_fork, 0));
+    for (size_t p = 0; p < count; ++p) do_backward_enqueue(b->ctx[p], &A[p], dS[p], dA[p], ldda[p]);
+    for (size_t s = 0; s < b->streams.size(); ++s) {
+      RPCA_CUDA_TRY(cudaEventRecord(b->ev_join[s], b->streams[s]));
+      RPCA_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_join[s], 0));
+    }
+    const int cnt = (int)count;
+    k_gather_flags<<<(unsigned)cdiv(cnt, 256), 256, 0, b->origin>>>(b->err_ptrs.as<const uint32_t*>(), cnt,
+                                                                  b->flags.as<uint32_t>());
+    RPCA_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return batch_check(b);
   });
 }
 

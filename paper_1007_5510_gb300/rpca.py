@@ -24,7 +24,7 @@ EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", 
            "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
            "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc",
            "rpca_batch_init", "rpca_batch_run", "rpca_batch_destroy", "rpca_batch_last_error",
-           "rpca_backward", "rpca_test_arm_wait_expiry"]
+           "rpca_backward", "rpca_test_arm_wait_expiry", "rpca_batch_backward"]
 
 
 class RpcaError(RuntimeError):
@@ -108,6 +108,9 @@ def load_library(path=None):
     lib.rpca_batch_destroy.restype = None
     lib.rpca_batch_last_error.argtypes = [vp]
     lib.rpca_batch_last_error.restype = ctypes.c_char_p
+    lib.rpca_batch_backward.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(i64)]
+    lib.rpca_batch_backward.restype = st
     lib.rpca_test_arm_wait_expiry.argtypes = [i32, u64, i64]
     lib.rpca_test_arm_wait_expiry.restype = st
     if path is None:
@@ -381,7 +384,8 @@ class Batch:
     context per problem over `nstreams` library streams; from the second run
     with the same buffers on, one CUDA-graph launch per run."""
 
-    def __init__(self, shapes, k, l, i, dtype=BF16, seeds=None, nstreams=16, stream=None):
+    def __init__(self, shapes, k, l, i, dtype=BF16, seeds=None, nstreams=16, stream=None, adjoint=False):
+        """adjoint: every problem keeps what backward() needs (m >= n each)."""
         lib = load_library()
         self.shapes = [(int(m), int(n)) for m, n in shapes]
         self.k, self.dtype = k, dtype
@@ -390,7 +394,7 @@ class Batch:
         sp = _stream_ptr(stream)
         arr = (Problem * cnt)()
         for p, (m, n) in enumerate(self.shapes):
-            arr[p] = Problem(m, n, k, l, i, ctypes.c_uint64(seeds[p]), None, dtype, 0, 0, sp)
+            arr[p] = Problem(m, n, k, l, i, ctypes.c_uint64(seeds[p]), None, dtype, ADJOINT if adjoint else 0, 0, sp)
         self.ctx = ctypes.c_void_p()
         status = lib.rpca_batch_init(ctypes.byref(self.ctx), cnt, arr, nstreams)
         if status != OK:
@@ -421,6 +425,29 @@ class Batch:
         if status != OK:
             raise RpcaError(status, lib.rpca_batch_last_error(self.ctx).decode())
         return outs
+
+    def backward(self, As, dSs, dAs=None):
+        """dA[p] = sum_j dS[p][j] dsigma_j/dA for every problem of the last
+        run (batch made with adjoint=True; As the same device matrices)."""
+        torch = _torch()
+        lib = load_library()
+        cnt = len(self.shapes)
+        cdt = torch.float64 if self.dtype == F64 else torch.float32
+        dSs = [torch.as_tensor(d, dtype=torch.float64, device="cuda").contiguous() for d in dSs]
+        if dAs is None:
+            dAs = [torch.empty(m, n, dtype=cdt, device="cuda") for m, n in self.shapes]
+        mats = (Matrix * cnt)()
+        for p, A in enumerate(As):
+            mats[p] = Matrix(ctypes.c_void_p(A.data_ptr()), A.stride(0), None)
+        vp = ctypes.c_void_p
+        dS = (vp * cnt)(*[vp(d.data_ptr()) for d in dSs])
+        dA = (vp * cnt)(*[vp(d.data_ptr()) for d in dAs])
+        ld = (ctypes.c_int64 * cnt)(*[d.stride(0) for d in dAs])
+        self._keep_b = (mats, dS, dA, ld, dSs)
+        status = lib.rpca_batch_backward(self.ctx, mats, dS, dA, ld)
+        if status != OK:
+            raise RpcaError(status, lib.rpca_batch_last_error(self.ctx).decode())
+        return dAs
 
     def close(self):
         if self.ctx:

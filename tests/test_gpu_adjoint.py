@@ -112,3 +112,34 @@ def test_autograd_wrapper_matches_direct_call():
     loss.backward()
     direct, _ = _gpu_grad(A, 6, 8, 1, 4, "L2")
     assert np.abs(At.grad.cpu().numpy() - direct).max() <= 1e-10 * np.abs(direct).max()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batched_adjoint_matches_single_problems(dtype):
+    """rpca_batch_backward over uneven problems equals rpca_backward of each
+    problem on its own (which the FD and dense-SVD pins above cover)."""
+    rpca = R()
+    rng = np.random.default_rng(41)
+    shapes = [(int(rng.integers(200, 3000)), int(rng.integers(30, 150))) for _ in range(7)]
+    k, l, i = 4, 8, 1
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    code = rpca.F64 if dtype == "f64" else rpca.F32
+    As = [torch.from_numpy(rng.standard_normal((m, n)) @ np.diag(0.9 ** np.arange(n))).to(tdt).cuda()
+          for m, n in shapes]
+    b = rpca.Batch(shapes, k, l, i, dtype=code, seeds=range(10, 10 + len(shapes)), nstreams=3, adjoint=True)
+    try:
+        outs = b.run(As)
+        dSs = [torch.ones(k, dtype=torch.float64, device="cuda") for _ in shapes]
+        dAs = b.backward(As, dSs)
+        torch.cuda.synchronize()
+        for p, (m, n) in enumerate(shapes):
+            obj = rpca.PCA(m, n, k, l, i, code, seed=10 + p, adjoint=True)
+            try:
+                obj.run(As[p])
+                ref = obj.backward(As[p], np.ones(k))
+            finally:
+                obj.close()
+            e = float((dAs[p] - ref).abs().max() / ref.abs().max())
+            assert e < (1e-12 if dtype == "f64" else 1e-5), (p, e)
+    finally:
+        b.close()

@@ -448,6 +448,57 @@ def test_t_pass_tensor_cores_f32(m, n, w):
     assert e < 5e-5
 
 
+@pytest.mark.parametrize("m,n,l", [(1000, 512, 12), (5000, 4096, 60), (3001, 2000, 30), (40_001, 2608, 63)])
+def test_fused_pass_tensor_cores_fp8(m, n, l):
+    """FP8-e4m3 bytes widened exactly to BF16 by the converters, the
+    per-column scales folded into X (H = A8 diag(s) X) and into F's rows,
+    X and H as BF16 hi/lo slices.  Against the oracle on the dequantised
+    values."""
+    rng = np.random.default_rng(m + l + 7)
+    A = torch.from_numpy(rng.standard_normal((m, n)).astype(np.float32)).cuda()
+    q, sc = gen.quantize_fp8_torch(A)
+    X = rng.standard_normal((n, l))
+    H, F = R().fused_pass(q, _tt(X), col_scale=sc, kernel=2)
+    torch.cuda.synchronize()
+    Adq = (q.view(torch.float8_e4m3fn).float() * sc[None, :]).double().cpu().numpy()
+    Ho, Fo = ro.fused_pass_products(Adq, X.astype(np.float32).astype(np.float64))
+    eh, ef = _rel(H.cpu().numpy(), Ho), _rel(F.cpu().numpy(), Fo)
+    print("PARITY fused fp8 tc %dx%d l=%d H %.2e F %.2e" % (m, n, l, eh, ef))
+    assert eh < 3e-5 and ef < 5e-5
+
+
+@pytest.mark.parametrize("m,n,w", [(3001, 512, 66), (20000, 4096, 180)])
+def test_t_pass_tensor_cores_fp8(m, n, w):
+    rng = np.random.default_rng(m + w + 3)
+    A = torch.from_numpy(rng.standard_normal((m, n)).astype(np.float32)).cuda()
+    q, sc = gen.quantize_fp8_torch(A)
+    Q = np.linalg.qr(rng.standard_normal((m, w)))[0]
+    T = R().t_pass(q, _tt(Q), col_scale=sc, kernel=2)
+    torch.cuda.synchronize()
+    Adq = (q.view(torch.float8_e4m3fn).float() * sc[None, :]).double().cpu().numpy()
+    To = ro.t_pass_product(Adq, Q.astype(np.float32).astype(np.float64))
+    e = _rel(T.cpu().numpy(), To)
+    print("PARITY t pass fp8 tc %dx%d w=%d %.2e" % (m, n, w, e))
+    assert e < 5e-5
+
+
+def test_fused_pass_tensor_cores_bf16_shifted():
+    """BF16 storage with a centring shift: the converters form a - s in FP32
+    and split it, so the shift costs no precision."""
+    rng = np.random.default_rng(31)
+    m, n, l = 20_000, 1024, 40
+    A = rng.standard_normal((m, n)) * 0.01 + 5.0
+    At, Ao = _stored(A, "bf16")
+    s = Ao[:128].mean(axis=0).astype(np.float32)
+    X = rng.standard_normal((n, l))
+    H, F = R().fused_pass(At, _tt(X), shift=_tt(s), kernel=2)
+    torch.cuda.synchronize()
+    Ho, Fo = ro.fused_pass_products(Ao, X.astype(np.float32).astype(np.float64), shift=s.astype(np.float64))
+    eh, ef = _rel(H.cpu().numpy(), Ho), _rel(F.cpu().numpy(), Fo)
+    print("PARITY fused bf16 shifted tc H %.2e F %.2e" % (eh, ef))
+    assert eh < 5e-5 and ef < 1e-4
+
+
 def test_pca_bf16_tensor_cores_vs_fp32():
     """Whole method on BF16 storage (tensor-core passes) against the oracle on
     the same BF16 values, and its spectral error against the FP32 path's."""
