@@ -1138,14 +1138,12 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
 // reorthogonalised Krylov blocks T is well conditioned (its singular values
 // are those of A on the Krylov space), so forming G loses nothing the
 // tolerances can see.
-// The FP32 sweeps stop at a relative off-diagonal of 1e-5 (about two
-// sweeps before FP32 convergence); three FP64 refinement steps then take the
-// vectors to FP64 accuracy wherever the relative gap exceeds ~1e-4 (each step
-// squares the error relative to the gap).  A much looser sweep tolerance
-// leaves vector errors of tolerance / relative gap near the edge of a
-// cluster of singular values, outside the refinement's quadratic basin.
-constexpr int kGramRefineSteps = 3;
-constexpr double kGramJacobiTol = 1e-5;
+// The FP32 sweeps run to FP32 convergence (relative off-diagonal
+// 4 sqrt(w) u): a looser sweep tolerance leaves vector errors of
+// tolerance / relative gap near the edge of a cluster of singular values,
+// outside the refinement's quadratic basin (measured at the precision
+// workload: tolerance 1e-5 and three steps left U^T U - I at 3e-4).
+constexpr int kGramRefineSteps = 2;
 
 void svd_from_gram(int w, const double* G, double* S, double* Vs, double* W, double* work, uint32_t* dev_err,
                    cudaStream_t st) {
@@ -1157,6 +1155,7 @@ void svd_from_gram(int w, const double* G, double* S, double* Vs, double* W, dou
   double* P = work + 4 * ww;
   double* Sm = work + 5 * ww;
   double* E = B;                                   // B is free once the sweeps are done
+  const double kGramJacobiTol = 4.0 * std::sqrt((double)w) * 5.96e-8;
   chol32_shift(w, G, B, st);
   if (getenv("RPCA_JACOBI_SINGLE") || !jacobi_cluster_f32(w, B, Jc32, kGramJacobiTol, 40, dev_err, st)) {
     const size_t mat = ww * sizeof(float);

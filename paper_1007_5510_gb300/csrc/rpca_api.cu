@@ -485,11 +485,9 @@ void validate(const rpca_problem* p) {
 // or, for FP32 A (converter kernels), two BF16 planes of Q, or the X^T
 // slices plus the two BF16 planes of H that the F pass reads.
 size_t tc_work_bytes(rpca_dtype dt, int64_t m, int64_t n, int w) {
-  size_t b = (size_t)m * round_up(w, 64) * 2;
-  if (dt == RPCA_F32) {
-    b = std::max<size_t>((size_t)2 * m * round_up(w, 64) * 2,
-                         (size_t)2 * 64 * round_up(n, 128) * 2 + 256 + (size_t)2 * m * 64 * 2);
-  }
+  (void)dt;   // every storage type may take the converter kernels (FP32, FP8, shifted BF16)
+  const size_t b = std::max<size_t>((size_t)2 * m * round_up(w, 64) * 2,
+                                    (size_t)2 * 64 * round_up(n, 128) * 2 + 256 + (size_t)2 * m * 64 * 2);
   return b + 4096;
 }
 
@@ -500,11 +498,13 @@ bool gram_step4(const rpca_ctx* c) { return !c->f64 && c->w <= 192 && !c->adjoin
 // Will the T pass of an FP32 context read the first two BF16 slices of the
 // sliced Q directly (converter kernel; TMA-aligned A)?
 bool tpass_f32_slices_ok(const rpca_ctx* c, const rpca_matrix* Am) {
-  if (c->prob.dtype != RPCA_F32 || !c->sliced || c->simt || c->adjoint) return false;
-  if (c->host_a) return (c->n * 4) % 16 == 0;
+  const rpca_dtype dt = c->prob.dtype;
+  if ((dt != RPCA_F32 && dt != RPCA_FP8E4M3) || !c->sliced || c->simt || c->adjoint) return false;
+  const int64_t eb = (int64_t)dtype_bytes(dt);
+  if (c->host_a) return (c->n * eb) % 16 == 0;
   const void* A = c->transposed ? c->At.ptr : Am->data;
   const int64_t lda = c->transposed ? c->n : Am->ld;
-  return (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda * 4) % 16 == 0;
+  return (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda * eb) % 16 == 0;
 }
 
 // One streamed pass over the working matrix (device-resident or tiles).
@@ -1487,7 +1487,7 @@ rpca_status rpca_op_fused_pass(rpca_dtype dtype, int64_t m, int64_t n, int32_t p
     err.alloc(64 * sizeof(uint32_t));
     RPCA_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, 64 * sizeof(uint32_t), st));
     if (kernel != 1 && dtype != RPCA_F64) {
-      work.alloc(dtype == RPCA_F32 ? tc_work_bytes(dtype, m, n, 64) : (size_t)64 * round_up(n, 8) * 2 + 4096);
+      work.alloc(tc_work_bytes(dtype, m, n, 64));
       a.work = work.ptr;
       a.work_bytes = work.bytes;
     }
