@@ -245,8 +245,11 @@ def main():
 
     t16 = ms16 / args.steps / 1e3
     t32 = ms32 / args.steps / 1e3
-    stream_bytes16 = (i + 2) * m * n * bytes_bf16
-    stream_bytes32 = (i + 2) * m * n * bytes_f32
+    # passes over A per PCA as the library reports them: i+2, or i+1 when T
+    # was formed from the fused passes' F blocks
+    np16, np32, np8 = ctx16.passes_last_run(), ctx32.passes_last_run(), ctx8.passes_last_run()
+    stream_bytes16 = np16 * m * n * bytes_bf16
+    stream_bytes32 = np32 * m * n * bytes_f32
     value = world * stream_bytes16 / t16 / 1e9
     hbm, peak_kind = peaks()
 
@@ -300,7 +303,7 @@ def main():
             "data": "synthetic", "gpu_launches": int(launches),
             "config": {"workload": "precision: m=%d n=%d k=%d l=%d i=%d, BF16 storage "
                                    "(FP32 measured alongside)" % (m, n, k, l, i),
-                       "m": m, "n": n, "k": k, "l": l, "i": i, "streams_per_pca": i + 2,
+                       "m": m, "n": n, "k": k, "l": l, "i": i, "streams_per_pca": np16,
                        "l2_flush": "not needed: A (%.1f GB) >> L2" % (m * n * 2 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "kernels": "cuda-cores" if args.simt else "auto"},
@@ -308,10 +311,12 @@ def main():
             "pct_hbm_peak": round(100 * stream_bytes16 / t16 / 1e9 / hbm, 2),
             "fp32": {"value": round(world * stream_bytes32 / t32 / 1e9, 2), "unit": "GB/s",
                      "s_per_pca": round(t32, 6), "fused_pass_ms": round(fused_ms32, 4),
-                     "phases_ms": phases32},
+                     "streams_per_pca": np32, "phases_ms": phases32},
             "bf16_speedup_vs_fp32": round(t32 / t16, 3),
-            "fp8": {"value": round(world * (i + 2) * m * n * 1 / t8 / 1e9, 2), "unit": "GB/s",
-                    "s_per_pca": round(t8, 6), "kernels": "cuda-cores (FP8 bytes, per-column scales)",
+            "fp8": {"value": round(world * np8 * m * n * 1 / t8 / 1e9, 2), "unit": "GB/s",
+                    "s_per_pca": round(t8, 6), "streams_per_pca": np8,
+                    "kernels": "tensor cores (FP8 bytes widened to BF16 by converter warps, per-column scales "
+                               "folded into X and the result rows)",
                     "phases_ms": {nm: round(v / max(1, runs8), 4) for nm, v in zip(names, ph8)}},
             "phases_ms": phases16,
             "roofline": {"bound": "hbm", "kernel": "fused pass (BF16, l=%d)" % l,

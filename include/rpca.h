@@ -90,6 +90,15 @@ typedef enum {
                                  per run instead of one per pass.  Not part of
                                  the paper (no device memory there). */
 
+#define RPCA_KEEP_T_PASS 0x40u /* always run Step 3 as its own pass over A.
+                                 Without it, FP32 and FP8 problems whose
+                                 Step 2 ran as one Cholesky QR of H with a
+                                 well-conditioned factor (max/min diagonal of
+                                 R <= 8) form T = A^T Q = [F^(0) .. F^(i)] R^-1
+                                 from the blocks F^(j) = A^T H^(j) their
+                                 passes accumulate (Section 3: Q = H R^-1),
+                                 and read A i+1 times instead of i+2 */
+
 typedef struct {
   int64_t m, n;           /* A is m x n; 1 <= k < min(m, n) */
   int32_t k, l, i;        /* rank, block width (l >= k), power steps (i >= 0);
@@ -216,6 +225,11 @@ rpca_status rpca_gaussian(uint64_t seed, uint32_t domain, int64_t count,
  * A replay of a batch's captured CUDA graph adds the number of kernels the
  * graph holds. */
 uint64_t rpca_kernel_launches(void);
+
+/* Passes over A of the last completed run of c: i+2 (Step 1's i+1 and
+ * Step 3's), or i+1 when T was formed from the F blocks (RPCA_KEEP_T_PASS
+ * above); 0 before a run completed. */
+int32_t rpca_last_run_passes(const rpca_ctx* c);
 
 /* Per-phase device times of a context created with RPCA_TIMING, summed
  * over the runs finished since the previous call (then reset).  Phases:

@@ -124,7 +124,13 @@ __global__ void k_compact_sq(int nblk, int l, const double* __restrict__ C, int6
 // Y (128-row tiles, 64 columns at y0) = beta * Y + X M, with X (nkb boxes of
 // 64 columns at x0) and Y in slice planes and M given by its transposed
 // slices (resident).  Warp 0 lane 0: TMA; warp 1 lane 0: MMA (six slice
-// products per K step into a double-buffered TMEM accumulator); warps 2-5:
+// products per K step into a double-buffered TMEM accumulator pair: the
+// hi*hi product in one, the five smaller products in the other, added with
+// round-to-nearest in the epilogue -- the tensor cores' accumulation rounds
+// with a bias of about one unit in the last place per MMA, so a single
+// accumulator taking all six products over K = 192 drifted by ~5e-6
+// relative, which showed as a 1e-5 departure from orthonormality of the
+// U = Q M product at 1e6 rows); warps 2-5:
 // epilogue (one tile row per thread: optional FP32 output, optional beta
 // term from the old slices, re-slicing into a shared staging tile that a
 // TMA store writes back).
@@ -198,7 +204,7 @@ k_apply_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     tc::fence_mbar_init();
   }
   if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, 128);
+    tc::tmem_alloc(tmem_slot, 256);
     tc::tmem_relinquish();
   }
   tc::tc_fence_before();
@@ -270,8 +276,9 @@ k_apply_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 #pragma unroll
             for (int pr = 0; pr < 6; ++pr) {
               const int a = (int)((PA >> (4 * pr)) & 0xFu), bs = (int)((PB >> (4 * pr)) & 0xFu);
-              tc::mma_f16(tmem + b * 64, tc::sdesc_add(xS[a], kk * 32), tc::sdesc_add(mS[bs], kk * 32), idesc,
-                          (kb > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+              // accumulator b*128 takes hi*hi, b*128 + 64 the rest
+              tc::mma_f16(tmem + b * 128 + (pr == 0 ? 0u : 64u), tc::sdesc_add(xS[a], kk * 32),
+                          tc::sdesc_add(mS[bs], kk * 32), idesc, (kb > 0 || kk > 0 || pr > 1) ? 1u : 0u);
             }
           }
           tc::mma_commit(&empty[s]);
@@ -295,11 +302,15 @@ k_apply_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       if (!ok) break;
       tc::tc_fence_after();
       float acc[64];
-      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * 64u;
-      tc::tmem_ld16(taddr + 0, *reinterpret_cast<float(*)[16]>(&acc[0]));
-      tc::tmem_ld16(taddr + 16, *reinterpret_cast<float(*)[16]>(&acc[16]));
-      tc::tmem_ld16(taddr + 32, *reinterpret_cast<float(*)[16]>(&acc[32]));
-      tc::tmem_ld16(taddr + 48, *reinterpret_cast<float(*)[16]>(&acc[48]));
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * 128u;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        float lo[16];
+        tc::tmem_ld16(taddr + 16 * g, *reinterpret_cast<float(*)[16]>(&acc[16 * g]));
+        tc::tmem_ld16(taddr + 64 + 16 * g, lo);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[16 * g + j] += lo[j];
+      }
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tfree[b]);
@@ -357,7 +368,7 @@ k_apply_bf16x3(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 int g_sms_sl = 0;

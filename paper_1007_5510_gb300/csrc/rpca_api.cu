@@ -291,7 +291,8 @@ static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, vo
 // stream is being captured.
 static bool block_qr_sliced_whole(int64_t m, int nblk, int l, float* H, int64_t ld, void* S, int64_t prow,
                                   double* E_out, bool fp32_out, const QrScratch& s, double* G, double* R,
-                                  double* Rinv, double* tmp, uint32_t* dev_err, cudaStream_t st) {
+                                  double* Rinv, double* tmp, uint32_t* dev_err, cudaStream_t st,
+                                  double* kappa = nullptr) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   RPCA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
   if (cap != cudaStreamCaptureStatusNone) return false;
@@ -323,10 +324,21 @@ static bool block_qr_sliced_whole(int64_t m, int nblk, int l, float* H, int64_t 
   }
   // any shifted diagonal block: leave H to the block path
   std::vector<uint32_t> qf((size_t)kQfWords * nblk);
+  std::vector<double> rd(w);
   RPCA_CUDA_TRY(cudaMemcpyAsync(qf.data(), s.qf, qf.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RPCA_CUDA_TRY(cudaMemcpy2DAsync(rd.data(), sizeof(double), R, (size_t)(w + 1) * sizeof(double), sizeof(double), w,
+                                  cudaMemcpyDeviceToHost, st));
   RPCA_CUDA_TRY(cudaStreamSynchronize(st));
   for (int b = 0; b < nblk; ++b)
     if (qf[(size_t)kQfWords * b + 1]) return false;
+  if (kappa) {
+    double lo = INFINITY, hi = 0.0;
+    for (double v : rd) {
+      lo = std::min(lo, std::fabs(v));
+      hi = std::max(hi, std::fabs(v));
+    }
+    *kappa = lo > 0.0 ? hi / lo : INFINITY;
+  }
   // R^-1 (upper): Rinv_bc = -R_bb^-1 sum_{b<a<=c} R_ba Rinv_ac, from the diagonal outwards
   for (int c = 1; c < nblk; ++c)
     for (int b = c - 1; b >= 0; --b) {
@@ -385,6 +397,15 @@ struct rpca_ctx {
   // blocks X^(0..i) are kept orthonormal to each other in Xall (n x w)
   bool reorth = false;
   DevBuf Xall;
+  // T without its own pass over A: T = A^T Q = [F^(0) .. F^(i)] R^-1 from
+  // the F blocks the fused passes accumulate anyway (Fall, n x w FP32), when
+  // the whole-H Cholesky QR ran and kappa(R) is small (the F blocks' error
+  // is amplified by it).  Converter-kernel storage only (FP32, FP8), whose F
+  // carries FP32-class error.
+  bool mirror = false;
+  bool mirrored_last = false;    // the last run formed T this way
+  double last_kappa = 0.0;       // max/min diagonal of R in the last whole-H QR
+  DevBuf Fall;
   // RPCA_HOST_RESIDENT: device copy of host A, valid once this run's first
   // pass has copied every tile
   bool resident = false, resident_valid = false;
@@ -473,7 +494,8 @@ void validate(const rpca_problem* p) {
   if (p->l > 255) throw Invalid("l > 255 is not supported");
   if ((int64_t)(p->i + 1) * p->l > 256) throw Invalid("(i+1) l > 256 is not supported");
   if (p->dtype < RPCA_F64 || p->dtype > RPCA_FP8E4M3) throw Invalid("unknown dtype");
-  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT | RPCA_TIMING | RPCA_ADJOINT | RPCA_HOST_RESIDENT))
+  if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT | RPCA_TIMING | RPCA_ADJOINT | RPCA_HOST_RESIDENT |
+                   RPCA_KEEP_T_PASS))
     throw Invalid("unknown flag");
   if ((p->flags & RPCA_HOST_RESIDENT) && !(p->flags & RPCA_HOST_A)) throw Invalid("RPCA_HOST_RESIDENT needs RPCA_HOST_A");
   if ((p->flags & RPCA_ADJOINT) && ((p->flags & (RPCA_CENTER | RPCA_HOST_A)) || p->n > p->m))
@@ -490,6 +512,11 @@ size_t tc_work_bytes(rpca_dtype dt, int64_t m, int64_t n, int w) {
                                     (size_t)2 * 64 * round_up(n, 128) * 2 + 256 + (size_t)2 * m * 64 * 2);
   return b + 4096;
 }
+
+// kappa(R) up to which T is formed from the F blocks: their relative error
+// (~1e-5 from the BF16 hi/lo products) times kappa stays below the FP32
+// tolerance on sigma (1e-4).
+constexpr double kMirrorKappa = 8.0;
 
 // Step 4 from the Gram of T (FP32-class storage; the single-CTA Cholesky
 // preconditioner takes w <= 192), else from a QR of T.
@@ -626,7 +653,7 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   a.shift = c->centered ? c->shift.ptr : nullptr;
   if (j <= c->i) {
     // Step 1: pass j forms H^(j) = A_c X and (j < i) F = A_c^T H^(j)
-    a.mode = (j < c->i) ? MODE_FUSED : MODE_H;
+    a.mode = (j < c->i || c->mirror) ? MODE_FUSED : MODE_H;
     void* Xj = c->reorth ? xall_block(c, j) : c->X.ptr;
     const int64_t ldxj = c->reorth ? c->w : c->ldx;
     a.X = Xj;
@@ -652,10 +679,14 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
       column_to_vec(f64, c->n, c->F.ptr, c->ldx, c->l, 1.0 / (double)c->m, c->d.as<double>(), st);
       vec_mat(f64, c->n, c->l, c->d.as<double>(), Xj, ldxj, c->vtmp.as<double>(), st);
       sub_rowvec(f64, c->m, c->l, c->vtmp.as<double>(), c->H.ptr, c->w, st);
-      if (j < c->i)
+      if (j < c->i || c->mirror)
         rank1_sub(f64, c->n, c->l, (double)c->m, c->d.as<double>(), c->vtmp.as<double>(), c->F.ptr,
                   c->ldx, st);
     }
+    // F^(j) = A_c^T H^(j), kept for forming T without a pass
+    if (c->mirror)
+      copy_matrix(f64, f64, c->n, c->l, c->F.ptr, c->ldx, static_cast<char*>(c->Fall.ptr) + (size_t)j * c->l * es,
+                  c->w, st);
     if (j < c->i && c->reorth) {
       // block Lanczos: X^(j+1) = orth(F - X_{<=j} X_{<=j}^T F), the
       // projection applied twice (same Krylov space as orth(F), far better
@@ -687,14 +718,16 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   const bool t32s = tpass_f32_slices_ok(c, Am);
   c->tic(c->i + 1);
   const bool q32 = !(t16 || t32s) || c->adjoint;
+  bool whole = false;
   if (c->sliced) {
     // the whole-H Cholesky QR's scratch (G, R, R^-1, one block): Step 4's
     // work area, free until then
     const size_t ww = (size_t)c->w * c->w;
     double* sw = c->svdwork;
-    if (!(c->reorth && block_qr_sliced_whole(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows,
-                                             c->E, q32, c->qs, sw, sw + 2 * ww, sw + ww, sw + 3 * ww, c->dev_err(),
-                                             st)))
+    whole = c->reorth && block_qr_sliced_whole(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows,
+                                               c->E, q32, c->qs, sw, sw + 2 * ww, sw + ww, sw + 3 * ww, c->dev_err(),
+                                               st, &c->last_kappa);
+    if (!whole)
       block_qr_sliced(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows, c->E, q32, c->qs,
                       c->dev_err(), st);
   } else {
@@ -702,6 +735,21 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
              c->Hlo.as<float>());
   }
   c->toc(c->i + 1);
+  // T = [F^(0) .. F^(i)] R^-1 (FP32 products; R^-1 from the whole-H
+  // factorisation, still in Step 4's work area) when kappa(R) keeps the F
+  // blocks' FP32-class error below the FP32 tolerances
+  c->mirrored_last = c->mirror && whole && c->last_kappa <= kMirrorKappa;
+  if (c->mirrored_last) {
+    c->tic(c->i + 2);
+    gemm_xm(false, c->n, c->w, c->w, c->Fall.ptr, c->w, c->svdwork + (size_t)c->w * c->w, c->w, 1.0, 0.0, c->T.ptr,
+            c->w, st);
+    copy_matrix(false, true, c->n, c->w, c->T.ptr, c->w, c->T64.ptr, c->w, st);
+    c->toc(c->i + 2);
+    if (!gram_step4(c))
+      gemm_xm(f64, c->n, c->w, c->w, c->T.ptr, c->w, c->E, c->w, -0.5, 1.0, c->T.ptr, c->w, st);
+    c->next_pass = c->i + 2;
+    return RPCA_OK;
+  }
   a.mode = MODE_T;
   a.p = c->w;
   a.H = c->H.ptr;
@@ -955,6 +1003,9 @@ rpca_status do_init(rpca_ctx* c, const rpca_problem* p) {
   c->G64.alloc(G.size() * sizeof(double));
   RPCA_CUDA_TRY(cudaMemcpy(c->G64.ptr, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
   c->reorth = !c->adjoint;
+  c->mirror = c->reorth && c->sliced && !c->simt && (p->dtype == RPCA_F32 || p->dtype == RPCA_FP8E4M3) &&
+              !(p->flags & RPCA_KEEP_T_PASS);
+  if (c->mirror) c->Fall.alloc((size_t)c->n * c->w * es);
   if (c->reorth) {
     // X^(0) = orth(G), once per context (G is fixed)
     c->Xall.alloc((size_t)c->n * c->w * es);
@@ -1456,6 +1507,11 @@ rpca_status rpca_gaussian(uint64_t seed, uint32_t domain, int64_t count, double*
 }
 
 uint64_t rpca_kernel_launches(void) { return g_launches.load(); }
+
+int32_t rpca_last_run_passes(const rpca_ctx* c) {
+  if (!c || c->next_pass != c->i + 2) return 0;
+  return c->i + 1 + (c->mirrored_last ? 0 : 1);
+}
 
 int32_t rpca_phase_times(rpca_ctx* c, double* ms, int32_t cap, int32_t* runs) {
   if (!c || !c->timing) return 0;

@@ -17,14 +17,14 @@ OK, MORE = 0, 1
 STATUS = {0: "RPCA_OK", 1: "RPCA_MORE", -1: "RPCA_EINVAL", -2: "RPCA_ENOMEM", -3: "RPCA_ECUDA",
           -4: "RPCA_ENODEV", -5: "RPCA_EBREAKDOWN", -6: "RPCA_ETIMEOUT", -7: "RPCA_ESTATE"}
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
-CENTER, HOST_A, SIMT, TIMING, ADJOINT, HOST_RESIDENT = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+CENTER, HOST_A, SIMT, TIMING, ADJOINT, HOST_RESIDENT, KEEP_T_PASS = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20, 0x40
 
 EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
            "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
            "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
            "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc",
            "rpca_batch_init", "rpca_batch_run", "rpca_batch_destroy", "rpca_batch_last_error",
-           "rpca_backward", "rpca_test_arm_wait_expiry", "rpca_batch_backward"]
+           "rpca_backward", "rpca_test_arm_wait_expiry", "rpca_batch_backward", "rpca_last_run_passes"]
 
 
 class RpcaError(RuntimeError):
@@ -111,6 +111,8 @@ def load_library(path=None):
     lib.rpca_batch_backward.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(i64)]
     lib.rpca_batch_backward.restype = st
+    lib.rpca_last_run_passes.argtypes = [vp]
+    lib.rpca_last_run_passes.restype = i32
     lib.rpca_test_arm_wait_expiry.argtypes = [i32, u64, i64]
     lib.rpca_test_arm_wait_expiry.restype = st
     if path is None:
@@ -215,7 +217,8 @@ class PCA:
     """A context: rpca_init on construction, passes, finish, rerun."""
 
     def __init__(self, m, n, k, l, i, dtype=F32, seed=0, center=False, G=None, host_a=False,
-                 tile_rows=0, simt=False, stream=None, timing=False, adjoint=False, host_resident=False):
+                 tile_rows=0, simt=False, stream=None, timing=False, adjoint=False, host_resident=False,
+                 keep_t_pass=False):
         """host_a: A is in host memory and every pass streams it in tiles;
         host_resident (with host_a): the first pass of each run copies it
         once into a device copy that the later passes read."""
@@ -224,7 +227,7 @@ class PCA:
         self.host_a = bool(host_a)
         flags = ((CENTER if center else 0) | (HOST_A if host_a else 0) | (SIMT if simt else 0)
                  | (ADJOINT if adjoint else 0) | (HOST_RESIDENT if host_resident else 0)
-                 | (TIMING if timing else 0))
+                 | (TIMING if timing else 0) | (KEEP_T_PASS if keep_t_pass else 0))
         self._G = None
         Gp = None
         if G is not None:
@@ -295,6 +298,10 @@ class PCA:
         _check(load_library().rpca_rerun(self.ctx, ctypes.byref(mat), _ptr(U), U.stride(0),
                                          _ptr(S), _ptr(V), V.stride(0)), self.ctx)
         return U, S, V
+
+    def passes_last_run(self):
+        """Passes over A of the last run (i+2, or i+1 with T from the F blocks)."""
+        return int(load_library().rpca_last_run_passes(self.ctx))
 
     def phase_times(self):
         """(list of per-phase ms summed over runs, run count) since last call."""

@@ -499,6 +499,38 @@ def test_fused_pass_tensor_cores_bf16_shifted():
     assert eh < 5e-5 and ef < 1e-4
 
 
+@pytest.mark.parametrize("dtype", ["f32", "fp8"])
+def test_pca_t_from_f_blocks_matches_t_pass(dtype):
+    """Step 3 without its pass over A: T = [F^(0) .. F^(i)] R^-1 from the F
+    blocks of the fused passes (Q = H R^-1 in Step 2).  Same results as the
+    run with its own T pass, and the oracle's at the FP32 bounds; the
+    context reports i+1 passes over A instead of i+2."""
+    m, n, k, l, i = 60_000, 1024, 20, 48, 2
+    A = gen.lowrank_np(m, n, np.exp(-np.arange(1, n + 1) / 25.0), seed=13) + \
+        1e-3 * np.random.default_rng(13).standard_normal((m, n))
+    At = torch.from_numpy(A.astype(np.float32)).cuda()
+    sc = None
+    code = R().F32
+    if dtype == "fp8":
+        At, sc = gen.quantize_fp8_torch(At)
+        code = R().FP8E4M3
+    outs = {}
+    for keep in (False, True):
+        ctx = R().PCA(m, n, k, l, i, code, seed=21, keep_t_pass=keep)
+        try:
+            U, S, V = ctx.run(At, col_scale=sc)
+            outs[keep] = (U.clone(), S.clone(), V.clone(), ctx.passes_last_run())
+        finally:
+            ctx.close()
+    assert outs[False][3] == i + 1 and outs[True][3] == i + 2, (outs[False][3], outs[True][3])
+    s0, s1 = outs[False][1].cpu().numpy(), outs[True][1].cpu().numpy()
+    assert np.max(np.abs(s0 - s1) / s1) < 2e-5
+    Ao = At.double().cpu().numpy() if dtype == "f32" else \
+        (At.view(torch.float8_e4m3fn).float() * sc[None, :]).double().cpu().numpy()
+    Uo, So, Vo = ro.rpca(Ao, k, l, i, seed=21, reorth=True)
+    _compare(outs[False][0], outs[False][1], outs[False][2], Uo, So, Vo, 1e-4, 1e-3, "T from F blocks %s" % dtype)
+
+
 def test_pca_bf16_tensor_cores_vs_fp32():
     """Whole method on BF16 storage (tensor-core passes) against the oracle on
     the same BF16 values, and its spectral error against the FP32 path's."""
