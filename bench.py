@@ -434,15 +434,22 @@ def run_batched(args, world, rank, local, dist):
     dev = torch.device("cuda", local)
     shapes = gen.batched_shapes(count=args.count, seed=5510 + rank)
     t0 = time.perf_counter()
-    As = [gen.workload_torch("batched", dev, m=m, n=n, seed=1007 + 7919 * rank + p, rank_cap=1024,
-                             dtype=torch.bfloat16) for p, (m, n) in enumerate(shapes)]
+    As = []
+    for p, (m, n) in enumerate(shapes):
+        # rows padded to a multiple of 8 elements (16 bytes): the layout the
+        # grouped kernels' TMA loads take
+        buf = torch.zeros(m, (n + 7) // 8 * 8, dtype=torch.bfloat16, device=dev)
+        buf[:, :n] = gen.workload_torch("batched", dev, m=m, n=n, seed=1007 + 7919 * rank + p, rank_cap=1024,
+                                        dtype=torch.bfloat16)
+        As.append(buf[:, :n])
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     b = rpca.Batch(shapes, k, l, i, dtype=rpca.BF16, seeds=range(len(shapes)), nstreams=16)
-    outs = b.run(As)                          # direct run, records the graph
+    outs = b.run(As)                          # direct run (per-problem form: records the graph)
     for _ in range(max(0, args.warmup - 1)):
-        outs = b.run(As, outs)                # graph replays
+        outs = b.run(As, outs)
     torch.cuda.synchronize()
+    grouped = b.grouped
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
     sampler.start()
@@ -472,8 +479,11 @@ def run_batched(args, world, rank, local, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "gpu_launches": int(launches),
             "config": {"workload": "batched: %d BF16 PCAs, m ~ U[1000, 50000], n ~ U[64, 1024], "
-                                   "sigma_j = j^-1.5, k=%d l=%d i=%d, one graph launch per step"
-                                   % (len(shapes), k, l, i),
+                                   "sigma_j = j^-1.5, k=%d l=%d i=%d, %s"
+                                   % (len(shapes), k, l, i, "grouped kernels (one launch per step of the "
+                                      "method over all problems)" if grouped else
+                                      "per-problem contexts, one graph launch per step"),
+                       "grouped": bool(grouped), "lda": "n rounded up to a multiple of 8",
                        "problems": len(shapes), "a_bytes": a_bytes, "streams_per_pca": i + 2,
                        "l2_flush": "not needed: A (%.1f GB in total) >> L2" % (a_bytes / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},

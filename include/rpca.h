@@ -61,8 +61,8 @@ typedef enum {
 } rpca_status;
 
 /* Storage type of A.  Compute precision: FP64 for RPCA_F64, otherwise FP32
- * accumulation (tensor-core operands BF16, or TF32 x3 for FP32 products;
- * FP8 bytes are widened on the CUDA cores). */
+ * accumulation on BF16 tensor-core operands (FP32 data through exact BF16
+ * hi/lo splits, FP8 bytes widened exactly to BF16 by converter warps). */
 typedef enum {
   RPCA_F64 = 0,
   RPCA_F32 = 1,
@@ -98,6 +98,9 @@ typedef enum {
                                  from the blocks F^(j) = A^T H^(j) their
                                  passes accumulate (Section 3: Q = H R^-1),
                                  and read A i+1 times instead of i+2 */
+#define RPCA_NO_GROUPED  0x80u /* rpca_batch_init: give this batch one
+                                 context per problem even when its problems
+                                 fit the grouped kernels (see rpca_batch_init) */
 
 typedef struct {
   int64_t m, n;           /* A is m x n; 1 <= k < min(m, n) */
@@ -262,12 +265,50 @@ rpca_status rpca_backward(rpca_ctx* c, const rpca_matrix* A, const double* dS,
 /* ---------------------------------------------------------------------- */
 typedef struct rpca_batch rpca_batch;
 
-/* One context per problem (problems[p] as for rpca_init; device matrices
- * only, no RPCA_TIMING), spread over nstreams streams of the library that
- * fork from and join to problems[0].stream.  All workspace is allocated
- * here. */
+/* A batch of independent problems (problems[p] as for rpca_init; device
+ * matrices only, no RPCA_TIMING).  Two forms:
+ *   grouped   when every problem is BF16 with no flags (RPCA_KEEP_T_PASS
+ *             aside), m >= n, n <= 1024, l <= 32, (i+1) l <= 64,
+ *             n (i+1) l <= 45056, and all share k, l and i: each step of
+ *             Section 3 runs as one launch over all problems (about
+ *             3 i + 8 kernels per run; rpca_batch_grouped says so).  Step 1
+ *             is the block Lanczos form, Step 2 a twice-repeated Cholesky
+ *             QR, Step 4 a Householder QR plus one-sided Jacobi in FP32 on
+ *             the n side.  A numerically rank-deficient H is reported as
+ *             RPCA_EBREAKDOWN for its problem (the per-problem form handles
+ *             it).  X^(0) = orth(G) is formed here.
+ *   per-problem otherwise (or with RPCA_NO_GROUPED on any problem): one
+ *             context per problem, spread over nstreams streams of the
+ *             library that fork from and join to problems[0].stream.
+ * All workspace of the chosen form is allocated here. */
 rpca_status rpca_batch_init(rpca_batch** out, int32_t count,
                             const rpca_problem* problems, int32_t nstreams);
+
+/* 1 if the batch's last run (before any run: the batch as created) used
+ * the grouped kernels, 0 otherwise or for NULL. */
+int32_t rpca_batch_grouped(const rpca_batch* b);
+
+/* Launch parameters of the grouped kernels: tuning[0] H-pass TMA stages
+ * (2..8), [1] T-pass stages (2..8), [2] rows per T-pass work item,
+ * [3] rows per row-kernel item (multiples of 64).  Get and set copy 4
+ * int32 values (host); set clamps them to their ranges.  RPCA_EINVAL for a
+ * per-problem batch or NULL arguments. */
+rpca_status rpca_batch_get_tuning(const rpca_batch* b, int32_t* tuning);
+rpca_status rpca_batch_set_tuning(rpca_batch* b, const int32_t* tuning);
+
+/* Autotuner of the grouped kernels: times rpca_batch_run on these
+ * arguments for a set of launch parameters (coordinate search over the
+ * four values above, each candidate run twice and timed once with CUDA
+ * events), keeps the fastest, and records it in the JSON file cache_path
+ * (host path; NULL: no cache) under a key made of the storage type, the
+ * power-of-two buckets of the largest n and of the mean m, k, l and i.  A
+ * key already in the file is applied without timing.  The outputs are
+ * written as by rpca_batch_run.  *chosen (4 values, may be NULL) receives
+ * the parameters in use.  RPCA_EINVAL for a per-problem batch. */
+rpca_status rpca_batch_tune(rpca_batch* b, const rpca_matrix* A, void* const* U,
+                            const int64_t* ldu, double* const* S, void* const* V,
+                            const int64_t* ldv, const char* cache_path,
+                            int32_t* chosen);
 
 /* All problems: A[p] as for rpca_pass, outputs as for rpca_finish (arrays
  * of count pointers / leading dimensions; U, S, V or their entries may be

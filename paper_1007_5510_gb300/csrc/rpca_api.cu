@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -11,6 +13,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "grouped.h"
 
 namespace rpca {
 
@@ -495,7 +498,7 @@ void validate(const rpca_problem* p) {
   if ((int64_t)(p->i + 1) * p->l > 256) throw Invalid("(i+1) l > 256 is not supported");
   if (p->dtype < RPCA_F64 || p->dtype > RPCA_FP8E4M3) throw Invalid("unknown dtype");
   if (p->flags & ~(RPCA_CENTER | RPCA_HOST_A | RPCA_SIMT | RPCA_TIMING | RPCA_ADJOINT | RPCA_HOST_RESIDENT |
-                   RPCA_KEEP_T_PASS))
+                   RPCA_KEEP_T_PASS | RPCA_NO_GROUPED))
     throw Invalid("unknown flag");
   if ((p->flags & RPCA_HOST_RESIDENT) && !(p->flags & RPCA_HOST_A)) throw Invalid("RPCA_HOST_RESIDENT needs RPCA_HOST_A");
   if ((p->flags & RPCA_ADJOINT) && ((p->flags & (RPCA_CENTER | RPCA_HOST_A)) || p->n > p->m))
@@ -1182,7 +1185,14 @@ struct rpca_batch {
   std::vector<uint32_t> host_flags;
   int bad = -1;                          // index of the last failing problem
   std::string last_error;
+  // grouped kernels over all problems (BF16 batches that fit them); the
+  // per-problem contexts are then made only if a run's layout needs them
+  rpca::grp::GroupedBatch* grp = nullptr;
+  bool last_grouped = false;
+  std::vector<rpca_problem> problems;
+  int nstreams = 1;
   ~rpca_batch() {
+    if (grp) rpca::grp::grouped_destroy(grp);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (auto* c : ctx) rpca_destroy(c);
@@ -1218,6 +1228,179 @@ void batch_enqueue(rpca_batch* b, const rpca_matrix* A, void* const* U, const in
                                                                     b->flags.as<uint32_t>());
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
+}
+
+// One context per problem over the batch's stream pool (the per-problem
+// form; also made lazily for a grouped batch whose run needs it).
+rpca_status batch_make_contexts(rpca_batch* b) {
+  const int32_t count = (int32_t)b->problems.size();
+  const int ns = std::min<int32_t>(b->nstreams, count);
+  b->streams.assign(ns, nullptr);
+  b->ev_join.assign(ns, nullptr);
+  for (int i = 0; i < ns; ++i) {
+    RPCA_CUDA_TRY(cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking));
+    RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming));
+  }
+  RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  std::vector<const uint32_t*> ptrs(count);
+  for (int32_t p = 0; p < count; ++p) {
+    rpca_problem q = b->problems[p];
+    q.stream = b->streams[p % ns];
+    rpca_ctx* c = new rpca_ctx();
+    b->ctx.push_back(c);
+    rpca_status si = guarded(c, [&] { return do_init(c, &q); });
+    if (si != RPCA_OK) {
+      b->last_error = "problem " + std::to_string(p) + ": " + c->last_error;
+      return si;
+    }
+    ptrs[p] = c->err.as<uint32_t>();
+  }
+  b->err_ptrs.alloc(count * sizeof(uint32_t*));
+  b->flags.alloc(count * sizeof(uint32_t));
+  b->host_flags.assign(count, 0u);
+  RPCA_CUDA_TRY(cudaMemcpy(b->err_ptrs.ptr, ptrs.data(), count * sizeof(uint32_t*), cudaMemcpyHostToDevice));
+  return RPCA_OK;
+}
+
+// A grouped run: after the caller's queued work; the caller's stream waits
+// for it.  False when the layout of A needs the per-problem form.
+bool batch_grouped_run(rpca_batch* b, const rpca_matrix* A, void* const* U, const int64_t* ldu, double* const* S,
+                       void* const* V, const int64_t* ldv, rpca_status* st) {
+  RPCA_CUDA_TRY(cudaEventRecord(b->ev_in, b->caller));
+  RPCA_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+  if (!rpca::grp::grouped_run(b->grp, A, U, ldu, S, V, ldv, b->origin)) return false;
+  RPCA_CUDA_TRY(cudaEventRecord(b->ev_out, b->origin));
+  RPCA_CUDA_TRY(cudaStreamWaitEvent(b->caller, b->ev_out, 0));
+  *st = rpca::grp::grouped_check(b->grp, b->origin, &b->bad, &b->last_error);
+  return true;
+}
+
+// ----------------------------------------------------------- autotuner
+// Cache file: {"rpca_batch_tuning": {"<key>": [h, t, trows, rrows], ...}}
+std::string tune_key(const rpca_batch* b) {
+  int64_t maxn = 0;
+  double meanm = 0.0;
+  for (const auto& q : b->problems) {
+    maxn = std::max<int64_t>(maxn, q.n);
+    meanm += (double)q.m;
+  }
+  meanm /= (double)b->problems.size();
+  auto bucket = [](double v) {
+    int64_t e = 1;
+    while ((double)e < v) e <<= 1;
+    return e;
+  };
+  const rpca_problem& q = b->problems[0];
+  return "bf16/n" + std::to_string(bucket((double)maxn)) + "/m" + std::to_string(bucket(meanm)) + "/k" +
+         std::to_string(q.k) + "/l" + std::to_string(q.l) + "/i" + std::to_string(q.i);
+}
+
+std::vector<std::pair<std::string, std::vector<int>>> read_tune_cache(const char* path) {
+  std::vector<std::pair<std::string, std::vector<int>>> out;
+  if (!path) return out;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return out;
+  std::string t;
+  char buf[4096];
+  size_t r;
+  while ((r = std::fread(buf, 1, sizeof buf, f)) > 0) t.append(buf, r);
+  std::fclose(f);
+  const size_t top = t.find("\"rpca_batch_tuning\"");
+  if (top == std::string::npos) return out;
+  size_t pos = t.find('{', top);
+  while (pos != std::string::npos) {
+    const size_t k0 = t.find('"', pos + 1);
+    if (k0 == std::string::npos) break;
+    const size_t k1 = t.find('"', k0 + 1);
+    const size_t a0 = t.find('[', k1);
+    const size_t a1 = t.find(']', a0);
+    if (k1 == std::string::npos || a0 == std::string::npos || a1 == std::string::npos) break;
+    std::vector<int> v;
+    const char* c = t.c_str() + a0 + 1;
+    while (c < t.c_str() + a1) {
+      char* e = nullptr;
+      const long x = std::strtol(c, &e, 10);
+      if (e == c) {
+        ++c;
+        continue;
+      }
+      v.push_back((int)x);
+      c = e;
+    }
+    if (v.size() == 4) out.emplace_back(t.substr(k0 + 1, k1 - k0 - 1), v);
+    pos = t.find(',', a1);
+    if (pos == std::string::npos || t.find('"', pos) == std::string::npos) break;
+  }
+  return out;
+}
+
+void write_tune_cache(const char* path, const std::vector<std::pair<std::string, std::vector<int>>>& e) {
+  if (!path) return;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) throw Invalid(std::string("cannot write the tuning cache ") + path);
+  std::fprintf(f, "{\"rpca_batch_tuning\": {");
+  for (size_t i = 0; i < e.size(); ++i)
+    std::fprintf(f, "%s\n  \"%s\": [%d, %d, %d, %d]", i ? "," : "", e[i].first.c_str(), e[i].second[0],
+                 e[i].second[1], e[i].second[2], e[i].second[3]);
+  std::fprintf(f, "\n}}\n");
+  std::fclose(f);
+}
+
+rpca_status batch_tune(rpca_batch* b, const rpca_matrix* A, void* const* U, const int64_t* ldu, double* const* S,
+                       void* const* V, const int64_t* ldv, const char* path) {
+  const std::string key = tune_key(b);
+  auto cache = read_tune_cache(path);
+  for (const auto& e : cache)
+    if (e.first == key) {
+      rpca::grp::Tuning v{e.second[0], e.second[1], e.second[2], e.second[3]};
+      rpca::grp::grouped_set_tuning(b->grp, v);
+      rpca_status st = RPCA_OK;
+      if (!batch_grouped_run(b, A, U, ldu, S, V, ldv, &st)) throw Invalid("the matrices' layout needs the per-problem form");
+      return st;
+    }
+  cudaEvent_t e0, e1;
+  RPCA_CUDA_TRY(cudaEventCreate(&e0));
+  RPCA_CUDA_TRY(cudaEventCreate(&e1));
+  auto time_one = [&](const rpca::grp::Tuning& v, float* ms) -> rpca_status {
+    rpca::grp::grouped_set_tuning(b->grp, v);
+    rpca_status st = RPCA_OK;
+    if (!batch_grouped_run(b, A, U, ldu, S, V, ldv, &st)) throw Invalid("the matrices' layout needs the per-problem form");
+    if (st != RPCA_OK) return st;
+    RPCA_CUDA_TRY(cudaEventRecord(e0, b->origin));
+    if (!rpca::grp::grouped_run(b->grp, A, U, ldu, S, V, ldv, b->origin)) throw Invalid("layout");
+    RPCA_CUDA_TRY(cudaEventRecord(e1, b->origin));
+    st = rpca::grp::grouped_check(b->grp, b->origin, &b->bad, &b->last_error);
+    RPCA_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return st;
+  };
+  rpca::grp::Tuning best = rpca::grp::grouped_tuning(b->grp);
+  float best_ms = 0.f;
+  rpca_status st = time_one(best, &best_ms);
+  const int cand[4][3] = {{4, 6, 8}, {4, 6, 8}, {2048, 4096, 8192}, {1024, 2048, 4096}};
+  for (int d = 0; d < 4 && st == RPCA_OK; ++d)
+    for (int c = 0; c < 3 && st == RPCA_OK; ++c) {
+      rpca::grp::Tuning v = best;
+      int* f[4] = {&v.h_stages, &v.t_stages, &v.t_rows, &v.r_rows};
+      if (*f[d] == cand[d][c]) continue;
+      *f[d] = cand[d][c];
+      float ms = 0.f;
+      st = time_one(v, &ms);
+      if (st == RPCA_OK && ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != RPCA_OK) return st;
+  rpca::grp::grouped_set_tuning(b->grp, best);
+  st = RPCA_OK;
+  batch_grouped_run(b, A, U, ldu, S, V, ldv, &st);
+  if (st == RPCA_OK && path) {
+    cache.emplace_back(key, std::vector<int>{best.h_stages, best.t_stages, best.t_rows, best.r_rows});
+    write_tune_cache(path, cache);
+  }
+  return st;
 }
 
 rpca_status batch_check(rpca_batch* b) {
@@ -1351,37 +1534,30 @@ rpca_status rpca_batch_init(rpca_batch** out, int32_t count, const rpca_problem*
     for (int32_t p = 0; p < count; ++p) {
       if (problems[p].flags & RPCA_HOST_A) throw Invalid("batched problems take device matrices");
       if (problems[p].flags & RPCA_TIMING) throw Invalid("batched problems are not timed per phase");
+      try {
+        validate(&problems[p]);
+      } catch (const Invalid& e) {
+        throw Invalid("problem " + std::to_string(p) + ": " + e.what);
+      }
     }
     b->caller = static_cast<cudaStream_t>(problems[0].stream);
+    b->problems.assign(problems, problems + count);
+    b->nstreams = nstreams;
     RPCA_CUDA_TRY(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
     RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
-    const int ns = std::min<int32_t>(nstreams, count);
-    b->streams.assign(ns, nullptr);
-    b->ev_join.assign(ns, nullptr);
-    for (int i = 0; i < ns; ++i) {
-      RPCA_CUDA_TRY(cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking));
-      RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming));
-    }
-    RPCA_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
-    std::vector<const uint32_t*> ptrs(count);
-    for (int32_t p = 0; p < count; ++p) {
-      rpca_problem q = problems[p];
-      q.stream = b->streams[p % ns];
-      rpca_ctx* c = new rpca_ctx();
-      b->ctx.push_back(c);
-      rpca_status si = guarded(c, [&] { return do_init(c, &q); });
-      if (si != RPCA_OK) {
-        b->last_error = "problem " + std::to_string(p) + ": " + c->last_error;
-        return si;
+    if (rpca::grp::grouped_eligible(count, problems, nullptr)) {
+      std::vector<std::vector<double>> G(count);
+      for (int32_t p = 0; p < count; ++p) {
+        G[p].resize((size_t)problems[p].n * problems[p].l);
+        if (problems[p].G) std::memcpy(G[p].data(), problems[p].G, G[p].size() * sizeof(double));
+        else gaussian_stream(problems[p].seed, 0u, (int64_t)G[p].size(), G[p].data());
       }
-      ptrs[p] = c->err.as<uint32_t>();
+      b->grp = rpca::grp::grouped_create(count, problems, G, b->origin);
+      b->last_grouped = true;
+      return RPCA_OK;
     }
-    b->err_ptrs.alloc(count * sizeof(uint32_t*));
-    b->flags.alloc(count * sizeof(uint32_t));
-    b->host_flags.assign(count, 0u);
-    RPCA_CUDA_TRY(cudaMemcpy(b->err_ptrs.ptr, ptrs.data(), count * sizeof(uint32_t*), cudaMemcpyHostToDevice));
-    return RPCA_OK;
+    return batch_make_contexts(b);
   });
   if (s != RPCA_OK) {
     last_batch_error() = b->last_error;
@@ -1396,6 +1572,18 @@ rpca_status rpca_batch_run(rpca_batch* b, const rpca_matrix* A, void* const* U, 
                            double* const* S, void* const* V, const int64_t* ldv) {
   if (!b || !A) return RPCA_EINVAL;
   return bguarded(b, [&] {
+    if (b->grp) {
+      rpca_status gs = RPCA_OK;
+      if (batch_grouped_run(b, A, U, ldu, S, V, ldv, &gs)) {
+        b->last_grouped = true;
+        return gs;
+      }
+      if (b->ctx.empty()) {
+        rpca_status cs = batch_make_contexts(b);
+        if (cs != RPCA_OK) return cs;
+      }
+    }
+    b->last_grouped = false;
     const size_t count = b->ctx.size();
     std::vector<const void*> key;
     key.reserve(6 * count);
@@ -1449,6 +1637,7 @@ rpca_status rpca_batch_backward(rpca_batch* b, const rpca_matrix* A, const doubl
                                 const int64_t* ldda) {
   if (!b || !A || !dS || !dA || !ldda) return RPCA_EINVAL;
   return bguarded(b, [&] {
+    if (b->ctx.empty()) throw Invalid("the batch's problems were created without RPCA_ADJOINT");
     const size_t count = b->ctx.size();
     for (size_t p = 0; p < count; ++p)
       if (!b->ctx[p]->adjoint) throw Invalid("problem " + std::to_string(p) + " was created without RPCA_ADJOINT");
@@ -1481,6 +1670,42 @@ void rpca_batch_destroy(rpca_batch* b) {
 
 const char* rpca_batch_last_error(const rpca_batch* b) {
   return b ? b->last_error.c_str() : last_batch_error().c_str();
+}
+
+int32_t rpca_batch_grouped(const rpca_batch* b) { return (b && b->grp && b->last_grouped) ? 1 : 0; }
+
+rpca_status rpca_batch_get_tuning(const rpca_batch* b, int32_t* t) {
+  if (!b || !b->grp || !t) return RPCA_EINVAL;
+  const rpca::grp::Tuning v = rpca::grp::grouped_tuning(b->grp);
+  t[0] = v.h_stages;
+  t[1] = v.t_stages;
+  t[2] = v.t_rows;
+  t[3] = v.r_rows;
+  return RPCA_OK;
+}
+
+rpca_status rpca_batch_set_tuning(rpca_batch* b, const int32_t* t) {
+  if (!b || !b->grp || !t) return RPCA_EINVAL;
+  return bguarded(b, [&] {
+    rpca::grp::Tuning v;
+    v.h_stages = t[0];
+    v.t_stages = t[1];
+    v.t_rows = t[2];
+    v.r_rows = t[3];
+    rpca::grp::grouped_set_tuning(b->grp, v);
+    return RPCA_OK;
+  });
+}
+
+rpca_status rpca_batch_tune(rpca_batch* b, const rpca_matrix* A, void* const* U, const int64_t* ldu,
+                            double* const* S, void* const* V, const int64_t* ldv, const char* cache_path,
+                            int32_t* chosen) {
+  if (!b || !b->grp || !A) return RPCA_EINVAL;
+  return bguarded(b, [&] {
+    rpca_status st = batch_tune(b, A, U, ldu, S, V, ldv, cache_path);
+    if (st == RPCA_OK && chosen) rpca_batch_get_tuning(b, chosen);
+    return st;
+  });
 }
 
 const char* rpca_strerror(rpca_status s) {

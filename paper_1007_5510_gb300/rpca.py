@@ -18,13 +18,15 @@ STATUS = {0: "RPCA_OK", 1: "RPCA_MORE", -1: "RPCA_EINVAL", -2: "RPCA_ENOMEM", -3
           -4: "RPCA_ENODEV", -5: "RPCA_EBREAKDOWN", -6: "RPCA_ETIMEOUT", -7: "RPCA_ESTATE"}
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
 CENTER, HOST_A, SIMT, TIMING, ADJOINT, HOST_RESIDENT, KEEP_T_PASS = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20, 0x40
+NO_GROUPED = 0x80
 
 EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", "rpca_rerun",
            "rpca_strerror", "rpca_last_error", "rpca_op_fused_pass", "rpca_op_t_pass",
            "rpca_op_qr", "rpca_op_small_svd", "rpca_gaussian", "rpca_kernel_launches",
            "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc",
            "rpca_batch_init", "rpca_batch_run", "rpca_batch_destroy", "rpca_batch_last_error",
-           "rpca_backward", "rpca_test_arm_wait_expiry", "rpca_batch_backward", "rpca_last_run_passes"]
+           "rpca_backward", "rpca_test_arm_wait_expiry", "rpca_batch_backward", "rpca_last_run_passes",
+           "rpca_batch_grouped", "rpca_batch_get_tuning", "rpca_batch_set_tuning", "rpca_batch_tune"]
 
 
 class RpcaError(RuntimeError):
@@ -108,6 +110,16 @@ def load_library(path=None):
     lib.rpca_batch_destroy.restype = None
     lib.rpca_batch_last_error.argtypes = [vp]
     lib.rpca_batch_last_error.restype = ctypes.c_char_p
+    lib.rpca_batch_grouped.argtypes = [vp]
+    lib.rpca_batch_grouped.restype = i32
+    lib.rpca_batch_get_tuning.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.rpca_batch_get_tuning.restype = st
+    lib.rpca_batch_set_tuning.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.rpca_batch_set_tuning.restype = st
+    lib.rpca_batch_tune.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.c_char_p,
+                                    ctypes.POINTER(i32)]
+    lib.rpca_batch_tune.restype = st
     lib.rpca_batch_backward.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(i64)]
     lib.rpca_batch_backward.restype = st
@@ -387,26 +399,80 @@ def pca_autograd(A, k, l, i, seed=0):
 
 
 class Batch:
-    """Independent PCAs of uneven shapes run together (rpca_batch_*): one
-    context per problem over `nstreams` library streams; from the second run
-    with the same buffers on, one CUDA-graph launch per run."""
+    """Independent PCAs of uneven shapes run together (rpca_batch_*).  BF16
+    batches that fit the grouped kernels run every step as one launch over
+    all problems (`grouped`); others get one context per problem over
+    `nstreams` library streams, replayed as one CUDA graph from the second
+    run with the same buffers on."""
 
-    def __init__(self, shapes, k, l, i, dtype=BF16, seeds=None, nstreams=16, stream=None, adjoint=False):
-        """adjoint: every problem keeps what backward() needs (m >= n each)."""
+    def __init__(self, shapes, k, l, i, dtype=BF16, seeds=None, nstreams=16, stream=None, adjoint=False,
+                 grouped=True):
+        """adjoint: every problem keeps what backward() needs (m >= n each;
+        per-problem form).  grouped=False forces the per-problem form."""
         lib = load_library()
         self.shapes = [(int(m), int(n)) for m, n in shapes]
         self.k, self.dtype = k, dtype
         cnt = len(self.shapes)
         seeds = list(range(cnt)) if seeds is None else list(seeds)
         sp = _stream_ptr(stream)
+        flags = (ADJOINT if adjoint else 0) | (0 if grouped else NO_GROUPED)
         arr = (Problem * cnt)()
         for p, (m, n) in enumerate(self.shapes):
-            arr[p] = Problem(m, n, k, l, i, ctypes.c_uint64(seeds[p]), None, dtype, ADJOINT if adjoint else 0, 0, sp)
+            arr[p] = Problem(m, n, k, l, i, ctypes.c_uint64(seeds[p]), None, dtype, flags, 0, sp)
         self.ctx = ctypes.c_void_p()
         status = lib.rpca_batch_init(ctypes.byref(self.ctx), cnt, arr, nstreams)
         if status != OK:
             raise RpcaError(status, lib.rpca_batch_last_error(None).decode())
         self._keep = None
+
+    @property
+    def grouped(self):
+        """True if the last run (before any run: the batch) is grouped."""
+        return bool(load_library().rpca_batch_grouped(self.ctx))
+
+    @property
+    def tuning(self):
+        """(H-pass stages, T-pass stages, rows per T item, rows per row item)."""
+        t = (ctypes.c_int32 * 4)()
+        _check(load_library().rpca_batch_get_tuning(self.ctx, t))
+        return tuple(t)
+
+    @tuning.setter
+    def tuning(self, values):
+        t = (ctypes.c_int32 * 4)(*[int(v) for v in values])
+        _check(load_library().rpca_batch_set_tuning(self.ctx, t))
+
+    def tune(self, As, cache_path=None, outs=None):
+        """Autotunes the grouped kernels on these matrices (rpca_batch_tune;
+        cached in the JSON file cache_path) and returns the chosen tuning."""
+        outs, args = self._args(As, outs)
+        chosen = (ctypes.c_int32 * 4)()
+        path = None if cache_path is None else str(cache_path).encode()
+        status = load_library().rpca_batch_tune(self.ctx, *args, path, chosen)
+        if status != OK:
+            raise RpcaError(status, load_library().rpca_batch_last_error(self.ctx).decode())
+        return tuple(chosen)
+
+    def _args(self, As, outs):
+        torch = _torch()
+        cnt = len(self.shapes)
+        if len(As) != cnt:
+            raise ValueError("expected %d matrices, got %d" % (cnt, len(As)))
+        cdt = torch.float64 if self.dtype == F64 else torch.float32
+        if outs is None:
+            outs = [(torch.empty(m, self.k, dtype=cdt, device="cuda"), torch.empty(self.k, dtype=torch.float64, device="cuda"),
+                     torch.empty(n, self.k, dtype=cdt, device="cuda")) for m, n in self.shapes]
+        mats = (Matrix * cnt)()
+        for p, A in enumerate(As):
+            mats[p] = Matrix(ctypes.c_void_p(A.data_ptr()), A.stride(0), None)
+        vp = ctypes.c_void_p
+        U = (vp * cnt)(*[vp(o[0].data_ptr()) for o in outs])
+        S = (vp * cnt)(*[vp(o[1].data_ptr()) for o in outs])
+        V = (vp * cnt)(*[vp(o[2].data_ptr()) for o in outs])
+        ldu = (ctypes.c_int64 * cnt)(*[o[0].stride(0) for o in outs])
+        ldv = (ctypes.c_int64 * cnt)(*[o[2].stride(0) for o in outs])
+        self._keep = (mats, U, S, V, ldu, ldv)
+        return outs, (mats, U, ldu, S, V, ldv)
 
     def run(self, As, outs=None):
         """As: list of device tensors; returns [(U, S, V)] (allocated on the
