@@ -20,16 +20,18 @@ struct alignas(16) GrpProblem {
   int64_t m, n;
   int32_t n64;                  // round_up(n, 64)
   int32_t k;
-  float* H;                     // m x w FP32, ld w: H, then Q1 = H R1^-1
+  float* H;                     // m x wp FP32 (wp = w rounded up to 4): H, then Q1 = H R1^-1
   __nv_bfloat16* Z;             // m x 64 BF16
   __nv_bfloat16* XT0;           // X^(0)^T images (fixed per batch)
   __nv_bfloat16* XT;            // X^(j)^T images, j >= 1
   float* X;                     // n x w FP32, ld w
   float* F;                     // n x ldy_l FP32
-  float* T;                     // n x ldy_w FP32
+  float* T;                     // n x wp FP32
   double* G1;                   // w x w: H^T H, then R1 (upper)
   double* G2;                   // w x w: Q1^T Q1, then R2 (upper)
+  double* G3;                   // w x w: T1^T T1
   float* R1inv;                 // w x w FP32 (upper)
+  float* R2inv;                 // w x w FP32 (upper)
   float* MU;                    // w x k FP32
   float* U;                     // user m x k FP32 (ldu) or null
   float* V;                     // user n x k FP32 (ldv) or null
@@ -56,7 +58,7 @@ struct HPassArgs {
   const CUtensorMap* tmA;       // one map per problem (device array)
   int nstages;
   uint32_t xbytes;              // shared-memory bytes of the X^T images
-  int w, l, col0;               // H columns [col0, col0 + l)
+  int w, l, col0;               // H pitch (wp) and columns [col0, col0 + l)
   int write_z;                  // also write Z = bf16(H^(j))
   int xt_first;                 // read XT0 (j = 0) instead of XT
   uint32_t* err;
@@ -87,15 +89,21 @@ size_t tpass_smem(int nstages);
 void launch_orth(const GrpProblem* probs, int count, int j, int l, int w, int ldf, int max_n, uint32_t* err,
                  cudaStream_t st);
 // G1 += H^T H over the row items.
-void launch_gram(const GrpProblem* probs, const GrpRItem* items, int64_t nitems, int w, cudaStream_t st);
-// which = 1: G1 -> R1 (in place) and R1inv; which = 2: G2 -> R2 (in place).
+void launch_gram(const GrpProblem* probs, const GrpRItem* items, int64_t nitems, int w, uint32_t* err,
+                 cudaStream_t st);
+// which = 1: G1 -> R1 (in place) and R1inv; which = 2: G2 -> R2 and R2inv.
 void launch_chol(const GrpProblem* probs, int count, int w, int which, uint32_t* err, cudaStream_t st);
 // Q1 = H R1^-1 over H, Z = bf16(Q1), G2 += Q1^T Q1 over the row items.
-void launch_apply(const GrpProblem* probs, const GrpRItem* items, int64_t nitems, int w, cudaStream_t st);
-// Steps 4-6 on the n side: S, V and MU.
+void launch_apply(const GrpProblem* probs, const GrpRItem* items, int64_t nitems, int w, uint32_t* err,
+                  cudaStream_t st);
+// G3 += T1^T T1 over row items of the n side.
+void launch_gram_t(const GrpProblem* probs, const GrpRItem* items, int64_t nitems, int w, uint32_t* err,
+                   cudaStream_t st);
+// Steps 4-6 on the n side from G3: S, V and MU.
 void launch_svd(const GrpProblem* probs, int count, int w, int ldt, int max_n, uint32_t* err, cudaStream_t st);
 // U = Q1 MU over the row items.
-void launch_u(const GrpProblem* probs, const GrpRItem* items, int64_t nitems, int w, int k, cudaStream_t st);
+void launch_u(const GrpProblem* probs, const GrpRItem* items, int64_t nitems, int w, int k, uint32_t* err,
+              cudaStream_t st);
 
 }  // namespace grp
 }  // namespace rpca
@@ -111,7 +119,7 @@ namespace grp {
 
 // Launch parameters of the grouped kernels (the batch autotuner's knobs).
 struct Tuning {
-  int h_stages = 6;       // H pass TMA ring stages (16 KB each)
+  int h_stages = 8;       // H pass TMA ring stages (16 KB each)
   int t_stages = 8;       // T pass TMA ring stages (24 KB each)
   int t_rows = 4096;      // rows per T-pass item (multiple of 64)
   int r_rows = 2048;      // rows per row-kernel item

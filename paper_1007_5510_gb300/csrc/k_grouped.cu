@@ -11,11 +11,12 @@
 //                                       row range) items, FP32 reductions
 //   k_grp_orth    X^(j+1) = orth(F - X X^T F) (twice), Householder in
 //                 shared memory, one CTA per problem
-//   k_grp_gram    H^T H (FP32 register tiles, FP64 totals)
+//   k_grp_rows    H^T H, Q1 = H R1^-1, T1^T T1, U (FP32 register tiles,
+//                 FP64 Gram totals)
 //   k_grp_chol    Cholesky and triangular inverse (FP64), one CTA per problem
 //   k_grp_apply   Q1 = H R1^-1 rows (over H) -> bf16(Q1) and Q1^T Q1
-//   k_grp_svd     T = T1 R2^-1, Householder QR of T, one-sided Jacobi on R_T,
-//                 S and V, and M_U = R2^-1 W_k
+//   k_grp_eig     G_T = R2^-T (T1^T T1) R2^-1, its Cholesky factor R_T,
+//                 one-sided Jacobi on R_T, S and V, and M_U = R2^-1 W_k
 //   k_grp_u       U = Q1 M_U
 // Step 2 is a Cholesky QR of H repeated once on Q1 = H R1^-1 (CholQR2), but
 // the second factor R2 is never applied to the m-side data: T = A^T Q with
@@ -43,21 +44,11 @@ namespace rpca {
 namespace grp {
 
 // ------------------------------------------------------------- helpers
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          tc::smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
-      : "memory");
-}
-
 // Four FP32 reductions into 16-byte-aligned global memory.
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                : "memory");
 }
-
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // ======================================================= H pass (tcgen05)
 // H[:, j*l : j*l + l] = A X^(j) for every 128-row tile of every problem.
@@ -87,6 +78,7 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
+  if (__syncthreads_or((*(volatile uint32_t*)a.err & DEV_ERR_TIMEOUT) != 0)) return;   // an earlier step gave up
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t q0 = nitems * blockIdx.x / gridDim.x;
   const int64_t q1 = nitems * (blockIdx.x + 1) / gridDim.x;
@@ -129,7 +121,7 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
           const unsigned char* src = reinterpret_cast<const unsigned char*>(a.xt_first ? P.XT0 : P.XT);
           const uint32_t xb = (uint32_t)(P.n64 / 64) * HP_XCHUNK;
           tc::mbar_arrive_expect_tx(xfull, xb);
-          for (uint32_t off = 0; off < xb; off += HP_XCHUNK) bulk_load(xs + off, src + off, HP_XCHUNK, xfull);
+          for (uint32_t off = 0; off < xb; off += HP_XCHUNK) tc::bulk_load_1d(xs + off, src + off, HP_XCHUNK, xfull);
           ++nsw;
           prev = p;
         }
@@ -273,6 +265,7 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
+  if (__syncthreads_or((*(volatile uint32_t*)a.err & DEV_ERR_TIMEOUT) != 0)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t my_items = nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 

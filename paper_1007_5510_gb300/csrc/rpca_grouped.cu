@@ -4,6 +4,9 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -49,10 +52,10 @@ struct GroupedBatch {
   std::vector<GrpProblem> hp;
   std::vector<Slot> slot;
   std::vector<int64_t> m, n;
-  Mem dH, dZ, dXT0, dXT, dX, dAcc, dSmall, dProbs, dMaps, dHitems, dTF, dTT, dR, dErr;
+  Mem dH, dZ, dXT0, dXT, dX, dAcc, dSmall, dProbs, dMaps, dHitems, dTF, dTT, dR, dRT, dErr;
   size_t acc_bytes = 0;
   std::vector<CUtensorMap> maps;   // [0, count): A; [count, 2 count): Z
-  int64_t n_h = 0, n_tf = 0, n_tt = 0, n_r = 0;
+  int64_t n_h = 0, n_tf = 0, n_tt = 0, n_r = 0, n_rt = 0;
   std::vector<const void*> key;
   Tuning tune;
   std::vector<uint32_t> hflags;
@@ -81,7 +84,7 @@ bool grouped_eligible(int count, const rpca_problem* P, std::string* why) {
 static void build_items(GroupedBatch* g) {
   std::vector<int32_t> hp_, ht_;
   std::vector<GrpTItem> tf, tt;
-  std::vector<GrpRItem> ri;
+  std::vector<GrpRItem> ri, rt;
   const int sub_per_item = std::max(1, g->tune.t_rows / 64);
   for (int p = 0; p < g->count; ++p) {
     const int64_t m = g->m[p], n = g->n[p];
@@ -89,15 +92,19 @@ static void build_items(GroupedBatch* g) {
       hp_.push_back(p);
       ht_.push_back((int32_t)t);
     }
+    // (problem, row range, slab): the CTAs working at the same time on
+    // neighbouring items read the same rows of Z, which stay in L2
     const int nsub = (int)cdiv(m, 64);
-    for (int slab = 0; slab < (int)cdiv(n, 128); ++slab)
-      for (int s0 = 0; s0 < nsub; s0 += sub_per_item) {
+    for (int s0 = 0; s0 < nsub; s0 += sub_per_item)
+      for (int slab = 0; slab < (int)cdiv(n, 128); ++slab) {
         GrpTItem it{p, slab, s0, std::min(sub_per_item, nsub - s0)};
         tf.push_back(it);
         tt.push_back(it);
       }
     for (int64_t r0 = 0; r0 < m; r0 += g->tune.r_rows)
       ri.push_back(GrpRItem{p, (int32_t)r0, (int32_t)std::min<int64_t>(g->tune.r_rows, m - r0), 0});
+    for (int64_t r0 = 0; r0 < n; r0 += 256)
+      rt.push_back(GrpRItem{p, (int32_t)r0, (int32_t)std::min<int64_t>(256, n - r0), 0});
   }
   g->n_h = (int64_t)hp_.size();
   g->n_tf = (int64_t)tf.size();
@@ -113,6 +120,9 @@ static void build_items(GroupedBatch* g) {
   RPCA_CUDA_TRY(cudaMemcpy(g->dTT.ptr, tt.data(), g->n_tt * sizeof(GrpTItem), cudaMemcpyHostToDevice));
   g->dR.alloc(g->n_r * sizeof(GrpRItem));
   RPCA_CUDA_TRY(cudaMemcpy(g->dR.ptr, ri.data(), g->n_r * sizeof(GrpRItem), cudaMemcpyHostToDevice));
+  g->n_rt = (int64_t)rt.size();
+  g->dRT.alloc(g->n_rt * sizeof(GrpRItem));
+  RPCA_CUDA_TRY(cudaMemcpy(g->dRT.ptr, rt.data(), g->n_rt * sizeof(GrpRItem), cudaMemcpyHostToDevice));
 }
 
 GroupedBatch* grouped_create(int count, const rpca_problem* P, const std::vector<std::vector<double>>& G,
@@ -139,18 +149,19 @@ GroupedBatch* grouped_create(int count, const rpca_problem* P, const std::vector
       g->n[p] = n;
       g->max_n = std::max<int>(g->max_n, (int)n);
       Slot s;
-      s.h = oh;   oh = up(oh + (size_t)m * w * 4, 256);
+      s.h = oh;   oh = up(oh + (size_t)m * g->ldt * 4, 256);
       s.z = oz;   oz = up(oz + (size_t)m * 64 * 2, 1024);
       s.xt = oxt; oxt = up(oxt + (size_t)round_up(n, 64) * 32 * 2, 1024);
       s.x = ox;   ox = up(ox + (size_t)n * w * 4, 256);
       s.f = of;   of = up(of + (size_t)n * g->ldf * 4, 256);
       s.t = ot;   ot = up(ot + (size_t)n * g->ldt * 4, 256);
-      s.g = og;   og = up(og + 2 * w * w * 8, 256);
-      s.r = orr;  orr = up(orr + w * w * 4, 256);
+      s.g = og;   og = up(og + 3 * w * w * 8, 256);
+      s.r = orr;  orr = up(orr + 2 * w * w * 4, 256);
       s.mu = omu; omu = up(omu + w * g->k * 4, 256);
       g->slot[p] = s;
     }
     g->dH.alloc(oh);
+    RPCA_CUDA_TRY(cudaMemset(g->dH.ptr, 0, oh));   // the pitch's pad columns stay zero
     g->dZ.alloc(oz);
     g->dXT0.alloc(oxt);
     g->dXT.alloc(oxt);
@@ -179,7 +190,9 @@ GroupedBatch* grouped_create(int count, const rpca_problem* P, const std::vector
       q.T = reinterpret_cast<float*>(acc + acc_t + s.t);
       q.G1 = reinterpret_cast<double*>(acc + acc_g + s.g);
       q.G2 = q.G1 + w * w;
+      q.G3 = q.G2 + w * w;
       q.R1inv = reinterpret_cast<float*>(g->dSmall.as<unsigned char>() + s.r);
+      q.R2inv = q.R1inv + w * w;
       q.MU = reinterpret_cast<float*>(g->dSmall.as<unsigned char>() + orr + s.mu);
       q.perr = perr + p;
     }
@@ -229,8 +242,9 @@ void grouped_set_tuning(GroupedBatch* g, const Tuning& t) {
 Tuning grouped_tuning(const GroupedBatch* g) { return g->tune; }
 
 int grouped_launches(const GroupedBatch* g) {
-  // per pass j < i: H, F, orth; then H, Gram, chol, apply, chol, T, svd, U
-  return 3 * g->i + 8;
+  // per pass j < i: H, F, orth; then H, Gram, chol, apply, chol, T,
+  // Gram of T, eig, U
+  return 3 * g->i + 9;
 }
 
 bool grouped_run(GroupedBatch* g, const rpca_matrix* A, void* const* U, const int64_t* ldu, double* const* S,
@@ -276,24 +290,60 @@ bool grouped_run(GroupedBatch* g, const rpca_matrix* A, void* const* U, const in
   const int32_t* it = ip + g->n_h;
   RPCA_CUDA_TRY(cudaMemsetAsync(g->dAcc.ptr, 0, g->acc_bytes, st));
   RPCA_CUDA_TRY(cudaMemsetAsync(err, 0, 4 * sizeof(uint32_t), st));
+  // RPCA_GROUPED_TRACE=1: wait for each launch and report it on stderr; a
+  // launch still running after 30 s ends the process (its kernels with it)
+  static const bool trace = std::getenv("RPCA_GROUPED_TRACE") != nullptr;
+  auto step = [&](const char* name) {
+    if (!trace) return;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      const cudaError_t q = cudaStreamQuery(st);
+      const double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (q == cudaSuccess) {
+        std::fprintf(stderr, "grouped trace: %s %.3f ms\n", name, 1e3 * s);
+        return;
+      }
+      if (q != cudaErrorNotReady) {
+        std::fprintf(stderr, "grouped trace: %s failed: %s\n", name, cudaGetErrorString(q));
+        std::abort();
+      }
+      if (s > 30.0) {
+        std::fprintf(stderr, "grouped trace: %s still running after 30 s\n", name);
+        std::fflush(stderr);
+        std::abort();
+      }
+    }
+  };
   const uint32_t xbytes = (uint32_t)(round_up(g->max_n, 64) / 64) * 32 * 128;
   for (int j = 0; j <= g->i; ++j) {
-    HPassArgs h{mA, g->tune.h_stages, xbytes, g->w, g->l, j * g->l, j < g->i ? 1 : 0, j == 0 ? 1 : 0, err};
+    HPassArgs h{mA, g->tune.h_stages, xbytes, g->ldt, g->l, j * g->l, j < g->i ? 1 : 0, j == 0 ? 1 : 0, err};
     launch_hpass(probs, ip, it, g->n_h, h, g->sms, st);
+    step("h pass");
     if (j < g->i) {
       TPassArgs t{mA, mZ, g->tune.t_stages, (int)round_up(g->l, 16), g->l, g->ldf, 0, err};
       launch_tpass(probs, g->dTF.as<GrpTItem>(), g->n_tf, t, g->sms, st);
+      step("f pass");
       launch_orth(probs, count, j, g->l, g->w, g->ldf, g->max_n, err, st);
+      step("orth");
     }
   }
-  launch_gram(probs, g->dR.as<GrpRItem>(), g->n_r, g->w, st);
+  launch_gram(probs, g->dR.as<GrpRItem>(), g->n_r, g->w, err, st);
+  step("gram of H");
   launch_chol(probs, count, g->w, 1, err, st);
-  launch_apply(probs, g->dR.as<GrpRItem>(), g->n_r, g->w, st);
+  step("chol 1");
+  launch_apply(probs, g->dR.as<GrpRItem>(), g->n_r, g->w, err, st);
+  step("apply");
   launch_chol(probs, count, g->w, 2, err, st);
+  step("chol 2");
   TPassArgs t{mA, mZ, g->tune.t_stages, (int)round_up(g->w, 16), g->w, g->ldt, 1, err};
   launch_tpass(probs, g->dTT.as<GrpTItem>(), g->n_tt, t, g->sms, st);
+  step("t pass");
+  launch_gram_t(probs, g->dRT.as<GrpRItem>(), g->n_rt, g->w, err, st);
+  step("gram of T");
   launch_svd(probs, count, g->w, g->ldt, g->max_n, err, st);
-  launch_u(probs, g->dR.as<GrpRItem>(), g->n_r, g->w, g->k, st);
+  step("eig");
+  launch_u(probs, g->dR.as<GrpRItem>(), g->n_r, g->w, g->k, err, st);
+  step("u");
   return true;
 }
 

@@ -46,6 +46,8 @@ def _check(rpca, shapes, outs, Ao, k, l, i, seeds, label):
         U, S, V = outs[p]
         s = S.cpu().numpy()
         Uh, Vh = U.cpu().double().numpy(), V.cpu().double().numpy()
+        # cheap checks first: a non-finite output must not reach LAPACK
+        assert np.isfinite(s).all() and np.isfinite(Uh).all() and np.isfinite(Vh).all(), (label, p)
         Uo, So, Vo = ro.rpca(Ao[p], k, l, i, seed=seeds[p], reorth=True)
         rel = float(np.max(np.abs(s - So) / So))
         au = est.max_principal_angle(Uh, Uo)
@@ -105,6 +107,7 @@ def test_grouped_matches_per_problem_form():
         assert g.grouped and not pp.grouped
         for p in range(len(shapes)):
             sg, sp = og[p][1].cpu().numpy(), op[p][1].cpu().numpy()
+            assert np.isfinite(sg).all() and np.isfinite(og[p][0].cpu().numpy()).all(), p
             assert np.max(np.abs(sg - sp) / sp) < 1e-3, p
             assert est.max_principal_angle(og[p][0].cpu().double().numpy(),
                                            op[p][0].cpu().double().numpy()) < A_TOL, p
