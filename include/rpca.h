@@ -289,7 +289,7 @@ rpca_status rpca_batch_init(rpca_batch** out, int32_t count,
 int32_t rpca_batch_grouped(const rpca_batch* b);
 
 /* Launch parameters of the grouped kernels: tuning[0] H-pass TMA stages
- * (2..8), [1] T-pass stages (2..8), [2] rows per T-pass work item,
+ * (2..8), [1] T-pass stages (2..5), [2] rows per T-pass work item,
  * [3] rows per row-kernel item (multiples of 64).  Get and set copy 4
  * int32 values (host); set clamps them to their ranges.  RPCA_EINVAL for a
  * per-problem batch or NULL arguments. */

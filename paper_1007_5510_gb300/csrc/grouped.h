@@ -40,10 +40,9 @@ struct alignas(16) GrpProblem {
   uint32_t* perr;               // this problem's error word
 };
 
-// T-pass work item: problem, 128-column slab, 64-row sub-panels
-// [sub0, sub0 + nsub).
+// T-pass work item: problem p, 64-row groups [sub0, sub0 + nsub).
 struct GrpTItem {
-  int32_t p, slab, sub0, nsub;
+  int32_t p, sub0, nsub, pad;
 };
 
 // Row-range work item of the SIMT kernels over the m side.
@@ -65,9 +64,10 @@ struct HPassArgs {
 };
 
 struct TPassArgs {
-  const CUtensorMap* tmA;
-  const CUtensorMap* tmZ;
+  const CUtensorMap* tmA;       // box 64 rows x 64 columns
+  const CUtensorMap* tmZ;       // box 64 rows x 64 columns
   int nstages;
+  int tmem_cols;                // power of two >= ntile_max * npad
   int npad;                     // MMA N (multiple of 16, <= 64)
   int ncols;                    // columns of Y that receive sums
   int ldy;
@@ -120,7 +120,7 @@ namespace grp {
 // Launch parameters of the grouped kernels (the batch autotuner's knobs).
 struct Tuning {
   int h_stages = 8;       // H pass TMA ring stages (16 KB each)
-  int t_stages = 8;       // T pass TMA ring stages (24 KB each)
+  int t_stages = 5;       // T pass TMA ring stages (40 KB each)
   int t_rows = 4096;      // rows per T-pass item (multiple of 64)
   int r_rows = 2048;      // rows per row-kernel item
 };

@@ -7,8 +7,8 @@
 // single-problem path):
 //   k_grp_hpass   H^(j) = A X^(j)       tcgen05, persistent, 128-row tiles
 //   k_grp_tpass   F = A^T bf16(H^(j)),  T = A^T bf16(Q1)
-//                                       tcgen05, (problem, 128-column slab,
-//                                       row range) items, FP32 reductions
+//                                       tcgen05, (problem, row range) items
+//                                       over all columns, FP32 reductions
 //   k_grp_orth    X^(j+1) = orth(F - X X^T F) (twice), Householder in
 //                 shared memory, one CTA per problem
 //   k_grp_rows    H^T H, Q1 = H R1^-1, T1^T T1, U (FP32 register tiles,
@@ -44,6 +44,19 @@ namespace rpca {
 namespace grp {
 
 // ------------------------------------------------------------- helpers
+// Named barrier 1 over the four epilogue warps (128 threads).
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool epi_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 128, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
 // Four FP32 reductions into 16-byte-aligned global memory.
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
@@ -59,6 +72,8 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 constexpr int HP_THREADS = 192;
 constexpr uint32_t HP_STAGE = 128 * 128;     // 128 rows x 64 BF16
 constexpr uint32_t HP_XCHUNK = 32 * 128;     // 32 rows x 64 BF16
+constexpr uint32_t HP_ZSTAGE = 128 * 128;    // epilogue staging of 128 Z rows
+constexpr int HP_HPITCH = 33;                // odd pitch (floats) of the H staging rows (l <= 32)
 
 __global__ void __launch_bounds__(HP_THREADS, 1)
 k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ item_p,
@@ -68,7 +83,9 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* xs = smem;                                        // X^T images (a.xbytes)
   unsigned char* ring = xs + a.xbytes;                             // nstages x HP_STAGE
-  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)a.nstages * HP_STAGE);
+  unsigned char* zst = ring + (size_t)a.nstages * HP_STAGE;        // 128 x 128 B: Z rows (swizzled)
+  float* hst = reinterpret_cast<float*>(zst + HP_ZSTAGE);          // 128 x (l | 1): H rows
+  uint64_t* full = reinterpret_cast<uint64_t*>(hst + 128 * HP_HPITCH);
   uint64_t* empty = full + a.nstages;
   uint64_t* tfull = empty + a.nstages;   // [2]
   uint64_t* tfree = tfull + 2;           // [2]
@@ -188,13 +205,17 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // tile rows -> shared staging (thread = row), then coalesced stores of
+    // the valid rows by all four warps
     const int quad = warp & 3;
     const int row = quad * 32 + lane;   // tile row = TMEM lane
+    const int et = tid - 64;            // 0..127
     int64_t ti = 0;
     for (int64_t q = q0; q < q1; ++q, ++ti) {
       const int b = (int)(ti & 1);
       bool ok = tc::mbar_wait(&tfull[b], (uint32_t)((ti >> 1) & 1), a.err, abort_flag);
       ok = __all_sync(0xffffffffu, ok);
+      ok = epi_bar_and(ok);
       if (!ok) break;
       tc::tc_fence_after();
       float v[32];
@@ -204,30 +225,39 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tfree[b]);
-      const GrpProblem& P = probs[item_p[q]];
-      const int64_t grow = (int64_t)item_t[q] * 128 + row;
-      if (grow < P.m) {
-        float* h = P.H + grow * a.w + a.col0;
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c < a.l) h[c] = v[c];
-        if (a.write_z) {
-          uint4* z = reinterpret_cast<uint4*>(P.Z + grow * 64);
+      for (int c = 0; c < 32; ++c)
+        if (c < a.l) hst[row * HP_HPITCH + c] = v[c];
+      if (a.write_z) {
 #pragma unroll
-          for (int g = 0; g < 8; ++g) {
-            uint32_t wd[4];
+        for (int g = 0; g < 8; ++g) {
+          uint32_t wd[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int c = 8 * g + 2 * e;   // l <= 32: columns past 31 are zero
-              const float x0 = (c < a.l) ? v[c & 31] : 0.f;
-              const float x1 = (c + 1 < a.l) ? v[(c + 1) & 31] : 0.f;
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-              wd[e] = *reinterpret_cast<uint32_t*>(&h2);
-            }
-            z[g] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+          for (int e = 0; e < 4; ++e) {
+            const int c = 8 * g + 2 * e;   // l <= 32: columns past 31 are zero
+            const float x0 = (c < a.l) ? v[c & 31] : 0.f;
+            const float x1 = (c + 1 < a.l) ? v[(c + 1) & 31] : 0.f;
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+            wd[e] = *reinterpret_cast<uint32_t*>(&h2);
           }
+          *reinterpret_cast<uint4*>(zst + row * 128 + ((g ^ (row & 7)) << 4)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
         }
       }
+      epi_bar();
+      const GrpProblem& P = probs[item_p[q]];
+      const int64_t row0 = (int64_t)item_t[q] * 128;
+      const int nr = (int)(P.m - row0 < 128 ? P.m - row0 : 128);
+      for (int e = et; e < nr * a.l; e += 128) {
+        const int r = e / a.l, c = e % a.l;
+        P.H[(row0 + r) * a.w + a.col0 + c] = hst[r * HP_HPITCH + c];
+      }
+      if (a.write_z)
+        for (int e = et; e < nr * 8; e += 128) {
+          const int r = e >> 3, g = e & 7;
+          reinterpret_cast<uint4*>(P.Z + (row0 + r) * 64)[g] =
+              *reinterpret_cast<const uint4*>(zst + r * 128 + ((g ^ (r & 7)) << 4));
+        }
+      epi_bar();   // the staging is free for the next tile
     }
   }
   // every MMA of this CTA has completed before TMEM is released
@@ -241,15 +271,21 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
 }
 
 // ================================================== T / F pass (tcgen05)
-// Y_p[slab rows, 0:N] += A_p[rows, slab]^T Z_p[rows, 0:N] for every item
-// (problem, 128-column slab, range of 64-row sub-panels).  A^T and Z are
-// MN-major operands (M = slab columns, N = Z columns, K = rows), as in the
-// single-problem T pass.  The item's partial sum lives in one of two TMEM
-// accumulators; the epilogue adds it to Y with vector FP32 reductions while
-// the next item accumulates in the other.
+// Y_p[:, 0:N] += A_p[rows, :]^T Z_p[rows, 0:N] for every item (problem,
+// range of 64-row groups), all of the problem's columns: A^T and Z are
+// MN-major operands (M = 128 columns of A per tile, N = Z columns, K = rows),
+// the ntile = ceil(n / 128) tile accumulators live in tensor memory for the
+// whole item, and the epilogue adds them to Y with vector FP32 reductions.
+//
+// A stage is the Z box of a 64-row group plus the A boxes (64 rows x 64
+// columns, 8 KB) of up to TPG_TPS column tiles of that group; a wide
+// problem's group spans several consecutive stages, which load its Z box
+// again (from L2, just read).  Each row of A is read once from memory, and
+// so is each row of Z.
 constexpr int TPG_THREADS = 192;
-constexpr uint32_t TPG_ABOX = 64 * 128;            // 64 rows x 64 BF16
-constexpr uint32_t TPG_STAGE = 3 * TPG_ABOX;       // two A boxes + one Z box
+constexpr uint32_t TPG_BOX = 64 * 128;          // 64 rows x 64 BF16
+constexpr int TPG_TPS = 2;
+constexpr uint32_t TPG_STAGE = (1 + 2 * TPG_TPS) * TPG_BOX;
 
 __global__ void __launch_bounds__(TPG_THREADS, 1)
 k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ items, int64_t nitems,
@@ -257,15 +293,15 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  if (__syncthreads_or((*(volatile uint32_t*)a.err & DEV_ERR_TIMEOUT) != 0)) return;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)a.nstages * TPG_STAGE);
   uint64_t* empty = full + a.nstages;
-  uint64_t* tfull = empty + a.nstages;   // [2]
-  uint64_t* tfree = tfull + 2;           // [2]
-  uint64_t* done = tfree + 2;
+  uint64_t* tfull = empty + a.nstages;
+  uint64_t* tfree = tfull + 1;
+  uint64_t* done = tfree + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-  if (__syncthreads_or((*(volatile uint32_t*)a.err & DEV_ERR_TIMEOUT) != 0)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t my_items = nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
@@ -274,16 +310,14 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&tfull[b], 1);
-      tc::mbar_init(&tfree[b], 4);
-    }
+    tc::mbar_init(tfull, 1);
+    tc::mbar_init(tfree, 4);
     tc::mbar_init(done, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, 128);
+    tc::tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
     tc::tmem_relinquish();
   }
   tc::tc_fence_before();
@@ -298,20 +332,24 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
       bool ok = true;
       for (int64_t qi = 0; qi < my_items && ok; ++qi) {
         const GrpTItem I = items[blockIdx.x + qi * gridDim.x];
+        const int ntile = (int)((probs[I.p].n + 127) / 128);
         const CUtensorMap* tA = &a.tmA[I.p];
         const CUtensorMap* tZ = &a.tmZ[I.p];
-        for (int sb = 0; sb < I.nsub; ++sb, ++it) {
-          const int s = (int)(it % a.nstages);
-          if (!tc::mbar_wait(&empty[s], (uint32_t)(((it / a.nstages) & 1) ^ 1), a.err, abort_flag)) {
-            ok = false;
-            break;
+        for (int gr = 0; gr < I.nsub && ok; ++gr) {
+          const int32_t r0 = (I.sub0 + gr) * 64;
+          for (int t0 = 0; t0 < ntile; t0 += TPG_TPS, ++it) {
+            const int nt = min(TPG_TPS, ntile - t0);
+            const int s = (int)(it % a.nstages);
+            if (!tc::mbar_wait(&empty[s], (uint32_t)(((it / a.nstages) & 1) ^ 1), a.err, abort_flag)) {
+              ok = false;
+              break;
+            }
+            unsigned char* st = smem + (size_t)s * TPG_STAGE;
+            tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(1 + 2 * nt) * TPG_BOX);
+            tc::tma_load_2d(st, tZ, &full[s], 0, r0);
+            for (int bx = 0; bx < 2 * nt; ++bx)
+              tc::tma_load_2d(st + (size_t)(1 + bx) * TPG_BOX, tA, &full[s], 128 * t0 + 64 * bx, r0);
           }
-          unsigned char* st = smem + (size_t)s * TPG_STAGE;
-          const int32_t r0 = (I.sub0 + sb) * 64;
-          tc::mbar_arrive_expect_tx(&full[s], TPG_STAGE);
-          tc::tma_load_2d(st, tA, &full[s], I.slab * 128, r0);
-          tc::tma_load_2d(st + TPG_ABOX, tA, &full[s], I.slab * 128 + 64, r0);
-          tc::tma_load_2d(st + 2 * TPG_ABOX, tZ, &full[s], 0, r0);
         }
       }
       volatile int never = 0;
@@ -325,28 +363,33 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
       int64_t it = 0;
       bool ok = true;
       for (int64_t qi = 0; qi < my_items && ok; ++qi) {
-        const int nsub = items[blockIdx.x + qi * gridDim.x].nsub;
-        const int b = (int)(qi & 1);
-        if (!tc::mbar_wait(&tfree[b], (uint32_t)(((qi >> 1) & 1) ^ 1), a.err, abort_flag)) break;
+        const GrpTItem I = items[blockIdx.x + qi * gridDim.x];
+        const int ntile = (int)((probs[I.p].n + 127) / 128);
+        if (!tc::mbar_wait(tfree, (uint32_t)((qi & 1) ^ 1), a.err, abort_flag)) break;
         tc::tc_fence_after();
-        for (int sb = 0; sb < nsub; ++sb, ++it) {
-          const int s = (int)(it % a.nstages);
-          if (!tc::mbar_wait(&full[s], (uint32_t)((it / a.nstages) & 1), a.err, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc::tc_fence_after();
-          const uint32_t sa = tc::smem_u32(smem + (size_t)s * TPG_STAGE);
+        for (int gr = 0; gr < I.nsub && ok; ++gr) {
+          for (int t0 = 0; t0 < ntile; t0 += TPG_TPS, ++it) {
+            const int nt = min(TPG_TPS, ntile - t0);
+            const int s = (int)(it % a.nstages);
+            if (!tc::mbar_wait(&full[s], (uint32_t)((it / a.nstages) & 1), a.err, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+            const uint32_t sa = tc::smem_u32(smem + (size_t)s * TPG_STAGE);
+            for (int tt = 0; tt < nt; ++tt) {
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = tc::sdesc_sw128(sa + kk * 2048, TPG_ABOX, 1024);
-            const uint64_t bd = tc::sdesc_sw128(sa + 2 * TPG_ABOX + kk * 2048, TPG_ABOX, 1024);
-            tc::mma_f16(tmem + (uint32_t)b * 64u, ad, bd, idesc, (sb > 0 || kk > 0) ? 1u : 0u);
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = tc::sdesc_sw128(sa + (uint32_t)(1 + 2 * tt) * TPG_BOX + kk * 2048, TPG_BOX, 1024);
+                const uint64_t bd = tc::sdesc_sw128(sa + kk * 2048, TPG_BOX, 1024);
+                tc::mma_f16(tmem + (uint32_t)((t0 + tt) * a.npad), ad, bd, idesc, (gr > 0 || kk > 0) ? 1u : 0u);
+              }
+            }
+            tc::mma_commit(&empty[s]);
           }
-          tc::mma_commit(&empty[s]);
         }
         if (!ok) break;
-        tc::mma_commit(&tfull[b]);
+        tc::mma_commit(tfull);
       }
       tc::mma_commit(done);
     }
@@ -355,27 +398,31 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
     const int quad = warp & 3;
     for (int64_t qi = 0; qi < my_items; ++qi) {
       const GrpTItem I = items[blockIdx.x + qi * gridDim.x];
-      const int b = (int)(qi & 1);
-      bool ok = tc::mbar_wait(&tfull[b], (uint32_t)((qi >> 1) & 1), a.err, abort_flag);
+      const GrpProblem& P = probs[I.p];
+      const int ntile = (int)((P.n + 127) / 128);
+      bool ok = tc::mbar_wait(tfull, (uint32_t)(qi & 1), a.err, abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc::tc_fence_after();
-      const GrpProblem& P = probs[I.p];
-      const int64_t row = (int64_t)I.slab * 128 + quad * 32 + lane;   // n-index of Y
-      float* y = (a.mode_t ? P.T : P.F) + row * a.ldy;
-      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * 64u;
-      for (int c16 = 0; c16 < a.npad; c16 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + c16, v);
-        if (row < P.n) {
+      float* ybase = a.mode_t ? P.T : P.F;
+      for (int t = 0; t < ntile; ++t) {
+        const int64_t row = (int64_t)t * 128 + quad * 32 + lane;   // n-index of Y
+        float* y = ybase + row * a.ldy;
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * a.npad);
+        for (int c16 = 0; c16 < a.npad; c16 += 16) {
+          float v[16];
+          tc::tmem_ld16(taddr + c16, v);
+          if (row < P.n) {
 #pragma unroll
-          for (int g = 0; g < 4; ++g)
-            if (c16 + 4 * g < a.ncols) red_add_v4(y + c16 + 4 * g, v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+            for (int g4 = 0; g4 < 4; ++g4)
+              if (c16 + 4 * g4 < a.ncols)
+                red_add_v4(y + c16 + 4 * g4, v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+          }
         }
       }
       tc::tc_fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&tfree[b]);
+      if (lane == 0) tc::mbar_arrive(tfree);
     }
   }
   if (warp == 1 && lane == 0) {
@@ -384,14 +431,14 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
 }
 
 // ------------------------------------------------------------- launchers
 size_t hpass_smem(uint32_t xbytes, int nstages) {
-  return 1024 + xbytes + (size_t)nstages * HP_STAGE + (2 * nstages + 7) * 8 + 16;
+  return 1024 + xbytes + (size_t)nstages * HP_STAGE + HP_ZSTAGE + 128 * HP_HPITCH * 4 + (2 * nstages + 7) * 8 + 16;
 }
-size_t tpass_smem(int nstages) { return 1024 + (size_t)nstages * TPG_STAGE + (2 * nstages + 5) * 8 + 16; }
+size_t tpass_smem(int nstages) { return 1024 + (size_t)nstages * TPG_STAGE + (2 * nstages + 3) * 8 + 16; }
 
 void launch_hpass(const GrpProblem* probs, const int32_t* item_p, const int32_t* item_t, int64_t nitems,
                   const HPassArgs& a, int grid, cudaStream_t st) {

@@ -1376,7 +1376,7 @@ rpca_status batch_tune(rpca_batch* b, const rpca_matrix* A, void* const* U, cons
   rpca::grp::Tuning best = rpca::grp::grouped_tuning(b->grp);
   float best_ms = 0.f;
   rpca_status st = time_one(best, &best_ms);
-  const int cand[4][3] = {{4, 6, 8}, {4, 6, 8}, {2048, 4096, 8192}, {1024, 2048, 4096}};
+  const int cand[4][3] = {{4, 6, 8}, {3, 4, 5}, {2048, 4096, 8192}, {1024, 2048, 4096}};
   for (int d = 0; d < 4 && st == RPCA_OK; ++d)
     for (int c = 0; c < 3 && st == RPCA_OK; ++c) {
       rpca::grp::Tuning v = best;

@@ -54,7 +54,7 @@ struct GroupedBatch {
   std::vector<int64_t> m, n;
   Mem dH, dZ, dXT0, dXT, dX, dAcc, dSmall, dProbs, dMaps, dHitems, dTF, dTT, dR, dRT, dErr;
   size_t acc_bytes = 0;
-  std::vector<CUtensorMap> maps;   // [0, count): A; [count, 2 count): Z
+  std::vector<CUtensorMap> maps;   // [0, count): A; [count, 2 count): Z (64 x 64 boxes)
   int64_t n_h = 0, n_tf = 0, n_tt = 0, n_r = 0, n_rt = 0;
   std::vector<const void*> key;
   Tuning tune;
@@ -92,15 +92,13 @@ static void build_items(GroupedBatch* g) {
       hp_.push_back(p);
       ht_.push_back((int32_t)t);
     }
-    // (problem, row range, slab): the CTAs working at the same time on
-    // neighbouring items read the same rows of Z, which stay in L2
+    // (problem, range of 64-row groups), all columns of A at once
     const int nsub = (int)cdiv(m, 64);
-    for (int s0 = 0; s0 < nsub; s0 += sub_per_item)
-      for (int slab = 0; slab < (int)cdiv(n, 128); ++slab) {
-        GrpTItem it{p, slab, s0, std::min(sub_per_item, nsub - s0)};
-        tf.push_back(it);
-        tt.push_back(it);
-      }
+    for (int s0 = 0; s0 < nsub; s0 += sub_per_item) {
+      GrpTItem it{p, s0, std::min(sub_per_item, nsub - s0), 0};
+      tf.push_back(it);
+      tt.push_back(it);
+    }
     for (int64_t r0 = 0; r0 < m; r0 += g->tune.r_rows)
       ri.push_back(GrpRItem{p, (int32_t)r0, (int32_t)std::min<int64_t>(g->tune.r_rows, m - r0), 0});
     for (int64_t r0 = 0; r0 < n; r0 += 256)
@@ -232,7 +230,7 @@ void grouped_destroy(GroupedBatch* g) { delete g; }
 void grouped_set_tuning(GroupedBatch* g, const Tuning& t) {
   Tuning v = t;
   v.h_stages = std::max(2, std::min(8, v.h_stages));
-  v.t_stages = std::max(2, std::min(8, v.t_stages));
+  v.t_stages = std::max(2, std::min(5, v.t_stages));
   v.t_rows = std::max(64, (int)round_up(std::min(v.t_rows, 1 << 20), 64));
   v.r_rows = std::max(64, (int)round_up(std::min(v.r_rows, 1 << 20), 64));
   const bool rebuild = v.t_rows != g->tune.t_rows || v.r_rows != g->tune.r_rows;
@@ -285,6 +283,12 @@ bool grouped_run(GroupedBatch* g, const rpca_matrix* A, void* const* U, const in
   const GrpProblem* probs = g->dProbs.as<GrpProblem>();
   const CUtensorMap* mA = g->dMaps.as<CUtensorMap>();
   const CUtensorMap* mZ = mA + count;
+  auto pow2 = [](int v) {
+    int c = 32;
+    while (c < v) c <<= 1;
+    return c;
+  };
+  const int ntile_max = (int)cdiv(g->max_n, 128);
   uint32_t* err = g->dErr.as<uint32_t>();
   const int32_t* ip = g->dHitems.as<int32_t>();
   const int32_t* it = ip + g->n_h;
@@ -320,7 +324,8 @@ bool grouped_run(GroupedBatch* g, const rpca_matrix* A, void* const* U, const in
     launch_hpass(probs, ip, it, g->n_h, h, g->sms, st);
     step("h pass");
     if (j < g->i) {
-      TPassArgs t{mA, mZ, g->tune.t_stages, (int)round_up(g->l, 16), g->l, g->ldf, 0, err};
+      const int npf = (int)round_up(g->l, 16);
+      TPassArgs t{mA, mZ, g->tune.t_stages, pow2(ntile_max * npf), npf, g->l, g->ldf, 0, err};
       launch_tpass(probs, g->dTF.as<GrpTItem>(), g->n_tf, t, g->sms, st);
       step("f pass");
       launch_orth(probs, count, j, g->l, g->w, g->ldf, g->max_n, err, st);
@@ -335,7 +340,8 @@ bool grouped_run(GroupedBatch* g, const rpca_matrix* A, void* const* U, const in
   step("apply");
   launch_chol(probs, count, g->w, 2, err, st);
   step("chol 2");
-  TPassArgs t{mA, mZ, g->tune.t_stages, (int)round_up(g->w, 16), g->w, g->ldt, 1, err};
+  const int npt = (int)round_up(g->w, 16);
+  TPassArgs t{mA, mZ, g->tune.t_stages, pow2(ntile_max * npt), npt, g->w, g->ldt, 1, err};
   launch_tpass(probs, g->dTT.as<GrpTItem>(), g->n_tt, t, g->sms, st);
   step("t pass");
   launch_gram_t(probs, g->dRT.as<GrpRItem>(), g->n_rt, g->w, err, st);
