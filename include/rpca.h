@@ -289,21 +289,22 @@ rpca_status rpca_batch_init(rpca_batch** out, int32_t count,
 int32_t rpca_batch_grouped(const rpca_batch* b);
 
 /* Launch parameters of the grouped kernels: tuning[0] H-pass TMA stages
- * (2..8), [1] T-pass stages (2..5), [2] rows per T-pass work item,
- * [3] rows per row-kernel item (multiples of 64).  Get and set copy 4
- * int32 values (host); set clamps them to their ranges.  RPCA_EINVAL for a
- * per-problem batch or NULL arguments. */
+ * (2..4), [1] T-pass stages (2..5), [2] rows per T-pass work item,
+ * [3] rows per row-kernel item (multiples of 64), [4] distance in ring
+ * stages of the H and T passes' L2 prefetches (0..64, 0: none).  Get and
+ * set copy 5 int32 values (host); set clamps them to their ranges.
+ * RPCA_EINVAL for a per-problem batch or NULL arguments. */
 rpca_status rpca_batch_get_tuning(const rpca_batch* b, int32_t* tuning);
 rpca_status rpca_batch_set_tuning(rpca_batch* b, const int32_t* tuning);
 
 /* Autotuner of the grouped kernels: times rpca_batch_run on these
  * arguments for a set of launch parameters (coordinate search over the
- * four values above, each candidate run twice and timed once with CUDA
+ * five values above, each candidate run twice and timed once with CUDA
  * events), keeps the fastest, and records it in the JSON file cache_path
  * (host path; NULL: no cache) under a key made of the storage type, the
  * power-of-two buckets of the largest n and of the mean m, k, l and i.  A
  * key already in the file is applied without timing.  The outputs are
- * written as by rpca_batch_run.  *chosen (4 values, may be NULL) receives
+ * written as by rpca_batch_run.  *chosen (5 values, may be NULL) receives
  * the parameters in use.  RPCA_EINVAL for a per-problem batch. */
 rpca_status rpca_batch_tune(rpca_batch* b, const rpca_matrix* A, void* const* U,
                             const int64_t* ldu, double* const* S, void* const* V,

@@ -60,6 +60,7 @@ struct HPassArgs {
   int w, l, col0;               // H pitch (wp) and columns [col0, col0 + l)
   int write_z;                  // also write Z = bf16(H^(j))
   int xt_first;                 // read XT0 (j = 0) instead of XT
+  int pf;                       // L2 prefetch distance in ring stages (0: none)
   uint32_t* err;
 };
 
@@ -72,6 +73,7 @@ struct TPassArgs {
   int ncols;                    // columns of Y that receive sums
   int ldy;
   int mode_t;                   // 0: Y = F, 1: Y = T
+  int pf;                       // L2 prefetch distance in ring stages (0: none)
   uint32_t* err;
 };
 
@@ -119,10 +121,11 @@ namespace grp {
 
 // Launch parameters of the grouped kernels (the batch autotuner's knobs).
 struct Tuning {
-  int h_stages = 8;       // H pass TMA ring stages (16 KB each)
+  int h_stages = 4;       // H pass TMA ring stages (32 KB each)
   int t_stages = 5;       // T pass TMA ring stages (40 KB each)
-  int t_rows = 4096;      // rows per T-pass item (multiple of 64)
+  int t_rows = 2048;      // rows per T-pass item (multiple of 64)
   int r_rows = 2048;      // rows per row-kernel item
+  int pf = 0;             // L2 prefetch distance of the H and T passes (stages; measured slower)
 };
 
 struct GroupedBatch;

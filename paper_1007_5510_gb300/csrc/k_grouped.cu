@@ -70,7 +70,9 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 // lane 0: MMA (M = 128, N = 32, K = 16 steps) into a double-buffered TMEM
 // accumulator; warps 2-5: epilogue (thread = tile row).
 constexpr int HP_THREADS = 192;
-constexpr uint32_t HP_STAGE = 128 * 128;     // 128 rows x 64 BF16
+constexpr int HP_KPS = 2;                    // 64-column steps per ring stage
+constexpr uint32_t HP_KCHUNK = 128 * 128;    // 128 rows x 64 BF16 (two 64-row boxes)
+constexpr uint32_t HP_STAGE = HP_KPS * HP_KCHUNK;   // 256 contiguous bytes of each row
 constexpr uint32_t HP_XCHUNK = 32 * 128;     // 32 rows x 64 BF16
 constexpr uint32_t HP_ZSTAGE = 128 * 128;    // epilogue staging of 128 Z rows
 constexpr int HP_HPITCH = 33;                // odd pitch (floats) of the H staging rows (l <= 32)
@@ -78,6 +80,7 @@ constexpr int HP_HPITCH = 33;                // odd pitch (floats) of the H stag
 __global__ void __launch_bounds__(HP_THREADS, 1)
 k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ item_p,
             const int32_t* __restrict__ item_t, int64_t nitems, HPassArgs a) {
+  // item_t[q]: row tile (low 24 bits) | 64-column steps of the problem (high 8)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -130,30 +133,59 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
       int prev = -1;
       int64_t it = 0, nsw = 0;   // ring stages issued, problem switches
       bool ok = true;
+      // L2 prefetch cursor a.pf stages ahead of the loads
+      int64_t pq = q0;
+      int pkb = 0;
+      auto prefetch_next = [&]() {
+        if (pq >= q1) return;
+        const int pp = item_p[pq];
+        const uint32_t pw = (uint32_t)item_t[pq];
+        const int32_t py = (int32_t)(pw & 0xffffffu) * 128;
+        tc::tma_prefetch_l2_2d(&a.tmA[pp], 64 * pkb, py);
+        tc::tma_prefetch_l2_2d(&a.tmA[pp], 64 * pkb, py + 64);
+        if (++pkb == (int)(pw >> 24)) {
+          pkb = 0;
+          ++pq;
+        }
+      };
+      for (int i = 0; i < a.pf; ++i) prefetch_next();
+      // item words read one tile ahead (their latency overlaps the tile)
+      int p_nx = q0 < q1 ? item_p[q0] : 0;
+      uint32_t t_nx = q0 < q1 ? (uint32_t)item_t[q0] : 0u;
       for (int64_t q = q0; q < q1 && ok; ++q) {
-        const int p = item_p[q];
-        const GrpProblem& P = probs[p];
+        const int p = p_nx;
+        const uint32_t tw = t_nx;
+        if (q + 1 < q1) {
+          p_nx = item_p[q + 1];
+          t_nx = (uint32_t)item_t[q + 1];
+        }
         if (p != prev) {
+          const GrpProblem& P = probs[p];
           if (nsw > 0 && !tc::mbar_wait(xfree, (uint32_t)((nsw - 1) & 1), a.err, abort_flag)) break;
           const unsigned char* src = reinterpret_cast<const unsigned char*>(a.xt_first ? P.XT0 : P.XT);
-          const uint32_t xb = (uint32_t)(P.n64 / 64) * HP_XCHUNK;
+          const uint32_t xb = (tw >> 24) * HP_XCHUNK;
           tc::mbar_arrive_expect_tx(xfull, xb);
           for (uint32_t off = 0; off < xb; off += HP_XCHUNK) tc::bulk_load_1d(xs + off, src + off, HP_XCHUNK, xfull);
           ++nsw;
           prev = p;
         }
-        const int32_t y0 = item_t[q] * 128;
-        const int nk = P.n64 / 64;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int32_t y0 = (int32_t)(tw & 0xffffffu) * 128;
+        const int nk = (int)(tw >> 24);
+        for (int kb0 = 0; kb0 < nk; kb0 += HP_KPS, ++it) {
+          const int nc = min(HP_KPS, nk - kb0);
           const int s = (int)(it % a.nstages);
           if (!tc::mbar_wait(&empty[s], (uint32_t)(((it / a.nstages) & 1) ^ 1), a.err, abort_flag)) {
             ok = false;
             break;
           }
           unsigned char* st = ring + (size_t)s * HP_STAGE;
-          tc::mbar_arrive_expect_tx(&full[s], HP_STAGE);
-          tc::tma_load_2d(st, &a.tmA[p], &full[s], 64 * kb, y0);
-          tc::tma_load_2d(st + HP_STAGE / 2, &a.tmA[p], &full[s], 64 * kb, y0 + 64);
+          tc::mbar_arrive_expect_tx(&full[s], (uint32_t)nc * HP_KCHUNK);
+          for (int c = 0; c < nc; ++c) {
+            tc::tma_load_2d(st + (size_t)c * HP_KCHUNK, &a.tmA[p], &full[s], 64 * (kb0 + c), y0);
+            tc::tma_load_2d(st + (size_t)c * HP_KCHUNK + HP_KCHUNK / 2, &a.tmA[p], &full[s], 64 * (kb0 + c), y0 + 64);
+          }
+          if (a.pf > 0)
+            for (int c = 0; c < nc; ++c) prefetch_next();
         }
       }
       // after an abort, the copies still in flight land before the CTA exits
@@ -170,8 +202,15 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
       int prev = -1;
       int64_t it = 0, nsw = 0, ti = 0;
       bool ok = true;
+      int p_nx = q0 < q1 ? item_p[q0] : 0;
+      uint32_t t_nx = q0 < q1 ? (uint32_t)item_t[q0] : 0u;
       for (int64_t q = q0; q < q1 && ok; ++q, ++ti) {
-        const int p = item_p[q];
+        const int p = p_nx;
+        const int nk = (int)(t_nx >> 24);
+        if (q + 1 < q1) {
+          p_nx = item_p[q + 1];
+          t_nx = (uint32_t)item_t[q + 1];
+        }
         if (p != prev) {
           if (nsw > 0) tc::mma_commit(xfree);   // every MMA reading the old X^T has been issued
           if (!tc::mbar_wait(xfull, (uint32_t)(nsw & 1), a.err, abort_flag)) break;
@@ -182,20 +221,23 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
         const int b = (int)(ti & 1);
         if (!tc::mbar_wait(&tfree[b], (uint32_t)(((ti >> 1) & 1) ^ 1), a.err, abort_flag)) break;
         tc::tc_fence_after();
-        const int nk = probs[p].n64 / 64;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        for (int kb0 = 0; kb0 < nk; kb0 += HP_KPS, ++it) {
+          const int nc = min(HP_KPS, nk - kb0);
           const int s = (int)(it % a.nstages);
           if (!tc::mbar_wait(&full[s], (uint32_t)((it / a.nstages) & 1), a.err, abort_flag)) {
             ok = false;
             break;
           }
           tc::tc_fence_after();
-          const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(ring + (size_t)s * HP_STAGE), 16, 1024);
-          const uint64_t bd = tc::sdesc_sw128(xa + (uint32_t)kb * HP_XCHUNK, 16, 1024);
+          for (int c = 0; c < nc; ++c) {
+            const int kb = kb0 + c;
+            const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(ring + (size_t)s * HP_STAGE + (size_t)c * HP_KCHUNK), 16, 1024);
+            const uint64_t bd = tc::sdesc_sw128(xa + (uint32_t)kb * HP_XCHUNK, 16, 1024);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(tmem + (uint32_t)b * 32u, tc::sdesc_add(ad, kk * 32), tc::sdesc_add(bd, kk * 32), idesc,
-                        (kb > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_f16(tmem + (uint32_t)b * 32u, tc::sdesc_add(ad, kk * 32), tc::sdesc_add(bd, kk * 32), idesc,
+                          (kb > 0 || kk > 0) ? 1u : 0u);
+          }
           tc::mma_commit(&empty[s]);
         }
         if (!ok) break;
@@ -245,7 +287,7 @@ k_grp_hpass(const GrpProblem* __restrict__ probs, const int32_t* __restrict__ it
       }
       epi_bar();
       const GrpProblem& P = probs[item_p[q]];
-      const int64_t row0 = (int64_t)item_t[q] * 128;
+      const int64_t row0 = (int64_t)((uint32_t)item_t[q] & 0xffffffu) * 128;
       const int nr = (int)(P.m - row0 < 128 ? P.m - row0 : 128);
       for (int e = et; e < nr * a.l; e += 128) {
         const int r = e / a.l, c = e % a.l;
@@ -330,6 +372,27 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
       // ------------------------------------------------------------ producer
       int64_t it = 0;
       bool ok = true;
+      // L2 prefetch cursor a.pf stages ahead of the loads
+      int64_t pqi = 0;
+      int pgr = 0, pt0 = 0;
+      auto prefetch_next = [&]() {
+        if (pqi >= my_items) return;
+        const GrpTItem J = items[blockIdx.x + pqi * gridDim.x];
+        const int jt = (int)((probs[J.p].n + 127) / 128);
+        const int32_t r0 = (J.sub0 + pgr) * 64;
+        if (pt0 == 0) tc::tma_prefetch_l2_2d(&a.tmZ[J.p], 0, r0);
+        const int nt = min(TPG_TPS, jt - pt0);
+        for (int bx = 0; bx < 2 * nt; ++bx) tc::tma_prefetch_l2_2d(&a.tmA[J.p], 128 * pt0 + 64 * bx, r0);
+        pt0 += TPG_TPS;
+        if (pt0 >= jt) {
+          pt0 = 0;
+          if (++pgr >= J.nsub) {
+            pgr = 0;
+            ++pqi;
+          }
+        }
+      };
+      for (int i = 0; i < a.pf; ++i) prefetch_next();
       for (int64_t qi = 0; qi < my_items && ok; ++qi) {
         const GrpTItem I = items[blockIdx.x + qi * gridDim.x];
         const int ntile = (int)((probs[I.p].n + 127) / 128);
@@ -349,6 +412,7 @@ k_grp_tpass(const GrpProblem* __restrict__ probs, const GrpTItem* __restrict__ i
             tc::tma_load_2d(st, tZ, &full[s], 0, r0);
             for (int bx = 0; bx < 2 * nt; ++bx)
               tc::tma_load_2d(st + (size_t)(1 + bx) * TPG_BOX, tA, &full[s], 128 * t0 + 64 * bx, r0);
+            if (a.pf > 0) prefetch_next();
           }
         }
       }

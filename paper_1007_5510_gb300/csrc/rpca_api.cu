@@ -1276,7 +1276,7 @@ bool batch_grouped_run(rpca_batch* b, const rpca_matrix* A, void* const* U, cons
 }
 
 // ----------------------------------------------------------- autotuner
-// Cache file: {"rpca_batch_tuning": {"<key>": [h, t, trows, rrows], ...}}
+// Cache file: {"rpca_batch_tuning": {"<key>": [h, t, trows, rrows, pf], ...}}
 std::string tune_key(const rpca_batch* b) {
   int64_t maxn = 0;
   double meanm = 0.0;
@@ -1327,7 +1327,7 @@ std::vector<std::pair<std::string, std::vector<int>>> read_tune_cache(const char
       v.push_back((int)x);
       c = e;
     }
-    if (v.size() == 4) out.emplace_back(t.substr(k0 + 1, k1 - k0 - 1), v);
+    if (v.size() == 5) out.emplace_back(t.substr(k0 + 1, k1 - k0 - 1), v);
     pos = t.find(',', a1);
     if (pos == std::string::npos || t.find('"', pos) == std::string::npos) break;
   }
@@ -1340,8 +1340,8 @@ void write_tune_cache(const char* path, const std::vector<std::pair<std::string,
   if (!f) throw Invalid(std::string("cannot write the tuning cache ") + path);
   std::fprintf(f, "{\"rpca_batch_tuning\": {");
   for (size_t i = 0; i < e.size(); ++i)
-    std::fprintf(f, "%s\n  \"%s\": [%d, %d, %d, %d]", i ? "," : "", e[i].first.c_str(), e[i].second[0],
-                 e[i].second[1], e[i].second[2], e[i].second[3]);
+    std::fprintf(f, "%s\n  \"%s\": [%d, %d, %d, %d, %d]", i ? "," : "", e[i].first.c_str(), e[i].second[0],
+                 e[i].second[1], e[i].second[2], e[i].second[3], e[i].second[4]);
   std::fprintf(f, "\n}}\n");
   std::fclose(f);
 }
@@ -1352,7 +1352,7 @@ rpca_status batch_tune(rpca_batch* b, const rpca_matrix* A, void* const* U, cons
   auto cache = read_tune_cache(path);
   for (const auto& e : cache)
     if (e.first == key) {
-      rpca::grp::Tuning v{e.second[0], e.second[1], e.second[2], e.second[3]};
+      rpca::grp::Tuning v{e.second[0], e.second[1], e.second[2], e.second[3], e.second[4]};
       rpca::grp::grouped_set_tuning(b->grp, v);
       rpca_status st = RPCA_OK;
       if (!batch_grouped_run(b, A, U, ldu, S, V, ldv, &st)) throw Invalid("the matrices' layout needs the per-problem form");
@@ -1376,11 +1376,11 @@ rpca_status batch_tune(rpca_batch* b, const rpca_matrix* A, void* const* U, cons
   rpca::grp::Tuning best = rpca::grp::grouped_tuning(b->grp);
   float best_ms = 0.f;
   rpca_status st = time_one(best, &best_ms);
-  const int cand[4][3] = {{4, 6, 8}, {3, 4, 5}, {2048, 4096, 8192}, {1024, 2048, 4096}};
-  for (int d = 0; d < 4 && st == RPCA_OK; ++d)
+  const int cand[5][3] = {{2, 3, 4}, {3, 4, 5}, {2048, 4096, 8192}, {1024, 2048, 4096}, {0, 8, 16}};
+  for (int d = 0; d < 5 && st == RPCA_OK; ++d)
     for (int c = 0; c < 3 && st == RPCA_OK; ++c) {
       rpca::grp::Tuning v = best;
-      int* f[4] = {&v.h_stages, &v.t_stages, &v.t_rows, &v.r_rows};
+      int* f[5] = {&v.h_stages, &v.t_stages, &v.t_rows, &v.r_rows, &v.pf};
       if (*f[d] == cand[d][c]) continue;
       *f[d] = cand[d][c];
       float ms = 0.f;
@@ -1397,7 +1397,7 @@ rpca_status batch_tune(rpca_batch* b, const rpca_matrix* A, void* const* U, cons
   st = RPCA_OK;
   batch_grouped_run(b, A, U, ldu, S, V, ldv, &st);
   if (st == RPCA_OK && path) {
-    cache.emplace_back(key, std::vector<int>{best.h_stages, best.t_stages, best.t_rows, best.r_rows});
+    cache.emplace_back(key, std::vector<int>{best.h_stages, best.t_stages, best.t_rows, best.r_rows, best.pf});
     write_tune_cache(path, cache);
   }
   return st;
@@ -1681,6 +1681,7 @@ rpca_status rpca_batch_get_tuning(const rpca_batch* b, int32_t* t) {
   t[1] = v.t_stages;
   t[2] = v.t_rows;
   t[3] = v.r_rows;
+  t[4] = v.pf;
   return RPCA_OK;
 }
 
@@ -1692,6 +1693,7 @@ rpca_status rpca_batch_set_tuning(rpca_batch* b, const int32_t* t) {
     v.t_stages = t[1];
     v.t_rows = t[2];
     v.r_rows = t[3];
+    v.pf = t[4];
     rpca::grp::grouped_set_tuning(b->grp, v);
     return RPCA_OK;
   });

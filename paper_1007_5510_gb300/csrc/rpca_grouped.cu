@@ -88,9 +88,11 @@ static void build_items(GroupedBatch* g) {
   const int sub_per_item = std::max(1, g->tune.t_rows / 64);
   for (int p = 0; p < g->count; ++p) {
     const int64_t m = g->m[p], n = g->n[p];
+    // tile index | 64-column steps << 24 (n <= 1024: at most 16 steps)
+    const uint32_t nk = (uint32_t)cdiv(n, 64);
     for (int64_t t = 0; t < cdiv(m, 128); ++t) {
       hp_.push_back(p);
-      ht_.push_back((int32_t)t);
+      ht_.push_back((int32_t)((uint32_t)t | (nk << 24)));
     }
     // (problem, range of 64-row groups), all columns of A at once
     const int nsub = (int)cdiv(m, 64);
@@ -229,10 +231,11 @@ void grouped_destroy(GroupedBatch* g) { delete g; }
 
 void grouped_set_tuning(GroupedBatch* g, const Tuning& t) {
   Tuning v = t;
-  v.h_stages = std::max(2, std::min(8, v.h_stages));
+  v.h_stages = std::max(2, std::min(4, v.h_stages));
   v.t_stages = std::max(2, std::min(5, v.t_stages));
   v.t_rows = std::max(64, (int)round_up(std::min(v.t_rows, 1 << 20), 64));
   v.r_rows = std::max(64, (int)round_up(std::min(v.r_rows, 1 << 20), 64));
+  v.pf = std::max(0, std::min(64, v.pf));
   const bool rebuild = v.t_rows != g->tune.t_rows || v.r_rows != g->tune.r_rows;
   g->tune = v;
   if (rebuild) build_items(g);
@@ -320,12 +323,12 @@ bool grouped_run(GroupedBatch* g, const rpca_matrix* A, void* const* U, const in
   };
   const uint32_t xbytes = (uint32_t)(round_up(g->max_n, 64) / 64) * 32 * 128;
   for (int j = 0; j <= g->i; ++j) {
-    HPassArgs h{mA, g->tune.h_stages, xbytes, g->ldt, g->l, j * g->l, j < g->i ? 1 : 0, j == 0 ? 1 : 0, err};
+    HPassArgs h{mA, g->tune.h_stages, xbytes, g->ldt, g->l, j * g->l, j < g->i ? 1 : 0, j == 0 ? 1 : 0, g->tune.pf, err};
     launch_hpass(probs, ip, it, g->n_h, h, g->sms, st);
     step("h pass");
     if (j < g->i) {
       const int npf = (int)round_up(g->l, 16);
-      TPassArgs t{mA, mZ, g->tune.t_stages, pow2(ntile_max * npf), npf, g->l, g->ldf, 0, err};
+      TPassArgs t{mA, mZ, g->tune.t_stages, pow2(ntile_max * npf), npf, g->l, g->ldf, 0, g->tune.pf, err};
       launch_tpass(probs, g->dTF.as<GrpTItem>(), g->n_tf, t, g->sms, st);
       step("f pass");
       launch_orth(probs, count, j, g->l, g->w, g->ldf, g->max_n, err, st);
@@ -341,7 +344,7 @@ bool grouped_run(GroupedBatch* g, const rpca_matrix* A, void* const* U, const in
   launch_chol(probs, count, g->w, 2, err, st);
   step("chol 2");
   const int npt = (int)round_up(g->w, 16);
-  TPassArgs t{mA, mZ, g->tune.t_stages, pow2(ntile_max * npt), npt, g->w, g->ldt, 1, err};
+  TPassArgs t{mA, mZ, g->tune.t_stages, pow2(ntile_max * npt), npt, g->w, g->ldt, 1, g->tune.pf, err};
   launch_tpass(probs, g->dTT.as<GrpTItem>(), g->n_tt, t, g->sms, st);
   step("t pass");
   launch_gram_t(probs, g->dRT.as<GrpRItem>(), g->n_rt, g->w, err, st);

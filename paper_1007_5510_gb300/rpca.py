@@ -432,21 +432,25 @@ class Batch:
 
     @property
     def tuning(self):
-        """(H-pass stages, T-pass stages, rows per T item, rows per row item)."""
-        t = (ctypes.c_int32 * 4)()
+        """(H-pass stages, T-pass stages, rows per T item, rows per row item,
+        L2 prefetch distance)."""
+        t = (ctypes.c_int32 * 5)()
         _check(load_library().rpca_batch_get_tuning(self.ctx, t))
         return tuple(t)
 
     @tuning.setter
     def tuning(self, values):
-        t = (ctypes.c_int32 * 4)(*[int(v) for v in values])
+        values = [int(v) for v in values]
+        if len(values) != 5:
+            raise ValueError("tuning takes 5 values")
+        t = (ctypes.c_int32 * 5)(*values)
         _check(load_library().rpca_batch_set_tuning(self.ctx, t))
 
     def tune(self, As, cache_path=None, outs=None):
         """Autotunes the grouped kernels on these matrices (rpca_batch_tune;
         cached in the JSON file cache_path) and returns the chosen tuning."""
         outs, args = self._args(As, outs)
-        chosen = (ctypes.c_int32 * 4)()
+        chosen = (ctypes.c_int32 * 5)()
         path = None if cache_path is None else str(cache_path).encode()
         status = load_library().rpca_batch_tune(self.ctx, *args, path, chosen)
         if status != OK:

@@ -142,14 +142,14 @@ def test_grouped_tuning_and_autotuner_cache(tmp_path):
     b = rpca.Batch(shapes, k, l, i, dtype=rpca.BF16, seeds=seeds)
     try:
         base = [o[1].clone() for o in b.run(As)]
-        b.tuning = (4, 4, 1024, 512)
-        assert b.tuning == (4, 4, 1024, 512)
+        b.tuning = (4, 4, 1024, 512, 0)
+        assert b.tuning == (4, 4, 1024, 512, 0)
         outs = b.run(As)
         torch.cuda.synchronize()
         for p in range(len(shapes)):
             a, c = base[p].cpu().numpy(), outs[p][1].cpu().numpy()
             assert np.max(np.abs(a - c) / a) < 1e-4, p
-        _check(rpca, shapes, outs, Ao, k, l, i, seeds, "tuned (4, 4, 1024, 512)")
+        _check(rpca, shapes, outs, Ao, k, l, i, seeds, "tuned (4, 4, 1024, 512, 0)")
         cache = tmp_path / "tuning.json"
         chosen = b.tune(As, cache)
         data = json.loads(cache.read_text())["rpca_batch_tuning"]
@@ -157,7 +157,7 @@ def test_grouped_tuning_and_autotuner_cache(tmp_path):
         key = next(iter(data))
         assert key.startswith("bf16/n") and "/k12/l16/i1" in key
         # a cached key is applied without timing
-        b.tuning = (6, 8, 4096, 2048)
+        b.tuning = (3, 5, 4096, 2048, 16)
         assert b.tune(As, cache) == chosen
         assert b.tuning == chosen
         outs = b.run(As)
