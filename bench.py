@@ -67,6 +67,8 @@ def parse():
                     help="precision: the headline (one 1e6 x 4096 PCA); batched: 512 uneven BF16 PCAs; "
                          "out_of_core: FP32 A in pinned host memory (n = 8192), streamed in tiles")
     ap.add_argument("--count", type=int, default=512, help="problems in the batched workload")
+    ap.add_argument("--no-batched", action="store_true", help="leave the batched workload out of the default line")
+    ap.add_argument("--no-backward", action="store_true", help="batched workload: forward only")
     return ap.parse_args()
 
 
@@ -279,6 +281,23 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end(A16, m, n, k, l, i, bytes_bf16, min(args.steps, 3), dev, world, dist, W["seed"])
 
+    batched = None
+    if not args.no_batched:
+        # the 512-problem batched workload, forward and backward (sub-object)
+        del A8, s8
+        ctx8.close()
+        torch.cuda.empty_cache()
+        tb = time.perf_counter()
+        bshapes, bAs = batched_inputs(args.count, rank, dev)
+        bgen = time.perf_counter() - tb
+        batched = batched_measure(bshapes, bAs, args.steps, args.warmup, world, dist, dev,
+                                  backward=not args.no_backward)
+        batched["gen_s"] = round(bgen, 2)
+        batched["workload"] = ("batched: %d BF16 PCAs, m ~ U[1000, 50000], n ~ U[64, 1024], sigma_j = j^-1.5"
+                               % len(bshapes))
+        del bAs
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rows = min(CPU_SAMPLE_ROWS, m)
@@ -328,6 +347,7 @@ def main():
                          "avg_launch_ms": round(fused_ms16, 4),
                          "t_pass_ms": round(tpass_ms16, 4)},
             "accuracy": acc,
+            "batched": batched,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -336,7 +356,8 @@ def main():
         print(json.dumps(line))
     ctx16.close()
     ctx32.close()
-    ctx8.close()
+    if args.no_batched:
+        ctx8.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -422,76 +443,120 @@ def end_to_end(A_dev, m, n, k, l, i, b, steps, dev, world, dist, seed):
             "d2h_bytes_per_step": (m + n) * k * 4 + k * 8}
 
 
+def batched_inputs(count, rank, dev):
+    """The batched workload's matrices: `count` BF16 problems (m ~ U[1000,
+    50000], n ~ U[64, 1024], sigma_j = j^-1.5), rows padded to a multiple of
+    8 elements (16 bytes: the layout the grouped kernels' TMA loads take)."""
+    import torch
+    from synth import generators as gen
+    shapes = gen.batched_shapes(count=count, seed=5510 + rank)
+    As = []
+    for p, (m, n) in enumerate(shapes):
+        buf = torch.zeros(m, (n + 7) // 8 * 8, dtype=torch.bfloat16, device=dev)
+        buf[:, :n] = gen.workload_torch("batched", dev, m=m, n=n, seed=1007 + 7919 * rank + p, rank_cap=1024,
+                                        dtype=torch.bfloat16)
+        As.append(buf[:, :n])
+    torch.cuda.synchronize()
+    return shapes, As
+
+
+def batched_measure(shapes, As, steps, warmup, world, dist, dev, backward=True):
+    """Forward (grouped kernels) and backward (per-problem adjoint contexts:
+    dA_p for dS_p = 1) of the batched workload, device-timed with CUDA events
+    on the caller's stream.  Returns a dict of the two measurements."""
+    import torch
+    from paper_1007_5510_gb300 import rpca
+    from synth import generators as gen
+    cfg = gen.CONFIGS["batched"]
+    k, l, i = cfg["k"], cfg["l"], cfg["i"]
+    stream = torch.cuda.current_stream()
+    a_bytes = sum(m * n * 2 for m, n in shapes)
+    hbm, peak_kind = peaks()
+
+    def timed(fn, nsteps):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nsteps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), world, dist, dev) / nsteps
+
+    b = rpca.Batch(shapes, k, l, i, dtype=rpca.BF16, seeds=range(len(shapes)), nstreams=16)
+    holder = {"outs": b.run(As)}
+    for _ in range(max(0, warmup - 1)):
+        holder["outs"] = b.run(As, holder["outs"])
+    torch.cuda.synchronize()
+    grouped = b.grouped
+    launches0 = rpca.kernel_launches()
+    ms = timed(lambda: holder.__setitem__("outs", b.run(As, holder["outs"])), steps)
+    launches = (rpca.kernel_launches() - launches0) / steps
+    b.close()
+    t = ms / 1e3
+    fwd = {"ms_per_step": round(ms, 4), "pcas_per_s": round(world * len(shapes) / t, 1),
+           "value": round(world * (i + 2) * a_bytes / t / 1e9, 2), "unit": "GB/s",
+           "pct_hbm_peak": round(100 * (i + 2) * a_bytes / t / 1e9 / hbm, 2),
+           "kernels_per_step": round(launches, 1),
+           "form": "grouped kernels (one launch per step of the method over all problems)"
+                   if grouped else "per-problem contexts, one graph launch per step"}
+    out = {"problems": len(shapes), "a_bytes": a_bytes, "k": k, "l": l, "i": i,
+           "lda": "n rounded up to a multiple of 8", "forward": fwd}
+    if backward:
+        # adjoint contexts (per problem), one forward, then the timed backward
+        ba = rpca.Batch(shapes, k, l, i, dtype=rpca.BF16, seeds=range(len(shapes)), nstreams=16, adjoint=True)
+        ba.run(As)
+        dS = [torch.ones(k, dtype=torch.float64, device=dev) for _ in shapes]
+        dA = [torch.empty(m, n, dtype=torch.float32, device=dev) for m, n in shapes]
+        ba.backward(As, dS, dA)
+        torch.cuda.synchronize()
+        bsteps = max(1, min(steps, 2))
+        msb = timed(lambda: ba.backward(As, dS, dA), bsteps)
+        ba.close()
+        del dA
+        out["backward"] = {"ms_per_step": round(msb, 4), "steps": bsteps,
+                           "grad": "dA_p of sum_j sigma_j for every problem (FP32, m_p x n_p)",
+                           "form": "per-problem adjoint contexts over 16 streams"}
+    return out
+
+
 def run_batched(args, world, rank, local, dist):
     """Batched workload: `count` independent BF16 PCAs (m ~ U[1000, 50000],
-    n ~ U[64, 1024], sigma_j = j^-1.5, k=16 l=20 i=1) per step, run as one
-    batch (one CUDA-graph launch per step after the first)."""
+    n ~ U[64, 1024], sigma_j = j^-1.5, k=16 l=20 i=1) per step, one batch."""
     import torch
     from paper_1007_5510_gb300 import rpca
     from synth import generators as gen
     cfg = gen.CONFIGS["batched"]
     k, l, i = cfg["k"], cfg["l"], cfg["i"]
     dev = torch.device("cuda", local)
-    shapes = gen.batched_shapes(count=args.count, seed=5510 + rank)
     t0 = time.perf_counter()
-    As = []
-    for p, (m, n) in enumerate(shapes):
-        # rows padded to a multiple of 8 elements (16 bytes): the layout the
-        # grouped kernels' TMA loads take
-        buf = torch.zeros(m, (n + 7) // 8 * 8, dtype=torch.bfloat16, device=dev)
-        buf[:, :n] = gen.workload_torch("batched", dev, m=m, n=n, seed=1007 + 7919 * rank + p, rank_cap=1024,
-                                        dtype=torch.bfloat16)
-        As.append(buf[:, :n])
-    torch.cuda.synchronize()
+    shapes, As = batched_inputs(args.count, rank, dev)
     gen_s = time.perf_counter() - t0
-    b = rpca.Batch(shapes, k, l, i, dtype=rpca.BF16, seeds=range(len(shapes)), nstreams=16)
-    outs = b.run(As)                          # direct run (per-problem form: records the graph)
-    for _ in range(max(0, args.warmup - 1)):
-        outs = b.run(As, outs)
-    torch.cuda.synchronize()
-    grouped = b.grouped
-    stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = rpca.kernel_launches()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        outs = b.run(As, outs)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    launches = rpca.kernel_launches() - launches0
+    res = batched_measure(shapes, As, args.steps, args.warmup, world, dist, dev, backward=not args.no_backward)
     clocks = sampler.stop()
-    ms = max_over_ranks(ms, world, dist, dev)
-    t = ms / args.steps / 1e3
-    a_bytes = sum(m * n * 2 for m, n in shapes)
-    hbm, peak_kind = peaks()
-    value = world * (i + 2) * a_bytes / t / 1e9
+    fwd = res["forward"]
     if rank == 0:
         print(json.dumps({
             "metric": "A-stream GB/s (% HBM peak) and s/PCA, BF16 vs FP32 at equal spectral error",
-            "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "value": fwd["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": fwd["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "gpu_launches": int(launches),
+            "gpu_launches": int(fwd["kernels_per_step"] * args.steps),
             "config": {"workload": "batched: %d BF16 PCAs, m ~ U[1000, 50000], n ~ U[64, 1024], "
-                                   "sigma_j = j^-1.5, k=%d l=%d i=%d, %s"
-                                   % (len(shapes), k, l, i, "grouped kernels (one launch per step of the "
-                                      "method over all problems)" if grouped else
-                                      "per-problem contexts, one graph launch per step"),
-                       "grouped": bool(grouped), "lda": "n rounded up to a multiple of 8",
-                       "problems": len(shapes), "a_bytes": a_bytes, "streams_per_pca": i + 2,
-                       "l2_flush": "not needed: A (%.1f GB in total) >> L2" % (a_bytes / 1e9),
+                                   "sigma_j = j^-1.5, k=%d l=%d i=%d, %s" % (len(shapes), k, l, i, fwd["form"]),
+                       "problems": len(shapes), "a_bytes": res["a_bytes"], "streams_per_pca": i + 2,
+                       "lda": res["lda"],
+                       "l2_flush": "not needed: A (%.1f GB in total) >> L2" % (res["a_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "pcas_per_s": round(world * len(shapes) / t, 1),
-            "pct_hbm_peak": round(100 * (i + 2) * a_bytes / t / 1e9 / hbm, 2),
+            "pcas_per_s": fwd["pcas_per_s"], "pct_hbm_peak": fwd["pct_hbm_peak"],
+            "backward": res.get("backward"),
             "clocks": clocks, "gen_s": round(gen_s, 2),
         }))
-    b.close()
 
 
 def run_out_of_core(args, world, rank, local, dist):
