@@ -1098,7 +1098,7 @@ void jacobi_svd(bool f64, int w, int kk, const double* B, double* S, double* Ub,
     float* Bc32 = reinterpret_cast<float*>(Bc);
     float* Jc32 = reinterpret_cast<float*>(Jc);
     const double tol = 4.0 * std::sqrt((double)w) * 5.96e-8;
-    if (getenv("RPCA_JACOBI_SINGLE") || !jacobi_cluster_f32(w, B, Jc32, tol, 40, dev_err, st)) {
+    if (!jacobi_cluster_f32(w, B, Jc32, tol, 40, dev_err, st)) {
       const size_t mat = (size_t)w * w * sizeof(float);
       const size_t smem = 2 * mat <= 200 * 1024 ? 2 * mat : (mat <= 200 * 1024 ? mat : 0);
       RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -1156,8 +1156,11 @@ void svd_from_gram(int w, const double* G, double* S, double* Vs, double* W, dou
   double* Sm = work + 5 * ww;
   double* E = B;                                   // B is free once the sweeps are done
   const double kGramJacobiTol = 4.0 * std::sqrt((double)w) * 5.96e-8;
+  // FP32 eigenvectors of G: one-sided Jacobi on a shifted FP32 Cholesky
+  // factor of G (relative accuracy for the small eigenvalues, which a
+  // two-sided Jacobi on G in FP32 lacks), over a cluster of CTAs
   chol32_shift(w, G, B, st);
-  if (getenv("RPCA_JACOBI_SINGLE") || !jacobi_cluster_f32(w, B, Jc32, kGramJacobiTol, 40, dev_err, st)) {
+  if (!jacobi_cluster_f32(w, B, Jc32, kGramJacobiTol, 40, dev_err, st)) {
     const size_t mat = ww * sizeof(float);
     const size_t smem = 2 * mat <= 200 * 1024 ? 2 * mat : (mat <= 200 * 1024 ? mat : 0);
     RPCA_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

@@ -161,6 +161,7 @@ void refine_eigvecs64(int w, const double* B, double* X, double* Xn, double* P, 
 // B (upper triangular FP64 container) with B^T B = G + 1e-6 max diag(G) I,
 // FP32 Cholesky (a preconditioner only; w <= 224).
 void chol32_shift(int w, const double* G, double* B, cudaStream_t st);
+
 // sigma_j = sqrt(S_jj) sorted descending, W = X reordered, Vs = W Sigma^-1.
 void eig_finish(int w, const double* Sm, const double* X, double* S, double* Vs, double* W, cudaStream_t st);
 // Step 4 from the Gram of T (FP32-class paths): S, W (right singular
