@@ -261,6 +261,44 @@ rpca_status rpca_backward(rpca_ctx* c, const rpca_matrix* A, const double* dS,
                           void* dA, int64_t ldda);
 
 /* ---------------------------------------------------------------------- */
+/* Error estimate (Appendix) and adaptive rank (Remark after Section 3).    */
+/* ---------------------------------------------------------------------- */
+
+/* p_{j,q}(D), the Appendix's power-method estimate of ||D||_2 for
+ * D = A - U diag(S) V^T:
+ *   p = max_c sqrt(||(D^T D)^j w_c|| / ||(D^T D)^(j-1) w_c||),
+ * j steps from q start vectors w_c (n x q, row-major FP64, host: `omega`;
+ * NULL: the Philox4x32-10 Gaussian stream of p->seed, domain 1).  D is
+ * applied only through products with A and A^T, D then D^T in turn: each
+ * step is an H pass and a T pass over A plus the rank-kd corrections, with
+ * the columns renormalised between steps.  p (problem) gives m, n, dtype and stream of A
+ * (device, no RPCA_CENTER / RPCA_HOST_A); U (m x kd, ldu), V (n x kd, ldv):
+ * device, compute type (FP64 for RPCA_F64, else FP32); S: kd FP64 values
+ * (host or device).  *est (host) receives p; col_est (host, q values, may be
+ * NULL) each column's estimate.  p <= ||D||_2 always; p >= ||D||_2 / 2 with
+ * probability at least 1 - (2n / ((2j - 1) 16^j))^(q/2) (eq. high_prob).
+ * The paper uses j = 6 and q = the rank.  Synchronises the stream. */
+rpca_status rpca_estimate_error(const rpca_problem* p, const rpca_matrix* A,
+                                const void* U, int64_t ldu, const double* S,
+                                const void* V, int64_t ldv, int32_t kd,
+                                int32_t j, int32_t q, const double* omega,
+                                double* est, double* col_est);
+
+/* Adaptive rank: runs the method (rpca_run) at k = p->k, then 2k, 4k, ...
+ * (at most kmax; oversampling l - k and power steps i kept from p) until
+ * the estimate of ||A - U S V^T||_2 (rpca_estimate_error, j steps, q = k
+ * start vectors) is at most tol.  U (m x kmax capacity, ldu >= kmax), S
+ * (kmax), V (n x kmax, ldv >= kmax) hold the last run's rank-k result;
+ * *k_out its rank and *eps_out its estimate (> tol only when kmax or the
+ * limits of the method stopped the doubling).  The Remark after Section 3
+ * refers the choice of k to the literature; this is the doubling rule with
+ * the paper's own estimator.  Synchronises p->stream. */
+rpca_status rpca_run_adaptive(const rpca_problem* p, const rpca_matrix* A,
+                              double tol, int32_t kmax, int32_t j, void* U,
+                              int64_t ldu, double* S, void* V, int64_t ldv,
+                              int32_t* k_out, double* eps_out);
+
+/* ---------------------------------------------------------------------- */
 /* Batches of independent problems (uneven shapes).                        */
 /* ---------------------------------------------------------------------- */
 typedef struct rpca_batch rpca_batch;

@@ -97,6 +97,18 @@ __device__ __forceinline__ void e4m3x4(uint32_t w, float* out) {
   }
 }
 
+// Two e4m3 values (16 bits) -> two BF16 (32 bits), exactly: the hardware
+// conversion to f16 (every e4m3 value is a normal f16 or zero), then the f16
+// bits re-biased to BF16 (exponent + 112; the low 3 mantissa bits of an
+// e4m3-derived f16 are zero, so shifting them out loses nothing).
+__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint32_t v16) {
+  uint32_t h;
+  asm("{\n .reg .b16 a;\n cvt.u16.u32 a, %1;\n cvt.rn.f16x2.e4m3x2 %0, a;\n}" : "=r"(h) : "r"(v16));
+  const uint32_t em = h & 0x7fff7fffu;
+  const uint32_t t = (em >> 3) & 0x0fff0fffu;
+  return (h & 0x80008000u) | (t + (__vcmpne2(em, 0u) & 0x38003800u));
+}
+
 // Convert row r (of R rows) of one 64-column group of a stage.
 //   raw: start of the group's raw bytes (FP32: two boxes of R x 32 at raw and
 //        raw + R*128; FP8: the 128-column box at raw, of which the group is
@@ -110,6 +122,29 @@ template <int SRC>
 __device__ __forceinline__ void convert_row(const unsigned char* raw, int R, int half, unsigned char* hi,
                                             unsigned char* lo, int r, const float* __restrict__ scg,
                                             const float* __restrict__ shg, int nvalid) {
+  if constexpr (SRC == SRC_FP8) {
+    // exact widening, no scale or shift: BF16 words straight from the bytes
+    // (columns past A are zero bytes from TMA's fill, hence zero here)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 t = *reinterpret_cast<const uint4*>(raw + sw128(r, 4 * half + j));
+      const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+      uint32_t o[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        o[2 * q] = e4m3x2_to_bf16x2(w[q] & 0xffffu);
+        o[2 * q + 1] = e4m3x2_to_bf16x2(w[q] >> 16);
+      }
+      *reinterpret_cast<uint4*>(hi + sw128(r, 2 * j)) = make_uint4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<uint4*>(hi + sw128(r, 2 * j + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+    (void)lo;
+    (void)scg;
+    (void)shg;
+    (void)nvalid;
+    (void)R;
+    return;
+  }
   float v[64];
   if constexpr (SRC == SRC_F32) {
 #pragma unroll
@@ -949,36 +984,6 @@ bool pass_cvt_src(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
   return launch_tpass<SRC, 2>(a, H16, 64, (int64_t)a.m * 64, 1, L, 0, false, st, dev_err, none);
 }
 
-// T pass over BF16 A as stored (no conversion), Q in one BF16 slice: the
-// sliced QR's first slice, or Q (FP32) rounded here.
-bool tpass_bf16_chunked(const PassArgs& a, cudaStream_t st, uint32_t* dev_err) {
-  const __nv_bfloat16* Y;
-  int64_t ldy;
-  int qblk;
-  if (a.q16) {
-    Y = static_cast<const __nv_bfloat16*>(a.q16);
-    ldy = a.q16_ld;
-    qblk = a.q_blk;
-  } else {
-    const int wq = (int)round_up(a.p, 64);
-    if (wq > 256 || (size_t)a.m * wq * 2 > a.work_bytes) return false;
-    __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(a.work);
-    const int64_t cnt = a.m * wq;
-    k_split_planes<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(a.m, a.p, wq, static_cast<const float*>(a.H), a.ldh, hi,
-                                                            nullptr);
-    RPCA_CUDA_TRY(cudaGetLastError());
-    count_launch();
-    Y = hi;
-    ldy = wq;
-    qblk = 0;
-  }
-  const int nyb = (int)(ldy / 64);
-  const int npad = qblk > 0 ? (int)ldy : (int)round_up(a.p, 16);
-  if (npad > 256) return false;
-  const size_t fes = a.f_f64 ? 8 : 4;
-  if (!a.accumulate_f) RPCA_CUDA_TRY(cudaMemset2DAsync(a.F, a.ldf * fes, 0, a.p * fes, a.n, st));
-  return launch_tpass<SRC_BF16, 1>(a, Y, ldy, 0, nyb, npad, qblk, a.f_f64, st, dev_err, take_wait_test(1));
-}
 
 }  // namespace
 

@@ -521,6 +521,10 @@ size_t tc_work_bytes(rpca_dtype dt, int64_t m, int64_t n, int w) {
 // tolerance on sigma (1e-4).
 constexpr double kMirrorKappa = 8.0;
 
+// Smallest sigma_k / sigma_1 for which Step 4 stays on the Gram route (its
+// FP32 preconditioner shifts G by 1e-6 of the largest eigenvalue).
+constexpr double kGramMinRatio = 1.7e-3;
+
 // Step 4 from the Gram of T (FP32-class storage; the single-CTA Cholesky
 // preconditioner takes w <= 192), else from a QR of T.
 bool gram_step4(const rpca_ctx* c) { return !c->f64 && c->w <= 192 && !c->adjoint && c->reorth; }
@@ -807,7 +811,7 @@ void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, in
   // Step 4: T = Q_T R_T; with E_T = Q_T^T Q_T - I, T = (Q_T (I - E_T/2))
   // ((I + E_T/2) R_T) to first order; R_T' = Ub S W^T  =>  V~ = Q_T (I - E_T/2) Ub
   const int w = c->w, k = c->k;
-  const bool g4 = gram_step4(c);
+  bool g4 = gram_step4(c);
   c->tic(c->i + 3);
   if (g4) {
     // Step 4 from G = T^T T (FP64): G' = (I - E/2) G (I - E/2) is the Gram
@@ -817,7 +821,25 @@ void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, in
     gemm64_small(w, w, w, -0.5, c->E, w, false, c->RT, w, false, 1.0, c->RT, w, c->RT2, w, st);
     gemm64_small(w, w, w, -0.5, c->RT2, w, false, c->E, w, false, 1.0, c->RT2, w, c->RT, w, st);
     svd_from_gram(w, c->RT, c->S, c->Ub, c->W, c->svdwork, c->dev_err(), st);
-  } else {
+    // The FP32 preconditioner of that route shifts G by 1e-6 of its largest
+    // eigenvalue: eigenvalues below a few shifts (sigma_k / sigma_1 < 1.7e-3)
+    // are not resolved, and the QR route of Step 4 (relative accuracy for
+    // the small singular values) runs instead.  The check reads two words
+    // on the host, so it is left out while the stream is captured.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    RPCA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusNone) {
+      double s0 = 0.0, sk = 0.0;
+      RPCA_CUDA_TRY(cudaMemcpyAsync(&s0, c->S, sizeof(double), cudaMemcpyDeviceToHost, st));
+      RPCA_CUDA_TRY(cudaMemcpyAsync(&sk, c->S + (k - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+      RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+      if (sk < kGramMinRatio * s0) {
+        gemm_xm(f64, c->n, w, w, c->T.ptr, w, c->E, w, -0.5, 1.0, c->T.ptr, w, st);   // T (I - E/2)
+        g4 = false;
+      }
+    }
+  }
+  if (!g4) {
     svd_of_T(f64, c->n, c->i + 1, c->l, c->k, c->T.ptr, c->Tc.ptr, c->Tlo.as<float>(), c->ET, c->RT, c->RT2, c->S,
              c->Ub, c->W, c->svdwork, c->qs, c->dev_err(), st);
   }
@@ -1450,6 +1472,111 @@ rpca_status read_op_error(const DevBuf& err, cudaStream_t st) {
   return RPCA_OK;
 }
 
+// ------------------------------------------------- error estimate (Appendix)
+// p_{j,q}(D) for D = A - U diag(S) V^T: j steps of the power method on D^T D
+// from q start vectors, each step D then D^T applied to the block (an H
+// pass and a T pass over A, with the rank-kd corrections), the columns
+// renormalised after every step; p = max_c sqrt(||D^T D w_c||) with w_c the
+// unit column after j - 1 steps.
+rpca_status do_estimate(const rpca_problem* p, const rpca_matrix* Am, const void* U, int64_t ldu, const double* S,
+                        const void* V, int64_t ldv, int kd, int j, int q, const double* omega, double* est,
+                        double* col_est) {
+  check_device();
+  if (!p || !Am || !Am->data || !U || !S || !V || !est) throw Invalid("null pointer");
+  if (p->m < 1 || p->n < 1 || kd < 1 || kd > 255 || kd > std::min(p->m, p->n) || j < 1 || j > 64 || q < 1 ||
+      q > 255 || q > p->n)
+    throw Invalid("bad sizes");
+  if (p->flags & (RPCA_CENTER | RPCA_HOST_A)) throw Invalid("the estimate takes an uncentred device matrix");
+  if (Am->ld < p->n || ldu < kd || ldv < kd) throw Invalid("bad leading dimension");
+  if (p->dtype < RPCA_F64 || p->dtype > RPCA_FP8E4M3) throw Invalid("unknown dtype");
+  const bool f64 = p->dtype == RPCA_F64;
+  const size_t es = f64 ? 8 : 4;
+  const int64_t m = p->m, n = p->n;
+  cudaStream_t st = static_cast<cudaStream_t>(p->stream);
+  DevBuf W, H, F, VS, small, err, work;
+  W.alloc((size_t)n * q * es);
+  H.alloc((size_t)m * q * es);
+  F.alloc((size_t)n * q * es);
+  VS.alloc((size_t)n * kd * es);
+  const size_t kq = (size_t)kd * q, kk = (size_t)kd * kd;
+  small.alloc((3 * kq + 3 * kk + (size_t)q * q + (size_t)q * q) * sizeof(double));
+  double* B = small.as<double>();
+  double* C = B + kq;
+  double* DS = C + kq + 2 * kk;
+  double* Gq = DS + kk;
+  double* Dn = Gq + (size_t)q * q;
+  DevBuf sb;
+  sb.alloc(kq * sizeof(double));
+  auto DSB = [&](const double* Bm) {   // diag(S) Bm (kd x q), FP64
+    gemm64_small(kd, q, kd, 1.0, DS, kd, false, Bm, q, false, 0.0, nullptr, 0, sb.as<double>(), q, st);
+    return sb.as<double>();
+  };
+  err.alloc(64 * sizeof(uint32_t));
+  RPCA_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, 64 * sizeof(uint32_t), st));
+  if (!f64) {
+    work.alloc(tc_work_bytes(p->dtype, m, n, std::max(q, kd)));
+  }
+  auto pass = [&](int mode, const void* X, int64_t ldx, int cols, void* Hout, int64_t ldh, void* Fout, int64_t ldf) {
+    PassArgs a;
+    a.dtype = p->dtype;
+    a.mode = mode;
+    a.A = Am->data; a.lda = Am->ld; a.m = m; a.n = n; a.scale = Am->col_scale;
+    a.X = X; a.ldx = ldx; a.p = cols; a.H = Hout; a.ldh = ldh; a.F = Fout; a.ldf = ldf;
+    a.work = work.ptr; a.work_bytes = work.bytes;
+    if (f64 || !launch_pass_tc(a, st, err.as<uint32_t>())) launch_pass_simt(a, st);
+  };
+  // start vectors (n x q, row-major): given, or the Philox stream of the
+  // problem's seed, domain 1 (G uses domain 0)
+  std::vector<double> om((size_t)n * q);
+  if (omega) std::memcpy(om.data(), omega, om.size() * sizeof(double));
+  else gaussian_stream(p->seed, 1u, (int64_t)om.size(), om.data());
+  {
+    DevBuf om64;
+    om64.alloc(om.size() * sizeof(double));
+    RPCA_CUDA_TRY(cudaMemcpyAsync(om64.ptr, om.data(), om.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    cast_f64_to(f64, (int64_t)om.size(), om64.as<double>(), W.ptr, st);
+    RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  // the iteration's constant terms: diag(S), VS = V S
+  std::vector<double> ds(kk, 0.0), sv(kd);
+  RPCA_CUDA_TRY(cudaMemcpyAsync(sv.data(), S, kd * sizeof(double), cudaMemcpyDefault, st));
+  RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int c = 0; c < kd; ++c) ds[(size_t)c * kd + c] = sv[c];
+  RPCA_CUDA_TRY(cudaMemcpyAsync(DS, ds.data(), kk * sizeof(double), cudaMemcpyHostToDevice, st));
+  gemm_xm(f64, n, kd, kd, V, ldv, DS, kd, 1.0, 0.0, VS.ptr, kd, st);
+  std::vector<double> gq((size_t)q * q), dn((size_t)q * q, 0.0);
+  std::vector<double> ratio(q, 0.0);
+  for (int step = 0; step < j; ++step) {
+    // Y = D W = A W - U S (V^T W), then D^T Y = A^T Y - V S (U^T Y): D and
+    // D^T applied in turn (forming A^T A W first would subtract quantities
+    // of size ||A||^2 to get ||D||^2, and lose it in FP32 when ||D|| is
+    // below sqrt(u32) ||A||)
+    pass(MODE_H, W.ptr, q, q, H.ptr, q, nullptr, 0);                   // H = A W
+    gram(f64, n, kd, q, V, ldv, W.ptr, q, B, q, false, st);            // B = V^T W
+    gemm_xm(f64, m, kd, q, U, ldu, DSB(B), q, -1.0, 1.0, H.ptr, q, st); // H -= U S B
+    pass(MODE_T, nullptr, 0, q, H.ptr, q, F.ptr, q);                   // F = A^T H
+    gram(f64, m, kd, q, U, ldu, H.ptr, q, C, q, false, st);            // C = U^T H
+    gemm_xm(f64, n, kd, q, VS.ptr, kd, C, q, -1.0, 1.0, F.ptr, q, st);  // F -= V S C
+    gram(f64, n, q, q, F.ptr, q, F.ptr, q, Gq, q, false, st);
+    RPCA_CUDA_TRY(cudaMemcpyAsync(gq.data(), Gq, gq.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RPCA_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int c = 0; c < q; ++c) ratio[c] = std::sqrt(std::max(gq[(size_t)c * q + c], 0.0));   // ||D^T D w_c||
+    if (step + 1 < j) {
+      for (int c = 0; c < q; ++c) dn[(size_t)c * q + c] = ratio[c] > 0.0 ? 1.0 / ratio[c] : 0.0;
+      RPCA_CUDA_TRY(cudaMemcpyAsync(Dn, dn.data(), dn.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      gemm_xm(f64, n, q, q, F.ptr, q, Dn, q, 1.0, 0.0, W.ptr, q, st);                 // W = F / ||F||
+    }
+  }
+  double best = 0.0;
+  for (int c = 0; c < q; ++c) {
+    const double pc = std::sqrt(ratio[c]);
+    if (col_est) col_est[c] = pc;
+    best = std::max(best, pc);
+  }
+  *est = best;
+  return read_op_error(err, st);
+}
+
 }  // namespace
 
 // ================================================================== C-ABI
@@ -1673,6 +1800,42 @@ const char* rpca_batch_last_error(const rpca_batch* b) {
 }
 
 int32_t rpca_batch_grouped(const rpca_batch* b) { return (b && b->grp && b->last_grouped) ? 1 : 0; }
+
+rpca_status rpca_estimate_error(const rpca_problem* p, const rpca_matrix* A, const void* U, int64_t ldu,
+                                const double* S, const void* V, int64_t ldv, int32_t kd, int32_t j, int32_t q,
+                                const double* omega, double* est, double* col_est) {
+  return guarded(nullptr, [&] { return do_estimate(p, A, U, ldu, S, V, ldv, kd, j, q, omega, est, col_est); });
+}
+
+rpca_status rpca_run_adaptive(const rpca_problem* p, const rpca_matrix* A, double tol, int32_t kmax, int32_t j,
+                              void* U, int64_t ldu, double* S, void* V, int64_t ldv, int32_t* k_out,
+                              double* eps_out) {
+  if (!p || !A || !U || !S || !V || !k_out || !eps_out || !(tol > 0.0) || j < 1) return RPCA_EINVAL;
+  if (kmax < p->k || ldu < kmax || ldv < kmax) return RPCA_EINVAL;
+  const int over = p->l - p->k;
+  if (over < 0) return RPCA_EINVAL;
+  const int64_t mn = std::min(p->m, p->n);
+  int k = p->k;
+  for (;;) {
+    rpca_problem q = *p;
+    q.k = k;
+    q.l = k + over;
+    if ((int64_t)(q.i + 1) * q.l > mn || q.l > 255 || (int64_t)(q.i + 1) * q.l > 256) return RPCA_EINVAL;
+    rpca_status s = rpca_run(&q, A, U, ldu, S, V, ldv);
+    if (s != RPCA_OK) return s;
+    double eps = 0.0;
+    s = rpca_estimate_error(&q, A, U, ldu, S, V, ldv, k, j, k, nullptr, &eps, nullptr);
+    if (s != RPCA_OK) return s;
+    *k_out = k;
+    *eps_out = eps;
+    if (eps <= tol || k >= kmax) return RPCA_OK;
+    // the next rank: doubled, within kmax and the method's limits
+    int next = std::min<int>(2 * k, kmax);
+    while (next > k && ((int64_t)(q.i + 1) * (next + over) > std::min<int64_t>(mn, 256) || next >= mn)) --next;
+    if (next <= k) return RPCA_OK;
+    k = next;
+  }
+}
 
 rpca_status rpca_batch_get_tuning(const rpca_batch* b, int32_t* t) {
   if (!b || !b->grp || !t) return RPCA_EINVAL;

@@ -26,7 +26,8 @@ EXPORTS = ["rpca_init", "rpca_pass", "rpca_finish", "rpca_destroy", "rpca_run", 
            "rpca_phase_times", "rpca_op_gram", "rpca_op_apply", "rpca_op_fused_pass_noalloc",
            "rpca_batch_init", "rpca_batch_run", "rpca_batch_destroy", "rpca_batch_last_error",
            "rpca_backward", "rpca_test_arm_wait_expiry", "rpca_batch_backward", "rpca_last_run_passes",
-           "rpca_batch_grouped", "rpca_batch_get_tuning", "rpca_batch_set_tuning", "rpca_batch_tune"]
+           "rpca_batch_grouped", "rpca_batch_get_tuning", "rpca_batch_set_tuning", "rpca_batch_tune",
+           "rpca_estimate_error", "rpca_run_adaptive"]
 
 
 class RpcaError(RuntimeError):
@@ -120,6 +121,13 @@ def load_library(path=None):
                                     ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.c_char_p,
                                     ctypes.POINTER(i32)]
     lib.rpca_batch_tune.restype = st
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.rpca_estimate_error.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(Matrix), vp, i64, vp, vp, i64, i32,
+                                        i32, i32, dp, dp, dp]
+    lib.rpca_estimate_error.restype = st
+    lib.rpca_run_adaptive.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(Matrix), ctypes.c_double, i32, i32,
+                                      vp, i64, vp, vp, i64, ctypes.POINTER(i32), dp]
+    lib.rpca_run_adaptive.restype = st
     lib.rpca_batch_backward.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(i64)]
     lib.rpca_batch_backward.restype = st
@@ -357,6 +365,65 @@ def pca(A, k, l, i, seed=0, center=False, G=None, col_scale=None, simt=False):
         return ctx.run(A, col_scale=col_scale)
     finally:
         ctx.close()
+
+
+def estimate_error(A, U, S, V, j=6, q=None, omega=None, seed=0, col_scale=None):
+    """The Appendix estimate p_{j,q}(D) of ||A - U diag(S) V^T||_2 on the
+    GPU (rpca_estimate_error).  omega: optional n x q start vectors (numpy,
+    FP64); else the Philox stream of `seed`.  Returns (p, per-column p)."""
+    import numpy as np
+    torch = _torch()
+    _check_mat(A, "A", _storage_dtypes())
+    m, n = A.shape
+    cdt = torch.float64 if A.dtype == torch.float64 else torch.float32
+    kd = int(S.shape[0])
+    _check_shape(U, "U", (cdt,), rows=m)
+    _check_shape(V, "V", (cdt,), rows=n)
+    _check_device(U, "U", A.device)
+    _check_device(V, "V", A.device)
+    if U.shape[1] < kd or V.shape[1] < kd:
+        raise ValueError("U and V need kd = len(S) columns")
+    q = kd if q is None else int(q)
+    om = None
+    if omega is not None:
+        om = np.ascontiguousarray(np.asarray(omega, np.float64))
+        if om.shape != (n, q):
+            raise ValueError("omega must be n x q")
+    Sd = torch.as_tensor(S, dtype=torch.float64, device=A.device).contiguous()
+    prob = Problem(m, n, kd, kd, 0, ctypes.c_uint64(seed), None, dtype_code(A), 0, 0, _stream_ptr())
+    mat = Matrix(ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                 ctypes.c_void_p(col_scale.data_ptr()) if col_scale is not None else None)
+    est = ctypes.c_double()
+    cols = (ctypes.c_double * q)()
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load_library().rpca_estimate_error(
+        ctypes.byref(prob), ctypes.byref(mat), _ptr(U), U.stride(0), _ptr(Sd), _ptr(V), V.stride(0), kd, int(j), q,
+        om.ctypes.data_as(dp) if om is not None else None, ctypes.byref(est), cols))
+    return est.value, list(cols)
+
+
+def pca_adaptive(A, tol, k0, kmax, oversample=2, i=2, j=6, seed=0, col_scale=None):
+    """Rank chosen by doubling from k0 (at most kmax) until the Appendix
+    estimate of the error is at most tol (rpca_run_adaptive).  Returns
+    (U, S, V, k, eps) with U, S, V cut to rank k."""
+    torch = _torch()
+    _check_mat(A, "A", _storage_dtypes())
+    m, n = A.shape
+    cdt = torch.float64 if A.dtype == torch.float64 else torch.float32
+    U = torch.empty(m, kmax, dtype=cdt, device=A.device)
+    V = torch.empty(n, kmax, dtype=cdt, device=A.device)
+    S = torch.empty(kmax, dtype=torch.float64, device=A.device)
+    prob = Problem(m, n, int(k0), int(k0) + int(oversample), int(i), ctypes.c_uint64(seed), None, dtype_code(A), 0,
+                   0, _stream_ptr())
+    mat = Matrix(ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                 ctypes.c_void_p(col_scale.data_ptr()) if col_scale is not None else None)
+    k_out = ctypes.c_int32()
+    eps = ctypes.c_double()
+    _check(load_library().rpca_run_adaptive(ctypes.byref(prob), ctypes.byref(mat), float(tol), int(kmax), int(j),
+                                            _ptr(U), U.stride(0), _ptr(S), _ptr(V), V.stride(0), ctypes.byref(k_out),
+                                            ctypes.byref(eps)))
+    k = k_out.value
+    return U[:, :k], S[:k], V[:, :k], k, eps.value
 
 
 def _pca_function():
