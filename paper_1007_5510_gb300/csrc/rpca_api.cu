@@ -287,6 +287,9 @@ static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, vo
 // Step 1 the columns of H are far from dependent (kappa(H) is that of A on
 // the Krylov space), so one pass leaves Q^T Q - I at the rounding of the
 // apply, which the first-order correction with the measured E_out absorbs.
+// When the factor's conditioning estimate kappa (max / min |diag R|) is at
+// most skip_e_kappa, that rounding is a few units of FP32 (u32 kappa) and
+// the second Gram is not formed: E_out = 0 and *e_zero is set.
 // The factorisation is checked before H is touched: when a diagonal block
 // needed a shifted Cholesky (numerical rank loss) this returns false with H
 // unchanged, and the block path with its shifted passes runs instead.  The
@@ -295,7 +298,7 @@ static void block_qr_sliced(int64_t m, int nblk, int l, float* H, int64_t ld, vo
 static bool block_qr_sliced_whole(int64_t m, int nblk, int l, float* H, int64_t ld, void* S, int64_t prow,
                                   double* E_out, bool fp32_out, const QrScratch& s, double* G, double* R,
                                   double* Rinv, double* tmp, uint32_t* dev_err, cudaStream_t st,
-                                  double* kappa = nullptr) {
+                                  double* kappa = nullptr, double skip_e_kappa = 0.0, bool* e_zero = nullptr) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   RPCA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
   if (cap != cudaStreamCaptureStatusNone) return false;
@@ -334,14 +337,18 @@ static bool block_qr_sliced_whole(int64_t m, int nblk, int l, float* H, int64_t 
   RPCA_CUDA_TRY(cudaStreamSynchronize(st));
   for (int b = 0; b < nblk; ++b)
     if (qf[(size_t)kQfWords * b + 1]) return false;
-  if (kappa) {
+  double kap;
+  {
     double lo = INFINITY, hi = 0.0;
     for (double v : rd) {
       lo = std::min(lo, std::fabs(v));
       hi = std::max(hi, std::fabs(v));
     }
-    *kappa = lo > 0.0 ? hi / lo : INFINITY;
+    kap = lo > 0.0 ? hi / lo : INFINITY;
   }
+  if (kappa) *kappa = kap;
+  const bool skip_e = E_out && kap <= skip_e_kappa;
+  if (e_zero) *e_zero = skip_e;
   // R^-1 (upper): Rinv_bc = -R_bb^-1 sum_{b<a<=c} R_ba Rinv_ac, from the diagonal outwards
   for (int c = 1; c < nblk; ++c)
     for (int b = c - 1; b >= 0; --b) {
@@ -354,7 +361,9 @@ static bool block_qr_sliced_whole(int64_t m, int nblk, int l, float* H, int64_t 
   for (int j = nblk - 1; j >= 0; --j)
     need(apply_slices(m, prow, S, lds, 0, j + 1, 64 * j, Rinv + (size_t)j * l, (j + 1) * l, l, w, 1.0, l, false,
                       true, nullptr, 0, 0, s.mt, st, dev_err, nullptr));
-  if (E_out) {
+  if (skip_e) {
+    RPCA_CUDA_TRY(cudaMemsetAsync(E_out, 0, (size_t)w * w * sizeof(double), st));
+  } else if (E_out) {
     need(gram_slices(m, prow, S, lds, 0, lds, 0, lds, s.Cfull, lds, st, dev_err, nullptr, true));
     compact_sq(nblk, l, s.Cfull, lds, E_out, st);
     sub_identity(nblk * l, E_out, st);
@@ -408,6 +417,7 @@ struct rpca_ctx {
   bool mirror = false;
   bool mirrored_last = false;    // the last run formed T this way
   double last_kappa = 0.0;       // max/min diagonal of R in the last whole-H QR
+  bool e_zero = false;           // the last run's E = Q^T Q - I was taken as 0 (kappa small)
   DevBuf Fall;
   // RPCA_HOST_RESIDENT: device copy of host A, valid once this run's first
   // pass has copied every tile
@@ -520,6 +530,9 @@ size_t tc_work_bytes(rpca_dtype dt, int64_t m, int64_t n, int w) {
 // (~1e-5 from the BF16 hi/lo products) times kappa stays below the FP32
 // tolerance on sigma (1e-4).
 constexpr double kMirrorKappa = 8.0;
+// Largest kappa estimate of the whole-H factor for which E = Q^T Q - I is
+// taken as 0 (no second Gram): u32 kappa stays below 1e-6.
+constexpr double kSkipEKappa = 16.0;
 
 // Smallest sigma_k / sigma_1 for which Step 4 stays on the Gram route (its
 // FP32 preconditioner shifts G by 1e-6 of the largest eigenvalue).
@@ -726,6 +739,7 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
   c->tic(c->i + 1);
   const bool q32 = !(t16 || t32s) || c->adjoint;
   bool whole = false;
+  c->e_zero = false;
   if (c->sliced) {
     // the whole-H Cholesky QR's scratch (G, R, R^-1, one block): Step 4's
     // work area, free until then
@@ -733,7 +747,7 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
     double* sw = c->svdwork;
     whole = c->reorth && block_qr_sliced_whole(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows,
                                                c->E, q32, c->qs, sw, sw + 2 * ww, sw + ww, sw + 3 * ww, c->dev_err(),
-                                               st, &c->last_kappa);
+                                               st, &c->last_kappa, kSkipEKappa, &c->e_zero);
     if (!whole)
       block_qr_sliced(c->m, c->i + 1, c->l, c->H.as<float>(), c->w, c->Hs.ptr, c->hs_rows, c->E, q32, c->qs,
                       c->dev_err(), st);
@@ -752,7 +766,7 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
             c->w, st);
     copy_matrix(false, true, c->n, c->w, c->T.ptr, c->w, c->T64.ptr, c->w, st);
     c->toc(c->i + 2);
-    if (!gram_step4(c))
+    if (!gram_step4(c) && !c->e_zero)
       gemm_xm(f64, c->n, c->w, c->w, c->T.ptr, c->w, c->E, c->w, -0.5, 1.0, c->T.ptr, c->w, st);
     c->next_pass = c->i + 2;
     return RPCA_OK;
@@ -796,7 +810,7 @@ rpca_status do_pass(rpca_ctx* c, const rpca_matrix* Am) {
     rank1_sub(f64, c->n, c->w, 1.0, c->d.as<double>(), c->q1.as<double>(), c->T.ptr, c->w, st);
   }
   // T <- T (I - E/2): the Rayleigh-Ritz matrix of the orthonormalised basis
-  gemm_xm(f64, c->n, c->w, c->w, c->T.ptr, c->w, c->E, c->w, -0.5, 1.0, c->T.ptr, c->w, st);
+  if (!c->e_zero) gemm_xm(f64, c->n, c->w, c->w, c->T.ptr, c->w, c->E, c->w, -0.5, 1.0, c->T.ptr, c->w, st);
   c->next_pass = c->i + 2;
   return RPCA_OK;
 }
@@ -818,8 +832,10 @@ void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, in
     // of the Rayleigh-Ritz matrix of the orthonormalised basis; its
     // eigenvectors W are T's right singular vectors and V = T (I - E/2) W / sigma
     gram(true, c->n, w, w, c->T64.ptr, w, c->T64.ptr, w, c->RT, w, false, st);
-    gemm64_small(w, w, w, -0.5, c->E, w, false, c->RT, w, false, 1.0, c->RT, w, c->RT2, w, st);
-    gemm64_small(w, w, w, -0.5, c->RT2, w, false, c->E, w, false, 1.0, c->RT2, w, c->RT, w, st);
+    if (!c->e_zero) {
+      gemm64_small(w, w, w, -0.5, c->E, w, false, c->RT, w, false, 1.0, c->RT, w, c->RT2, w, st);
+      gemm64_small(w, w, w, -0.5, c->RT2, w, false, c->E, w, false, 1.0, c->RT2, w, c->RT, w, st);
+    }
     svd_from_gram(w, c->RT, c->S, c->Ub, c->W, c->svdwork, c->dev_err(), st);
     // The FP32 preconditioner of that route shifts G by 1e-6 of its largest
     // eigenvalue: eigenvalues below a few shifts (sigma_k / sigma_1 < 1.7e-3)
@@ -834,7 +850,7 @@ void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, in
       RPCA_CUDA_TRY(cudaMemcpyAsync(&sk, c->S + (k - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
       RPCA_CUDA_TRY(cudaStreamSynchronize(st));
       if (sk < kGramMinRatio * s0) {
-        gemm_xm(f64, c->n, w, w, c->T.ptr, w, c->E, w, -0.5, 1.0, c->T.ptr, w, st);   // T (I - E/2)
+        if (!c->e_zero) gemm_xm(f64, c->n, w, w, c->T.ptr, w, c->E, w, -0.5, 1.0, c->T.ptr, w, st);   // T (I - E/2)
         g4 = false;
       }
     }
@@ -848,8 +864,10 @@ void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, in
   // Steps 5-6: U = Q (I - E/2) W[:, :k], V = Q_T (I - E_T/2) Ub[:, :k] (QR
   // form) or V = T (I - E/2) Ub[:, :k] with Ub = W / sigma (Gram form)
   // (working orientation; swapped back when the problem was transposed)
-  fold_fixup(f64, w, k, g4 ? c->E : c->ET, c->Ub, c->MV, st);
-  fold_fixup(f64, w, k, c->E, c->W, c->MU, st);
+  if (g4 && c->e_zero) copy_matrix(true, true, w, k, c->Ub, w, c->MV, k, st);
+  else fold_fixup(f64, w, k, g4 ? c->E : c->ET, c->Ub, c->MV, st);
+  if (c->e_zero) copy_matrix(true, true, w, k, c->W, w, c->MU, k, st);
+  else fold_fixup(f64, w, k, c->E, c->W, c->MU, st);
   const bool tlo = !g4 && c->Tlo.ptr && c->n >= kTcMinRows;
   const bool hlo = c->Hlo.ptr && c->m >= kTcMinRows;
   qr_apply(f64, c->n, w, k, c->T.ptr, tlo ? c->Tlo.as<float>() : nullptr, w, c->MV, k, 1.0, 0.0, c->outV.ptr,
