@@ -133,7 +133,10 @@ __global__ void k_refine_apply(int w, const double* __restrict__ S, const double
 // B (upper triangular, w x w, FP64 container) with B^T B = G + delta I to
 // FP32 accuracy: right-looking Cholesky in FP32 in shared memory, one CTA
 // of 32 x 32 threads (thread (ty, tx) updates rows ty + 32 a, columns
-// tx + 32 b of the trailing matrix, no index division in the loop).
+// tx + 32 b of the trailing matrix, no index division in the loop).  Row k
+// of the trailing matrix is left unscaled (c_kj = r_kk r_kj) and the update
+// is c_ij -= c_ki c_kj / c_kk, so each pivot needs one barrier; the rows
+// are scaled by 1 / r_kk on the way out.
 // It only preconditions Step 4 (its output seeds the FP32 Jacobi sweeps,
 // whose vectors are then refined in FP64 against G itself), so a shift
 // delta = 1e-6 max diag(G) keeps it defined whatever G's conditioning: the
@@ -155,24 +158,22 @@ __global__ void __launch_bounds__(1024) k_chol32_shift(int w, const double* __re
   for (int i = tid; i < w; i += blockDim.x) cm[i * ws + i] += delta;
   __syncthreads();
   for (int k = 0; k < w; ++k) {
-    // row k of R: r_kk = sqrt(c_kk), r_kj = c_kj / r_kk (kept in rowk)
-    const float d = sqrtf(fmaxf(cm[k * ws + k], delta));
-    for (int j = k + tid; j < w; j += blockDim.x) {
-      const float v = (j == k) ? d : cm[k * ws + j] / d;
-      rowk[j] = v;
-      cm[k * ws + j] = v;
-    }
-    __syncthreads();
-    // trailing update c_ij -= r_ki r_kj for k < i <= j
+    // pivot c_kk (floored at the shift: rounding cannot make it vanish)
+    const float ck = fmaxf(cm[k * ws + k], delta);
+    const float inv = __fdividef(1.f, ck);
+    if (tid == 0) rowk[k] = ck;
+    // trailing update c_ij -= c_ki c_kj / c_kk for k < i <= j (row k unchanged)
     for (int i = k + 1 + ty; i < w; i += 32) {
-      const float ri = rowk[i];
-      for (int j = i + tx; j < w; j += 32) cm[i * ws + j] -= ri * rowk[j];
+      const float a = cm[k * ws + i] * inv;
+      for (int j = i + tx; j < w; j += 32) cm[i * ws + j] = fmaf(-a, cm[k * ws + j], cm[i * ws + j]);
     }
     __syncthreads();
   }
+  // r_kk = sqrt(c_kk), r_kj = c_kj / r_kk
   for (int e = tid; e < w * w; e += blockDim.x) {
     const int i = e / w, j = e % w;
-    B[e] = j >= i ? (double)cm[i * ws + j] : 0.0;
+    const float rs = rsqrtf(rowk[i]);
+    B[e] = j > i ? (double)(cm[i * ws + j] * rs) : (j == i ? (double)(rowk[i] * rs) : 0.0);
   }
 }
 
