@@ -978,6 +978,85 @@ inline unsigned grid1(int64_t count, int threads = 256) {
   return (unsigned)std::max<int64_t>(1, cdiv(count, threads));
 }
 
+// C = X^T X (p x p, FP64, both triangles; C zeroed by the caller) for an
+// FP64 X whose entries are accurate to well below FP32 significance
+// anyway: each entry is rounded to FP32, every product x_a x_b is split
+// exactly into pr + e (pr = RN(x_a x_b), e = fma(x_a, x_b, -pr)), and the pr
+// are summed with Knuth's two-sum, the rounding errors and the e going into
+// a compensation term.  Each CTA sums rows_per_block rows of one upper tile
+// pair (64 x 64) with 4 x 4 entries per thread, then adds s + c to C in FP64
+// (and to the mirrored entry for an off-diagonal pair).  The result is
+// within a few u32^2 of sum |x_a x_b| of the exact Gram of the rounded X:
+// FP64-class for the eigenvalues of Step 4, at FP32 arithmetic rates (the
+// FP64 pipe retires about one sixtieth of the FP32 rate).  Explicit _rn
+// intrinsics keep the compiler from contracting the two-sum into FMAs.
+__global__ void __launch_bounds__(256)
+k_gram_comp(int64_t m, int p, const double* __restrict__ X, int64_t ldx, double* __restrict__ C, int64_t ldc,
+            int64_t rows_per_block, int nt) {
+  constexpr int RC = 32;
+  __shared__ float Xs[RC][64 + 1];
+  __shared__ float Ys[RC][64 + 1];
+  // upper tile pair (ti <= tj) of blockIdx.y
+  int ti = 0, tj = 0;
+  {
+    int y = (int)blockIdx.y;
+    while (y >= nt - ti) { y -= nt - ti; ++ti; }
+    tj = ti + y;
+  }
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int p0 = ti * 64, q0 = tj * 64;
+  const int64_t rbeg = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t rend = min(m, rbeg + rows_per_block);
+  float sum[4][4], cmp[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { sum[a][b] = 0.f; cmp[a][b] = 0.f; }
+  for (int64_t r0 = rbeg; r0 < rend; r0 += RC) {
+    for (int e = tid; e < RC * 64; e += 256) {
+      const int rr = e / 64, cc = e % 64;
+      const int64_t r = r0 + rr;
+      const bool rok = r < rend;
+      Xs[rr][cc] = (rok && p0 + cc < p) ? (float)X[r * ldx + p0 + cc] : 0.f;
+      Ys[rr][cc] = (rok && q0 + cc < p) ? (float)X[r * ldx + q0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < RC; ++rr) {
+      float xv[4], yv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xv[a] = Xs[rr][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yv[b] = Ys[rr][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float pr = __fmul_rn(xv[a], yv[b]);
+          const float e = fmaf(xv[a], yv[b], -pr);
+          const float s0 = sum[a][b];
+          const float s1 = __fadd_rn(s0, pr);
+          const float bp = __fsub_rn(s1, s0);
+          const float err = __fadd_rn(__fsub_rn(s0, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
+          sum[a][b] = s1;
+          cmp[a][b] = __fadd_rn(cmp[a][b], __fadd_rn(err, e));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = p0 + ty * 4 + a, j = q0 + tx * 4 + b;
+      if (i < p && j < p) {
+        const double v = (double)sum[a][b] + (double)cmp[a][b];
+        atomicAdd(&C[(int64_t)i * ldc + j], v);
+        if (ti != tj) atomicAdd(&C[(int64_t)j * ldc + i], v);
+      }
+    }
+}
+
 }  // namespace
 
 // ===================================================================== host
@@ -997,6 +1076,19 @@ void gram(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, const v
     k_gram<double><<<grid, 256, 0, st>>>(m, p, q, (const double*)X, ldx, (const double*)Y, ldy, C, ldc, rpb, active);
   else
     k_gram<float><<<grid, 256, 0, st>>>(m, p, q, (const float*)X, ldx, (const float*)Y, ldy, C, ldc, rpb, active);
+  RPCA_CUDA_TRY(cudaGetLastError());
+  count_launch();
+}
+
+void gram_sym_comp(int64_t m, int p, const double* X, int64_t ldx, double* C, int64_t ldc, cudaStream_t st) {
+  RPCA_CUDA_TRY(cudaMemset2DAsync(C, ldc * sizeof(double), 0, p * sizeof(double), p, st));
+  if (m <= 0 || p <= 0) return;
+  const int nt = (int)cdiv(p, 64);
+  const int npair = nt * (nt + 1) / 2;
+  const int64_t want = std::max<int64_t>(1, (int64_t)num_sms() / npair);
+  const int64_t rpb = std::max<int64_t>(64, round_up(cdiv(m, want), 32));
+  dim3 grid((unsigned)cdiv(m, rpb), (unsigned)npair);
+  k_gram_comp<<<grid, 256, 0, st>>>(m, p, X, ldx, C, ldc, rpb, nt);
   RPCA_CUDA_TRY(cudaGetLastError());
   count_launch();
 }
