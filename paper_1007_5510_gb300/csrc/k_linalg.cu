@@ -979,23 +979,24 @@ inline unsigned grid1(int64_t count, int threads = 256) {
 }
 
 // C = X^T X (p x p, FP64, both triangles; C zeroed by the caller) for an
-// FP64 X whose entries are accurate to well below FP32 significance
-// anyway: each entry is rounded to FP32, every product x_a x_b is split
-// exactly into pr + e (pr = RN(x_a x_b), e = fma(x_a, x_b, -pr)), and the pr
-// are summed with Knuth's two-sum, the rounding errors and the e going into
-// a compensation term.  Each CTA sums rows_per_block rows of one upper tile
-// pair (64 x 64) with 4 x 4 entries per thread, then adds s + c to C in FP64
-// (and to the mirrored entry for an off-diagonal pair).  The result is
-// within a few u32^2 of sum |x_a x_b| of the exact Gram of the rounded X:
-// FP64-class for the eigenvalues of Step 4, at FP32 arithmetic rates (the
-// FP64 pipe retires about one sixtieth of the FP32 rate).  Explicit _rn
-// intrinsics keep the compiler from contracting the two-sum into FMAs.
+// FP64 X, in FP32 arithmetic: each entry is split into x = h + t (h =
+// RN32(x), t = RN32(x - h)), every product h_a h_b is split exactly into
+// pr + e (pr = RN(h_a h_b), e = fma(h_a, h_b, -pr)), and the pr are summed
+// with Knuth's two-sum; the two-sum's rounding errors, the e and the cross
+// terms h_a t_b + t_a h_b go into a compensation term (t_a t_b, below
+// u32^2 |x_a x_b|, is dropped).  Each CTA sums rows_per_block rows of one
+// upper tile pair (64 x 64) with 4 x 4 entries per thread, then adds s + c
+// to C in FP64 (and to the mirrored entry for an off-diagonal pair).  The
+// result is within a few u32^2 of sum |x_a x_b| of the exact Gram: FP64-class
+// for the eigenvalues of Step 4, at FP32 arithmetic rates (the FP64 pipe
+// retires about one sixtieth of the FP32 rate).  Explicit _rn intrinsics
+// keep the compiler from contracting the two-sum into FMAs.
 __global__ void __launch_bounds__(256)
 k_gram_comp(int64_t m, int p, const double* __restrict__ X, int64_t ldx, double* __restrict__ C, int64_t ldc,
             int64_t rows_per_block, int nt) {
   constexpr int RC = 32;
-  __shared__ float Xs[RC][64 + 1];
-  __shared__ float Ys[RC][64 + 1];
+  __shared__ float Xs[RC][64 + 1], Xt[RC][64 + 1];
+  __shared__ float Ys[RC][64 + 1], Yt[RC][64 + 1];
   // upper tile pair (ti <= tj) of blockIdx.y
   int ti = 0, tj = 0;
   {
@@ -1017,17 +1018,28 @@ k_gram_comp(int64_t m, int p, const double* __restrict__ X, int64_t ldx, double*
       const int rr = e / 64, cc = e % 64;
       const int64_t r = r0 + rr;
       const bool rok = r < rend;
-      Xs[rr][cc] = (rok && p0 + cc < p) ? (float)X[r * ldx + p0 + cc] : 0.f;
-      Ys[rr][cc] = (rok && q0 + cc < p) ? (float)X[r * ldx + q0 + cc] : 0.f;
+      const double xa = (rok && p0 + cc < p) ? X[r * ldx + p0 + cc] : 0.0;
+      const double xb = (rok && q0 + cc < p) ? X[r * ldx + q0 + cc] : 0.0;
+      const float ha = (float)xa, hb = (float)xb;
+      Xs[rr][cc] = ha;
+      Xt[rr][cc] = (float)(xa - (double)ha);
+      Ys[rr][cc] = hb;
+      Yt[rr][cc] = (float)(xb - (double)hb);
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
     for (int rr = 0; rr < RC; ++rr) {
-      float xv[4], yv[4];
+      float xv[4], yv[4], xl[4], yl[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) xv[a] = Xs[rr][ty * 4 + a];
+      for (int a = 0; a < 4; ++a) {
+        xv[a] = Xs[rr][ty * 4 + a];
+        xl[a] = Xt[rr][ty * 4 + a];
+      }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) yv[b] = Ys[rr][tx * 4 + b];
+      for (int b = 0; b < 4; ++b) {
+        yv[b] = Ys[rr][tx * 4 + b];
+        yl[b] = Yt[rr][tx * 4 + b];
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -1038,8 +1050,9 @@ k_gram_comp(int64_t m, int p, const double* __restrict__ X, int64_t ldx, double*
           const float s1 = __fadd_rn(s0, pr);
           const float bp = __fsub_rn(s1, s0);
           const float err = __fadd_rn(__fsub_rn(s0, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
+          const float cross = fmaf(xv[a], yl[b], __fmul_rn(xl[a], yv[b]));
           sum[a][b] = s1;
-          cmp[a][b] = __fadd_rn(cmp[a][b], __fadd_rn(err, e));
+          cmp[a][b] = __fadd_rn(cmp[a][b], __fadd_rn(__fadd_rn(err, e), cross));
         }
     }
     __syncthreads();

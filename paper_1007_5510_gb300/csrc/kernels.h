@@ -61,8 +61,8 @@ bool pass_cvt(const PassArgs& a, cudaStream_t st, uint32_t* dev_err);
 void gram(bool f64, int64_t m, int p, int q, const void* X, int64_t ldx, const void* Y,
           int64_t ldy, double* C, int64_t ldc, bool accumulate, cudaStream_t st,
           const uint32_t* active = nullptr);
-// C (p x p, FP64, both triangles) = X^T X for X m x p FP64 whose entries
-// need only FP32 significance: exact FP32 products, compensated sums.
+// C (p x p, FP64, both triangles) = X^T X for X m x p FP64, FP64-class, in
+// FP32 arithmetic (hi/lo split, exact products, compensated sums).
 void gram_sym_comp(int64_t m, int p, const double* X, int64_t ldx, double* C, int64_t ldc, cudaStream_t st);
 // Y[:, 0:q] = beta * Y + alpha * X M, X m x p, M p x q FP64 (ldm).  In-place
 // safe when Y aliases X (rows are staged before they are overwritten).

@@ -828,8 +828,8 @@ void do_finish_enqueue(rpca_ctx* c, void* U, int64_t ldu, double* S, void* V, in
   bool g4 = gram_step4(c);
   c->tic(c->i + 3);
   if (g4) {
-    // Step 4 from G = T^T T (FP64-class: T's entries rounded to FP32, below
-    // their own error, exact products, compensated sums): G' = (I - E/2) G (I - E/2) is the Gram
+    // Step 4 from G = T^T T (FP64-class, in FP32 arithmetic with compensated
+    // sums): G' = (I - E/2) G (I - E/2) is the Gram
     // of the Rayleigh-Ritz matrix of the orthonormalised basis; its
     // eigenvectors W are T's right singular vectors and V = T (I - E/2) W / sigma
     gram_sym_comp(c->n, w, c->T64.as<double>(), w, c->RT, w, st);
