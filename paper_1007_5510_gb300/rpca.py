@@ -373,22 +373,31 @@ def estimate_error(A, U, S, V, j=6, q=None, omega=None, seed=0, col_scale=None):
     FP64); else the Philox stream of `seed`.  Returns (p, per-column p)."""
     import numpy as np
     torch = _torch()
-    _check_mat(A, "A", _storage_dtypes())
+    # shapes and types first, devices last
+    _check_shape(A, "A", _storage_dtypes())
     m, n = A.shape
     cdt = torch.float64 if A.dtype == torch.float64 else torch.float32
-    kd = int(S.shape[0])
-    _check_shape(U, "U", (cdt,), rows=m)
-    _check_shape(V, "V", (cdt,), rows=n)
-    _check_device(U, "U", A.device)
-    _check_device(V, "V", A.device)
-    if U.shape[1] < kd or V.shape[1] < kd:
-        raise ValueError("U and V need kd = len(S) columns")
+    if getattr(S, "ndim", 1) != 1:
+        raise ValueError("S must be a vector of singular values")
+    kd = int(len(S))
+    if kd < 1 or kd > min(m, n):
+        raise ValueError("S has %d values: the rank must be in [1, min(m, n)]" % kd)
+    _check_shape(U, "U", (cdt,), rows=m, cols=kd)
+    _check_shape(V, "V", (cdt,), rows=n, cols=kd)
     q = kd if q is None else int(q)
+    if q < 1 or q > n:
+        raise ValueError("q = %d start vectors: needs 1 <= q <= n" % q)
+    if int(j) < 1:
+        raise ValueError("j = %d power steps: needs j >= 1" % int(j))
     om = None
     if omega is not None:
         om = np.ascontiguousarray(np.asarray(omega, np.float64))
         if om.shape != (n, q):
             raise ValueError("omega must be n x q")
+    _check_vec(col_scale, "col_scale", n, torch.float32, A.device)
+    _check_device(A, "A")
+    _check_device(U, "U", A.device)
+    _check_device(V, "V", A.device)
     Sd = torch.as_tensor(S, dtype=torch.float64, device=A.device).contiguous()
     prob = Problem(m, n, kd, kd, 0, ctypes.c_uint64(seed), None, dtype_code(A), 0, 0, _stream_ptr())
     mat = Matrix(ctypes.c_void_p(A.data_ptr()), A.stride(0),
@@ -407,8 +416,16 @@ def pca_adaptive(A, tol, k0, kmax, oversample=2, i=2, j=6, seed=0, col_scale=Non
     estimate of the error is at most tol (rpca_run_adaptive).  Returns
     (U, S, V, k, eps) with U, S, V cut to rank k."""
     torch = _torch()
-    _check_mat(A, "A", _storage_dtypes())
+    _check_shape(A, "A", _storage_dtypes())
     m, n = A.shape
+    if not (float(tol) > 0.0):
+        raise ValueError("tol must be positive")
+    if int(k0) < 1 or int(kmax) < int(k0) or int(kmax) > min(m, n):
+        raise ValueError("needs 1 <= k0 <= kmax <= min(m, n), got k0 = %d, kmax = %d" % (int(k0), int(kmax)))
+    if int(oversample) < 0 or int(i) < 0 or int(j) < 1:
+        raise ValueError("needs oversample >= 0, i >= 0, j >= 1")
+    _check_vec(col_scale, "col_scale", n, torch.float32, A.device)
+    _check_device(A, "A")
     cdt = torch.float64 if A.dtype == torch.float64 else torch.float32
     U = torch.empty(m, kmax, dtype=cdt, device=A.device)
     V = torch.empty(n, kmax, dtype=cdt, device=A.device)

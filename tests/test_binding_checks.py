@@ -73,3 +73,63 @@ def test_context_matrix_shape_is_checked():
         ctx._matrix(torch.zeros(10, 4))                   # CPU tensor without host_a
     with pytest.raises(ValueError, match="stride"):
         ctx._matrix(torch.zeros(4, 10).t())
+
+
+def _est_ok():
+    m, n, kd = 40, 12, 3
+    return torch.zeros(m, n), torch.zeros(m, kd), torch.ones(kd, dtype=torch.float64), torch.zeros(n, kd)
+
+
+@pytest.mark.parametrize("case,word", [
+    ("A_int", "dtype"), ("S_matrix", "vector"), ("S_empty", "rank"), ("S_too_long", "rank"),
+    ("U_short", "rows"), ("U_narrow", "columns"), ("U_fp64", "dtype"), ("V_short", "rows"),
+    ("V_transposed", "stride"), ("q_zero", "start vectors"), ("q_above_n", "start vectors"),
+    ("j_zero", "power steps"), ("omega_shape", "omega"), ("scale_short", "col_scale"),
+    ("all_on_cpu", "CUDA"),
+])
+def test_estimate_error_binding_rejects(case, word):
+    """Every rejected argument fails before a pointer reaches the C-ABI."""
+    A, U, S, V = _est_ok()
+    kw = {}
+    if case == "A_int":
+        A = A.to(torch.int32)
+    elif case == "S_matrix":
+        S = torch.ones(3, 1, dtype=torch.float64)
+    elif case == "S_empty":
+        S = torch.ones(0, dtype=torch.float64)
+    elif case == "S_too_long":
+        S = torch.ones(13, dtype=torch.float64)
+    elif case == "U_short":
+        U = U[:-1]
+    elif case == "U_narrow":
+        U = U[:, :-1]
+    elif case == "U_fp64":
+        U = U.double()
+    elif case == "V_short":
+        V = V[:-1]
+    elif case == "V_transposed":
+        V = torch.zeros(3, 12).t()
+    elif case == "q_zero":
+        kw["q"] = 0
+    elif case == "q_above_n":
+        kw["q"] = 13
+    elif case == "j_zero":
+        kw["j"] = 0
+    elif case == "omega_shape":
+        kw["q"], kw["omega"] = 2, [[0.0] * 3] * 12
+    elif case == "scale_short":
+        kw["col_scale"] = torch.ones(11)
+    with pytest.raises(ValueError, match=word):
+        R.estimate_error(A, U, S, V, **kw)
+
+
+@pytest.mark.parametrize("kw,word", [
+    (dict(tol=0.0), "tol"), (dict(tol=-1.0), "tol"), (dict(k0=0), "k0"), (dict(kmax=2), "kmax"),
+    (dict(kmax=13), "kmax"), (dict(oversample=-1), "oversample"), (dict(j=0), "j >= 1"),
+    (dict(col_scale=torch.ones(5)), "col_scale"), (dict(), "CUDA"),
+])
+def test_pca_adaptive_binding_rejects(kw, word):
+    args = dict(tol=1e-3, k0=4, kmax=8)
+    args.update(kw)
+    with pytest.raises(ValueError, match=word):
+        R.pca_adaptive(torch.zeros(40, 12), **args)
