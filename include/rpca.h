@@ -292,7 +292,9 @@ rpca_status rpca_estimate_error(const rpca_problem* p, const rpca_matrix* A,
  * *k_out its rank and *eps_out its estimate (> tol only when kmax or the
  * limits of the method stopped the doubling).  The Remark after Section 3
  * refers the choice of k to the literature; this is the doubling rule with
- * the paper's own estimator.  Synchronises p->stream. */
+ * the paper's own estimator.  A is a device matrix: RPCA_CENTER and
+ * RPCA_HOST_A give RPCA_EINVAL before anything runs.  Synchronises
+ * p->stream. */
 rpca_status rpca_run_adaptive(const rpca_problem* p, const rpca_matrix* A,
                               double tol, int32_t kmax, int32_t j, void* U,
                               int64_t ldu, double* S, void* V, int64_t ldv,

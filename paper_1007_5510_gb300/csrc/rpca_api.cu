@@ -1831,6 +1831,8 @@ rpca_status rpca_run_adaptive(const rpca_problem* p, const rpca_matrix* A, doubl
                               double* eps_out) {
   if (!p || !A || !U || !S || !V || !k_out || !eps_out || !(tol > 0.0) || j < 1) return RPCA_EINVAL;
   if (kmax < p->k || ldu < kmax || ldv < kmax) return RPCA_EINVAL;
+  // the estimate takes an uncentred device matrix: refuse before any run
+  if (p->flags & (RPCA_CENTER | RPCA_HOST_A)) return RPCA_EINVAL;
   const int over = p->l - p->k;
   if (over < 0) return RPCA_EINVAL;
   const int64_t mn = std::min(p->m, p->n);

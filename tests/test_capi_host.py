@@ -100,3 +100,25 @@ def test_wait_expiry_hook_arms_and_disarms(lib):
     default so no later launch is affected."""
     assert lib.rpca_test_arm_wait_expiry(0, 2_000_000_000, -1) == 0
     assert lib.rpca_test_arm_wait_expiry(1, 2_000_000_000, -1) == 0
+
+
+@pytest.mark.parametrize("flags,expect_einval", [(0x1, True), (0x2, True), (0x0, False)])
+def test_adaptive_rank_refuses_centred_or_host_matrices_first(lib, flags, expect_einval):
+    """rpca_run_adaptive rejects RPCA_CENTER / RPCA_HOST_A before any run
+    (the error estimate takes an uncentred device matrix); a valid call on a
+    machine without a GPU reports ENODEV."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("the valid case would run on the GPU")
+    m, n, kmax = 100, 50, 10
+    A = np.zeros((m, n), np.float32)
+    U = np.zeros((m, kmax), np.float32)
+    V = np.zeros((n, kmax), np.float32)
+    S = np.zeros(kmax, np.float64)
+    p = _problem(flags=flags)
+    mat = rpca.Matrix(ctypes.c_void_p(A.ctypes.data), n, None)
+    k_out, eps = ctypes.c_int32(), ctypes.c_double()
+    s = lib.rpca_run_adaptive(ctypes.byref(p), ctypes.byref(mat), 1e-3, kmax, 6, ctypes.c_void_p(U.ctypes.data), kmax,
+                              ctypes.c_void_p(S.ctypes.data), ctypes.c_void_p(V.ctypes.data), kmax,
+                              ctypes.byref(k_out), ctypes.byref(eps))
+    assert s == (-1 if expect_einval else -4)
